@@ -1,0 +1,342 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by the mathematics, independent of
+the oracle's own code: closed forms, invariants, brute force on tiny inputs and a statistical
+expectation. Each test names the passage it pins."""
+
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adjoint, aliasing, assign, bispectrum, bspline, direct, fourier, power
+from paper_1512_07295_gb300 import catalogs
+
+
+# --- Sec. 2.3 kernels against eq:intkerFT -----------------------------------------------------------
+
+def _ft_numeric(p, nu):
+    """int W^(p)(s) exp(-2 pi i nu s) ds by Gauss-Legendre on every unit-half piece (exact for the
+    piecewise polynomials, whatever their coefficients)."""
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    total = 0.0
+    for a in np.arange(-p / 2.0, p / 2.0, 0.5):
+        s = a + 0.25 * (xg + 1.0)
+        total += 0.25 * np.sum(wg * bspline.weight(p, s) * np.cos(2 * np.pi * nu * s))
+    return total
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_kernel_fourier_transform_is_sinc_power(p):
+    # eq:intkerFT: the FT of the order-p B-spline of unit spacing is sinc^p(pi nu); this pins the
+    # piece-wise coefficients of Sec. 2.3 (and the CIC support reading |s| < 1).
+    for nu in [0.0, 0.1, 0.25, 0.37, 0.5, 0.8, 1.3]:
+        expect = bspline.sinc(np.pi * nu) ** p
+        assert abs(_ft_numeric(p, nu) - expect) < 1e-12
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_kernel_derivative_matches_finite_difference(p):
+    s = np.linspace(-2.3, 2.3, 461) + 1e-3
+    h = 1e-6
+    fd = (bspline.weight(p, s + h) - bspline.weight(p, s - h)) / (2 * h)
+    assert np.max(np.abs(fd - bspline.dweight(p, s))) < 1e-6
+
+
+# --- eq:delgrid: partition of unity, single particle, lattices -------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("shift", [False, True])
+def test_mass_conservation(p, shift):
+    pos = catalogs.poisson(500, 100.0, seed=11)
+    w = catalogs.random_weights(500, seed=12)
+    rho = assign.assign(pos, 100.0, 12, p, weights=w, shift=shift)
+    assert abs(rho.sum() - w.sum()) < 1e-11 * w.sum()
+    assert rho.min() >= 0.0
+
+
+def _poisson_sum_1d(u, ng, p, mmax):
+    """sum_j W^(p)(j - u) e^{-2 pi i n j/N} for all n, by Poisson summation of the continuous
+    transform: sum_m e^{-2 pi i (nu+m) u} sinc^p(pi (nu+m)), nu = n/N (eq:tdelG2 with eq:intkerFT)."""
+    nu = np.arange(ng) / ng
+    m = np.arange(-mmax, mmax + 1)
+    f = nu[:, None] + m[None, :]
+    return np.sum(np.exp(-2j * np.pi * f * u) * bspline.sinc(np.pi * f) ** p, axis=1)
+
+
+@pytest.mark.parametrize("p,tol", [(2, 2e-6), (3, 1e-9), (4, 1e-11)])
+@pytest.mark.parametrize("shift", [False, True])
+def test_single_particle_grid_transform(p, tol, shift):
+    # One particle: the DFT of its mass grid is the product over axes of the aliased window sums.
+    ng, box = 8, 10.0
+    x = np.array([[1.234, 5.678, 9.012]])
+    rho = assign.assign(x, box, ng, p, shift=shift)
+    g = np.fft.fftn(rho)
+    u = x[0] * ng / box + (0.5 if shift else 0.0)
+    ax = [_poisson_sum_1d(u[a], ng, p, 200000 if p == 2 else 4000) for a in range(3)]
+    expect = ax[0][:, None, None] * ax[1][None, :, None] * ax[2][None, None, :]
+    assert np.max(np.abs(g - expect)) < tol
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_full_lattice_has_no_power(p):
+    # Particles on every node: the partition of unity makes the grid uniform, so delta = 0 (both
+    # the plain and the shifted grid), and P vanishes in every bin.
+    ng, box = 8, 50.0
+    pos = catalogs.lattice(ng, box, offset=0.0)
+    rho1 = assign.assign(pos, box, ng, p)
+    rho2 = assign.assign(pos, box, ng, p, shift=True)
+    assert np.max(np.abs(rho1 - 1.0)) < 1e-12
+    assert np.max(np.abs(rho2 - 1.0)) < 1e-12
+    pk, _, cnt = power.power_spectrum(fourier.density_modes(rho1, p, rho2), box)
+    assert np.all(cnt > 0)
+    assert np.max(np.abs(pk)) < 1e-20 * box ** 3 / ng ** 3
+
+
+def test_second_lattice_pcs_pattern():
+    # Particles on every second node, PCS: node weights 2/3 (own node) and 1/6 (neighbours) give the
+    # per-axis pattern (2/3, 1/3); its DFT is N/2 at n = 0 and N/2 (2/3 - 1/3) at n = N/2, so the only
+    # non-zero modes have every n_i in {0, -N/2}.
+    ng, box = 8, 16.0
+    pos = catalogs.lattice(ng // 2, box, offset=0.0)
+    rho = assign.assign(pos, box, ng, 4)
+    d = fourier.fourier_coefficients(fourier.overdensity(rho))
+    a = {0: 1.0, ng // 2: 1.0 / 3.0}  # per-axis DFT normalised by its n = 0 value
+    for idx in itertools.product(range(ng), repeat=3):
+        if all(i in a for i in idx) and idx != (0, 0, 0):
+            assert abs(d[idx] - a[idx[0]] * a[idx[1]] * a[idx[2]]) < 1e-13
+        else:
+            assert abs(d[idx]) < 1e-13
+
+
+# --- FFT conventions ---------------------------------------------------------------------------------
+
+def test_fft_matches_direct_dft():
+    ng = 5
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((ng, ng, ng))
+    out = np.zeros((ng, ng, ng), dtype=complex)
+    j = np.array(list(itertools.product(range(ng), repeat=3)))
+    for n in itertools.product(range(ng), repeat=3):
+        ph = np.exp(-2j * np.pi * (j @ np.array(n)) / ng)
+        out[n] = np.sum(f.ravel() * ph) / ng ** 3
+    assert np.max(np.abs(fourier.fourier_coefficients(f) - out)) < 1e-14
+
+
+def test_parseval_full_grid():
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((6, 6, 6))
+    d = fourier.fourier_coefficients(f)
+    assert abs(np.sum(np.abs(d) ** 2) * f.size - np.sum(f * f)) < 1e-10
+
+
+def test_interlace_phase_nyquist_convention():
+    # Signed index: slot N/2 is -N/2, so the phase there is exp(-i pi/2) per axis.
+    ph = fourier.interlace_phase(8)
+    assert abs(ph[4, 0, 0] - np.exp(-1j * np.pi / 2)) < 1e-15
+    assert abs(ph[1, 2, 3] - np.exp(1j * np.pi * 6 / 8)) < 1e-15
+
+
+# --- binning: exact integer counts --------------------------------------------------------------------
+
+@pytest.mark.parametrize("ng", [6, 8, 12])
+def test_mode_counts_brute_force(ng):
+    edges = power.default_edges(ng)
+    _, _, cnt = power.power_spectrum(np.ones((ng, ng, ng), dtype=complex), 1.0, edges)
+    ref = np.zeros(len(edges) - 1, dtype=np.int64)
+    half = ng // 2
+    for n in itertools.product(range(-half, half), repeat=3):
+        r = math.sqrt(n[0] ** 2 + n[1] ** 2 + n[2] ** 2)
+        if r == 0:
+            continue
+        b = int(math.floor(r + 0.5))  # (b - 1/2) <= |n| < (b + 1/2)
+        if 1 <= b <= half:
+            ref[b - 1] += 1
+    assert np.array_equal(cnt, ref)
+
+
+# --- shot-noise aliasing sums (eq:Pknoint and its interlaced form with P = 0) --------------------------
+
+def _bspline_autocorr(p, m):
+    """int W^(p)(s) W^(p)(s + m) ds, Gauss-Legendre per half-unit piece (exact for polynomials)."""
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    tot = 0.0
+    for a in np.arange(-p / 2.0 - abs(m), p / 2.0 + abs(m), 0.5):
+        s = a + 0.25 * (xg + 1.0)
+        tot += 0.25 * np.sum(wg * bspline.weight(p, s) * bspline.weight(p, s + m))
+    return tot
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_alias_sum_equals_autocorrelation_series(p):
+    # sum_m sinc^{2p}(pi (x - m)) = sum_m M_{2p}(m) cos(2 pi m x), M the kernel autocorrelation; for
+    # CIC the coefficients are the rationals 2/3 and 1/6.
+    xs = np.array([0.05, 0.2, 0.33, 0.5])
+    series = np.zeros_like(xs)
+    coeffs = [_bspline_autocorr(p, m) for m in range(p)]
+    for m, c in enumerate(coeffs):
+        series += c * (1.0 if m == 0 else 2.0 * np.cos(2 * np.pi * m * xs))
+    imgs, _ = aliasing._image_sums(xs, p, 4000)
+    assert np.max(np.abs(series - imgs)) < (1e-9 if p == 2 else 1e-12)
+    if p == 2:
+        assert abs(coeffs[0] - float(Fraction(2, 3))) < 1e-14
+        assert abs(coeffs[1] - float(Fraction(1, 6))) < 1e-14
+
+
+@pytest.mark.parametrize("p,interlace", [(2, False), (2, True), (4, True)])
+def test_poisson_power_matches_alias_expectation(p, interlace):
+    # A uniform random catalogue has P = 0, so the window-corrected estimator averages to the aliased
+    # shot noise (eq:Pknoint; with interlacing only the even images survive, eq:intdelta). A wrong
+    # interlacing phase sign or a wrong window fails this by many sigma near the Nyquist frequency.
+    ng, box, npart, nseeds = 8, 100.0, 400, 300
+    shot = box ** 3 / npart
+    edges = power.default_edges(ng)
+    b = power.bin_index(ng, edges)
+    half = ng // 2
+    sn = fourier.signed_index(ng)
+    nvec = np.stack(np.meshgrid(sn, sn, sn, indexing="ij"), axis=-1)
+    sel = b >= 0
+    e_mode = aliasing.shot_noise_expectation(nvec[sel], ng, p, interlace, shot, mmax=3000)
+    cnt = np.bincount(b[sel], minlength=half)
+    expect = np.bincount(b[sel], weights=e_mode, minlength=half) / cnt
+    # per-mode variance: |delta|^2 of a sum of many particles is exponential (variance = mean^2);
+    # modes n and -n are identical except on Nyquist planes, so use half the count.
+    var_mode = np.bincount(b[sel], weights=e_mode ** 2, minlength=half) / cnt
+    acc = np.zeros(half)
+    for s in range(nseeds):
+        pos = catalogs.poisson(npart, box, seed=1000 + s)
+        r1 = assign.assign(pos, box, ng, p)
+        r2 = assign.assign(pos, box, ng, p, shift=True) if interlace else None
+        pk, _, _ = power.power_spectrum(fourier.density_modes(r1, p, r2), box, edges)
+        acc += pk
+    mean = acc / nseeds
+    sigma = np.sqrt(var_mode / (cnt / 2.0) / nseeds)
+    z = (mean - expect) / sigma
+    assert np.max(np.abs(z)) < 4.5, z
+
+
+def test_interlacing_removes_odd_images_in_expectation():
+    # With interlacing the expected PCS shot noise is much closer to 1/nbar near Nyquist.
+    shot = 1.0
+    n = np.array([[4, 0, 0], [3, 3, 0], [4, 4, 4]])
+    e_no = aliasing.shot_noise_expectation(n, 8, 4, False, shot)
+    e_in = aliasing.shot_noise_expectation(n, 8, 4, True, shot)
+    assert np.all(np.abs(e_in - 1.0) < np.abs(e_no - 1.0))
+
+
+# --- direct summation (eq:deltaDS) and the accuracy ordering of Sec. 3.2 ------------------------------
+
+def test_direct_sum_single_particle_is_plane_wave():
+    x = np.array([[1.0, 2.0, 3.0]])
+    d = direct.direct_modes(x, 8.0, 4)
+    n = fourier.signed_index(4)
+    u = x[0] * 4 / 8.0
+    exp = np.exp(-2j * np.pi * (n[:, None, None] * u[0] + n[None, :, None] * u[1] + n[None, None, :] * u[2]) / 4)
+    exp[0, 0, 0] -= 1.0
+    assert np.max(np.abs(d - exp)) < 1e-14
+
+
+def test_accuracy_ordering_against_direct_summation():
+    # Sec. 3.2: relative to the alias-free direct summation, PCS+interlacing beats CIC+interlacing,
+    # which beats plain CIC (power spectrum up to the Nyquist frequency).
+    box, ng = 100.0, 16
+    pos = catalogs.zeldovich(16, box, rms=2.0, seed=5)
+    ds = direct.direct_modes(pos, box, ng)
+    pk_ds, _, _ = power.power_spectrum(ds, box)
+
+    def err(p, inter):
+        r1 = assign.assign(pos, box, ng, p)
+        r2 = assign.assign(pos, box, ng, p, shift=True) if inter else None
+        pk, _, _ = power.power_spectrum(fourier.density_modes(r1, p, r2), box)
+        return np.max(np.abs(pk / pk_ds - 1.0))
+
+    e_cic, e_cic_i, e_pcs_i = err(2, False), err(2, True), err(4, True)
+    assert e_pcs_i < e_cic_i < e_cic
+
+
+# --- bispectrum (eq:Best, eq:Best2, eq:VBest) ----------------------------------------------------------
+
+def test_bispectrum_fft_form_equals_brute_force():
+    box, ng = 50.0, 12
+    pos = catalogs.zeldovich(12, box, rms=3.0, seed=8)
+    r1 = assign.assign(pos, box, ng, 4)
+    r2 = assign.assign(pos, box, ng, 4, shift=True)
+    delta = fourier.density_modes(r1, 4, r2)
+    b_fft, c_fft = bispectrum.bispectrum_fft(delta, box, 1, 1, 3)
+    b_bf, c_bf = bispectrum.bispectrum_brute(delta, box, 1, 1, 3)
+    assert np.array_equal(c_fft, c_bf)
+    ok = c_bf > 0
+    assert ok.sum() >= 6
+    assert np.max(np.abs(b_fft[ok] / b_bf[ok] - 1.0)) < 1e-10
+
+
+def test_bispectrum_single_triangle():
+    # A field with only the modes q1, q2, q3 = -q1 - q2 (and their partners) of unit amplitude:
+    # the triple product picks exactly the closed triangle.
+    ng, box = 12, 1.0
+    delta = np.zeros((ng, ng, ng), dtype=complex)
+    for q in ([1, 0, 0], [0, 2, 0], [-1, -2, 0]):
+        delta[tuple(np.mod(q, ng))] = 1.0
+        delta[tuple(np.mod(-np.array(q), ng))] = 1.0
+    b, c = bispectrum.bispectrum_fft(delta, box, 0, 1, 3)
+    tri = bispectrum.triangles(3)
+    t = tri.index((2, 2, 1))  # |q| = 1, 2, sqrt(5): shells 1, 2, 2 in 0-based shells of width 1
+    # triplets in that bin: (q2, q3) ordered pairs from the two |q| in [2,3) modes and their partners
+    assert c[t] > 0
+    # sum over triplets of delta delta delta = number of closed triplets using our modes
+    s_expected = 2 * 2  # (q1,q2,q3) and the negated triangle, each counted with the 2 orderings of s2=s3
+    assert abs(b[t] * c[t] - s_expected) < 1e-9
+
+
+def test_triangle_list_size():
+    # 16 shells of width 4 k_f (up to k_N/2 at N_G = 256): the reading s1 <= s2 + s3 + 1 gives 508.
+    assert len(bispectrum.triangles(16)) == 508
+
+
+# --- adjoint -----------------------------------------------------------------------------------------
+
+def test_adjoint_matches_central_differences():
+    box, ng, p = 20.0, 8, 4
+    pos = catalogs.poisson(24, box, seed=21)
+    rng = np.random.default_rng(22)
+    dl = rng.standard_normal(ng // 2)
+
+    def loss(x):
+        r1 = assign.assign(x, box, ng, p)
+        r2 = assign.assign(x, box, ng, p, shift=True)
+        pk, _, _ = power.power_spectrum(fourier.density_modes(r1, p, r2), box)
+        return float(np.dot(dl, pk))
+
+    g = adjoint.position_gradient(pos, box, ng, p, dl)
+    h = 1e-4
+    for i in range(0, 24, 5):
+        for a in range(3):
+            xp = pos.copy(); xp[i, a] += h
+            xm = pos.copy(); xm[i, a] -= h
+            fd = (loss(xp) - loss(xm)) / (2 * h)
+            assert abs(fd - g[i, a]) <= 1e-5 * max(1.0, np.max(np.abs(g))), (i, a, fd, g[i, a])
+
+
+# --- residual factor (eq:res1Di, eq:res1Dnoi, eq:res_comp) ---------------------------------------------
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_fres_hurwitz_forms(p):
+    x = np.array([0.1, 0.25, 0.4, 0.5])
+    for inter in (False, True):
+        assert np.max(np.abs(aliasing.fres_1d(x, p, inter) - aliasing.fres_1d_hurwitz(x, p, inter))) < 1e-9
+    # eq:res_comp from the two truncated sums directly
+    assert np.max(np.abs(aliasing.fres_1d(x, p, True) - aliasing.fres_1d(x / 2, p, False))) < 1e-12
+
+
+def test_oracle_header_marks_test_infrastructure():
+    assert "TEST INFRASTRUCTURE" in oracle.__doc__
+
+
+def test_mode_counts_with_edges_from_zero_exclude_k0():
+    # Bins whose lower edge is 0 must still leave out the n = 0 mode (delta(0) is not a fluctuation).
+    ng = 6
+    edges = np.array([0, 2, 4], dtype=np.int64)  # |n| in [0, 1) and [1, 2)
+    _, _, cnt = power.power_spectrum(np.ones((ng, ng, ng), dtype=complex), 1.0, edges)
+    assert cnt[0] == 0
+    assert cnt[1] == 6  # the six unit vectors
