@@ -339,4 +339,4 @@ def test_mode_counts_with_edges_from_zero_exclude_k0():
     edges = np.array([0, 2, 4], dtype=np.int64)  # |n| in [0, 1) and [1, 2)
     _, _, cnt = power.power_spectrum(np.ones((ng, ng, ng), dtype=complex), 1.0, edges)
     assert cnt[0] == 0
-    assert cnt[1] == 6  # the six unit vectors
+    assert cnt[1] == 6 + 12 + 8  # |n| = 1, sqrt(2), sqrt(3)
