@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the PCS + interlacing power-spectrum path on one GB300 (or N independent replicas).
+
+Workload (one step): P(k) of a 1024^3-particle Zel'dovich-displaced catalogue in a periodic box of
+L = 2000 Mpc/h on an N_G = 512 grid, PCS assignment with interlacing, FP32 cell + offset positions
+(binned by tile, resident in HBM), FP32 grids and FFT, FP64 shell sums: assignment of both grids,
+two real FFTs, the fused deconvolution / interlacing / shell reduction and the finalisation.
+
+Printed: one JSON line (rank 0). ``value`` = particles/s (P(k)/s in ``pk_per_s``); ``e2e`` = the same
+metric through pk_power from pinned host FP64 positions (H2D copy, preparation, binning, assignment,
+FFT, estimate, D2H of P(k) inside the timed region); ``roofline`` for the assignment kernel;
+``cpu_baseline`` = the FP64 CPU oracle on a bounded sample; ``fp64_plain`` = the plain FP64 GPU path
+(global FP64 atomics, FP64 FFT) on the same catalogue.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this build) on a bounded
+sample of the same workload and prints the same metric.
+"""
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particles/s & P(k)/s (PCS+interlace, N_g=512), % HBM roofline vs plain FP64 path"
+RMS_DISP = 4.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nside", type=int, default=1024)
+    ap.add_argument("--ng", type=int, default=512)
+    ap.add_argument("--box", type=float, default=2000.0)
+    ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"ZA clustered catalogue {a.nside}^3 particles, L={a.box:g} Mpc/h, N_G={a.ng}, PCS+interlacing P(k), "
+            f"FP32 cell+offset positions binned by tile")
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def oracle_sample_rate(pos_sample, n_full, box, ng, with_fft=True):
+    """Times the FP64 oracle: assignment of a particle sample (both grids) and, once, the FFT,
+    deconvolution, interlacing and binning at N_G; returns (particles/s of the full workload, detail)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    u = oracle.assign.grid_units(pos_sample, box, ng)
+    r1 = oracle.assign.assign_units(u, ng, 4)
+    r2 = oracle.assign.assign_units(u, ng, 4, shift=True)
+    t_assign = time.perf_counter() - t0
+    t_fft = 0.0
+    if with_fft:
+        t0 = time.perf_counter()
+        delta = oracle.fourier.density_modes(r1, 4, r2)
+        oracle.power.power_spectrum(delta, box)
+        t_fft = time.perf_counter() - t0
+        del delta
+    t_full = t_assign * (n_full / len(pos_sample)) + t_fft
+    return n_full / t_full, {"t_assign_s": t_assign, "t_fft_estimate_s": t_fft, "sample_particles": len(pos_sample),
+                             "t_full_extrapolated_s": t_full}
+
+
+def run_reference(a):
+    """The reference arm: the FP64 CPU oracle, one bounded sample of the workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1512_07295_gb300 import catalogs
+
+    n_full = a.nside ** 3
+    # a Zel'dovich catalogue of the same box and displacement recipe; the oracle's cost per particle
+    # does not depend on the clustering, so a 64^3 lattice stands in for the sample source
+    src = catalogs.zeldovich(64, a.box, rms=RMS_DISP, seed=3)
+    rng = np.random.default_rng(5)
+    sample = 1 << 14
+    rates = []
+    t_start = time.perf_counter()
+    for step in range(a.warmup + a.steps):
+        pos = src[rng.choice(len(src), size=sample, replace=False)]
+        rate, det = oracle_sample_rate(pos, n_full, a.box, a.ng, with_fft=True)
+        if step >= a.warmup:
+            rates.append(rate)
+    wall = time.perf_counter() - t_start
+    value = float(np.median(rates))
+    cores = len(os.sched_getaffinity(0))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * n_full / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "timed": "FP64 CPU oracle per step: 2^14-particle assignment of both "
+                   f"grids + one N_G={a.ng} FFT/deconvolution/binning, assignment time scaled to {n_full} particles"},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                         "sample": "2^14 particles per step (assignment, both grids, single-threaded NumPy) + full "
+                                   f"N_G={a.ng} FFT (scipy, {cores} workers) and binning; extrapolated linearly in N_P"},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.quick:
+        a.nside, a.ng, a.box = 128, 128, 500.0
+    if a.impl == "reference":
+        run_reference(a)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1512_07295_gb300 import api, catalogs, ffi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = ffi.lib()
+
+    n = a.nside ** 3
+    cfg = api.Config(ng=a.ng, box=a.box, order=4, interlace=True, prec="fp32")
+
+    # ---- input: seeded Zel'dovich catalogue (one independent realisation per rank) ----------------
+    pos64 = catalogs.zeldovich_torch(a.nside, a.box, RMS_DISP, seed=3 + rank, device=dev)
+    host64 = None
+    if not a.no_extras:
+        host64 = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        host64.copy_(pos64)
+    cells = api.prepare(pos64, cfg)
+    del pos64
+    torch.cuda.empty_cache()
+    binned = api.bin_particles(cells, cfg)
+    del cells
+    torch.cuda.empty_cache()
+    sorted_, _, offsets = binned
+    ws = api.workspace(cfg, n, ffi.PK_WS_POWER_BINNED, dev)
+    out = (torch.empty(cfg.nb, dtype=torch.float64, device=dev), torch.empty(cfg.nb, dtype=torch.float64, device=dev),
+           torch.empty(cfg.nb, dtype=torch.int64, device=dev))
+    torch.cuda.synchronize()
+
+    def step():
+        api.power_binned(binned, cfg, ws=ws, out=out)
+
+    # ---- timed region ------------------------------------------------------------------------------
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = lib.pk_profile_launches()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.pk_profile_launches() - launches0
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    value = world * n * a.steps / (ms_total * 1e-3)
+    pk_per_s = world * a.steps / (ms_total * 1e-3)
+
+    # ---- per-stage times (same calls, CUDA events at the stage boundaries) ----------------------------
+    lib.pk_profile_enable(1)
+    stages = np.zeros(5)
+    nprof = max(3, min(a.steps, 10))
+    buf = (ctypes.c_double * 5)()
+    for _ in range(nprof):
+        step()
+        lib.pk_profile_read(ctypes.cast(buf, ctypes.c_void_p), 5)
+        stages += np.array(list(buf))
+    lib.pk_profile_enable(0)
+    stages /= nprof
+    t_assign_ms = float(stages[2])
+
+    peaks = measured_peaks() or {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_tflops = nsm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max clock
+    p3 = cfg.order ** 3
+    assign_flop = 2.0 * 2 * p3 * n  # two grids, p^3 multiply-adds per particle each
+    assign_bytes = 16.0 * n + 2 * 4.0 * a.ng ** 3  # particle records read once, two grids written once
+    achieved_tflops = assign_flop / (t_assign_ms * 1e-3) / 1e12
+    achieved_gbs = assign_bytes / (t_assign_ms * 1e-3) / 1e9
+    nh = a.ng * a.ng * (a.ng // 2 + 1)
+    path_bytes = 16.0 * n + 2 * (4.0 * a.ng ** 3 + (4.0 * a.ng ** 3 + 8.0 * nh) + 8.0 * nh)
+    result = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "particles": n, "ng": a.ng, "box": a.box, "order": 4, "interlace": True,
+                   "l2": "inputs (16 B x 1024^3 particles = 17.2 GB) far exceed the 129 MB L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "pk_per_s": pk_per_s,
+        "path_hbm_roofline": {"algorithmic_bytes": path_bytes, "achieved_gbs": path_bytes / (ms_step * 1e-3) / 1e9,
+                              "peak_gbs": hbm_peak, "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak},
+        "stages_ms": {"weights": stages[0], "grid_clear": stages[1], "assign": stages[2], "fft": stages[3],
+                      "estimate": stages[4]},
+        "roofline": {"kernel": "k_assign_tile<4,float>", "bound": "alu", "achieved": achieved_tflops,
+                     "peak": alu_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops,
+                     "traffic": None, "hbm_achieved_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak,
+                     "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:g} MHz"},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+
+    if rank == 0 and not a.no_extras:
+        # ---- plain FP64 GPU path on the same catalogue --------------------------------------------
+        del ws
+        torch.cuda.empty_cache()
+        cfg64 = api.Config(ng=a.ng, box=a.box, order=4, interlace=True, prec="fp64")
+        ws64 = api.workspace(cfg64, n, ffi.PK_WS_POWER_BINNED, dev)
+        api.power_binned(binned, cfg64, ws=ws64)
+        torch.cuda.synchronize()
+        k64 = 2
+        e0.record(stream)
+        for _ in range(k64):
+            api.power_binned(binned, cfg64, ws=ws64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        result["fp64_plain"] = {"ms_per_step": ms64, "value": n / (ms64 * 1e-3), "unit": "particles/s",
+                                "speedup_of_fast_path": ms64 / ms_step}
+        del ws64, binned, sorted_, offsets
+        torch.cuda.empty_cache()
+
+        # ---- e2e through pk_power from pinned host FP64 positions ----------------------------------
+        wsp = api.workspace(cfg, n, ffi.PK_WS_POWER, dev)
+        dpos = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        pk_host = torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            dpos.copy_(host64, non_blocking=True)
+            pk, _, _ = api.power(dpos, cfg, ws=wsp)
+            pk_host.copy_(pk, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ke = 3
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / ke
+        result["e2e"] = {"value": n / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": 24 * n,
+                         "d2h_bytes_per_step": 8 * cfg.nb, "ms_per_step": ms_e2e,
+                         "path": "pk_power: pinned host FP64 xyz -> H2D -> prepare -> bin -> assign -> FFT -> estimate -> D2H"}
+        del wsp, dpos
+        torch.cuda.empty_cache()
+
+        # ---- FP64 CPU oracle on a bounded sample ---------------------------------------------------
+        rng = np.random.default_rng(11)
+        idx = np.sort(rng.choice(n, size=1 << 16, replace=False))
+        sample = host64[torch.from_numpy(idx)].numpy()
+        rate, det = oracle_sample_rate(sample, n, a.box, a.ng, with_fft=True)
+        cores = len(os.sched_getaffinity(0))
+        result["cpu_baseline"] = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"2^16 random particles of the catalogue assigned to both grids (single-threaded "
+                                            f"NumPy) + one full N_G={a.ng} FFT (scipy, {cores} workers), deconvolution and "
+                                            "binning; assignment time scaled linearly to the full catalogue",
+                                  **det}
+    elif not a.no_extras:
+        result["e2e"] = None
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

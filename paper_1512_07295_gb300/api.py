@@ -1,0 +1,276 @@
+"""PyTorch-facing wrappers of the C ABI (include/pk.h). Tensors supply device memory and the current
+CUDA stream; every step of the computation runs in libpk's kernels (and cuFFT for the transforms).
+
+Positions: an (n, 3) float64 CUDA tensor (length units), or an (n, 4) int32 CUDA tensor holding
+pk_cellpos records (packed cell, then the three FP32 offsets as raw bits) as produced by ``prepare``.
+"""
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import ffi
+from .ffi import check
+
+_PREC = {"fp64": ffi.PK_FP64, "fp32": ffi.PK_FP32, "fixed64": ffi.PK_FIXED64}
+
+
+@dataclass
+class Config:
+    """Mirror of pk_config. Bins default to b k_f, b = 1..ng/2 (edges in units of k_f/2)."""
+
+    ng: int
+    box: float
+    order: int = 4
+    interlace: bool = True
+    prec: str = "fp32"
+    bin_lo2: int = 1
+    bin_w2: int = 2
+    nbins: int = 0
+    subtract_shot: bool = False
+
+    def c(self):
+        nb = self.nbins if self.nbins > 0 else self.ng // 2
+        return ffi.PkConfig(int(self.ng), int(self.order), int(bool(self.interlace)), _PREC[self.prec], float(self.box),
+                            int(self.bin_lo2), int(self.bin_w2), int(nb), int(bool(self.subtract_shot)))
+
+    @property
+    def nb(self):
+        return self.nbins if self.nbins > 0 else self.ng // 2
+
+    @property
+    def real_dtype(self):
+        return torch.float32 if self.prec == "fp32" else torch.float64
+
+
+def _p(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _pos_format(pos):
+    if not pos.is_cuda or not pos.is_contiguous():
+        raise ValueError("positions must be a contiguous CUDA tensor")
+    if pos.dtype == torch.float64 and pos.dim() == 2 and pos.shape[1] == 3:
+        return ffi.PK_POS_F64_XYZ
+    if pos.dtype == torch.int32 and pos.dim() == 2 and pos.shape[1] == 4:
+        return ffi.PK_POS_CELL_F32OFF
+    raise ValueError("positions: (n,3) float64 or (n,4) int32 pk_cellpos records")
+
+
+def _weights(w, n, device):
+    if w is None:
+        return None
+    if w.dtype != torch.float32 or w.device != device or not w.is_contiguous() or w.numel() != n:
+        raise ValueError("weights: contiguous float32 tensor of n entries on the positions' device")
+    return w
+
+
+def workspace(cfg, n, kind, device):
+    size = ffi.lib().pk_workspace_size(ctypes.byref(cfg.c()), int(n), int(kind))
+    if size == 0:
+        raise ffi.PkError(ffi.PK_EINVAL, ffi.last_error())
+    return torch.empty(size, dtype=torch.uint8, device=device)
+
+
+def half_shape(ng):
+    return (ng, ng, ng // 2 + 1)
+
+
+def prepare(pos, cfg):
+    """FP64 positions -> (n, 4) int32 pk_cellpos records (a1)."""
+    if _pos_format(pos) != ffi.PK_POS_F64_XYZ:
+        raise ValueError("prepare takes (n,3) float64 positions")
+    out = torch.empty((pos.shape[0], 4), dtype=torch.int32, device=pos.device)
+    check(ffi.lib().pk_prepare(ctypes.byref(cfg.c()), _p(pos), pos.shape[0], _p(out), _stream(pos.device)))
+    return out
+
+
+def cellpos_split(cells):
+    """(packed cell int32, offsets float32 (n,3)) views of pk_cellpos records."""
+    return cells[:, 0], cells[:, 1:].view(torch.float32)
+
+
+def bin_particles(pos, cfg, weights=None):
+    """Counting sort by tile (a2): returns (sorted (n,4) int32, sorted weights or None, tile offsets int64)."""
+    fmt = _pos_format(pos)
+    n = pos.shape[0]
+    w = _weights(weights, n, pos.device)
+    ntile = ffi.lib().pk_tiles_per_axis(ctypes.byref(cfg.c()), None)
+    sorted_ = torch.empty((n, 4), dtype=torch.int32, device=pos.device)
+    wsorted = torch.empty(n, dtype=torch.float32, device=pos.device) if w is not None else None
+    offsets = torch.empty(ntile ** 3 + 1, dtype=torch.int64, device=pos.device)
+    ws = workspace(cfg, n, ffi.PK_WS_BIN, pos.device)
+    check(ffi.lib().pk_bin(ctypes.byref(cfg.c()), _p(pos), fmt, _p(w), n, _p(sorted_), _p(wsorted), _p(offsets), _p(ws),
+                           ws.numel(), _stream(pos.device)))
+    return sorted_, wsorted, offsets
+
+
+def assign(pos, cfg, weights=None):
+    """Mass grids (a3): (grid1, grid2 or None), each (ng, ng, ng) of the precision's real type."""
+    fmt = _pos_format(pos)
+    n = pos.shape[0]
+    w = _weights(weights, n, pos.device)
+    dt = cfg.real_dtype
+    g1 = torch.empty((cfg.ng,) * 3, dtype=dt, device=pos.device)
+    g2 = torch.empty((cfg.ng,) * 3, dtype=dt, device=pos.device) if cfg.interlace else None
+    ws = workspace(cfg, n, ffi.PK_WS_ASSIGN, pos.device)
+    check(ffi.lib().pk_assign(ctypes.byref(cfg.c()), _p(pos), fmt, _p(w), n, _p(g1), _p(g2), _p(ws), ws.numel(),
+                              _stream(pos.device)))
+    return g1, g2
+
+
+def fft_estimate(grid1, grid2, cfg, wsum):
+    """delta(n) on the half-complex layout (ng, ng, ng/2+1) from mass grids (a4+a5)."""
+    ctype = torch.complex64 if cfg.prec == "fp32" else torch.complex128
+    delta = torch.empty(half_shape(cfg.ng), dtype=ctype, device=grid1.device)
+    ws = workspace(cfg, 0, ffi.PK_WS_FFT_ESTIMATE, grid1.device)
+    check(ffi.lib().pk_fft_estimate(ctypes.byref(cfg.c()), _p(grid1), _p(grid2), float(wsum), _p(delta), _p(ws), ws.numel(),
+                                    _stream(grid1.device)))
+    return delta
+
+
+def _outputs(cfg, device):
+    nb = cfg.nb
+    return (torch.empty(nb, dtype=torch.float64, device=device), torch.empty(nb, dtype=torch.float64, device=device),
+            torch.empty(nb, dtype=torch.int64, device=device))
+
+
+def power(pos, cfg, weights=None, return_delta=False, ws=None):
+    """P(k) of a catalogue in any order (a1..a6): (pk, kmean, nmodes[, delta])."""
+    fmt = _pos_format(pos)
+    n = pos.shape[0]
+    w = _weights(weights, n, pos.device)
+    pk, km, nm = _outputs(cfg, pos.device)
+    delta = None
+    if return_delta:
+        ctype = torch.complex64 if cfg.prec == "fp32" else torch.complex128
+        delta = torch.empty(half_shape(cfg.ng), dtype=ctype, device=pos.device)
+    if ws is None:
+        ws = workspace(cfg, n, ffi.PK_WS_POWER, pos.device)
+    check(ffi.lib().pk_power(ctypes.byref(cfg.c()), _p(pos), fmt, _p(w), n, _p(pk), _p(km), _p(nm), _p(delta), _p(ws),
+                             ws.numel(), _stream(pos.device)))
+    return (pk, km, nm, delta) if return_delta else (pk, km, nm)
+
+
+def power_binned(binned, cfg, return_delta=False, ws=None, out=None):
+    """P(k) from the binned layout of ``bin_particles``: (pk, kmean, nmodes[, delta])."""
+    sorted_, wsorted, offsets = binned
+    n = sorted_.shape[0]
+    pk, km, nm = out if out is not None else _outputs(cfg, sorted_.device)
+    delta = None
+    if return_delta:
+        ctype = torch.complex64 if cfg.prec == "fp32" else torch.complex128
+        delta = torch.empty(half_shape(cfg.ng), dtype=ctype, device=sorted_.device)
+    if ws is None:
+        ws = workspace(cfg, n, ffi.PK_WS_POWER_BINNED, sorted_.device)
+    check(ffi.lib().pk_power_binned(ctypes.byref(cfg.c()), _p(sorted_), _p(wsorted), _p(offsets), n, _p(pk), _p(km), _p(nm),
+                                    _p(delta), _p(ws), ws.numel(), _stream(sorted_.device)))
+    return (pk, km, nm, delta) if return_delta else (pk, km, nm)
+
+
+def bispectrum_ntri(nshells):
+    return int(ffi.lib().pk_bispectrum_ntri(int(nshells)))
+
+
+def triangles(nshells):
+    """Shell triples (s1 >= s2 >= s3, s1 <= s2 + s3 + 1) in the library's order."""
+    return [(a, b, c) for a in range(nshells) for b in range(a + 1) for c in range(b + 1) if a <= b + c + 1]
+
+
+def bispectrum_counts(cfg, shell_lo, shell_w, nshells, device="cuda"):
+    """Exact N_tri per triangle (int64, device)."""
+    counts = torch.empty(bispectrum_ntri(nshells), dtype=torch.int64, device=device)
+    ws = workspace(cfg, nshells, ffi.PK_WS_BISPECTRUM_COUNTS, device)
+    check(ffi.lib().pk_bispectrum_counts(ctypes.byref(cfg.c()), int(shell_lo), int(shell_w), int(nshells), _p(counts), _p(ws),
+                                         ws.numel(), _stream(torch.device(device))))
+    return counts
+
+
+def bispectrum(delta, cfg, shell_lo, shell_w, nshells, counts=None):
+    """FFT bispectrum per triangle (float64, device); counts from ``bispectrum_counts``."""
+    if counts is None:
+        counts = bispectrum_counts(cfg, shell_lo, shell_w, nshells, delta.device)
+    out = torch.empty(bispectrum_ntri(nshells), dtype=torch.float64, device=delta.device)
+    ws = workspace(cfg, nshells, ffi.PK_WS_BISPECTRUM, delta.device)
+    check(ffi.lib().pk_bispectrum(ctypes.byref(cfg.c()), _p(delta), int(shell_lo), int(shell_w), int(nshells), _p(counts),
+                                  _p(out), _p(ws), ws.numel(), _stream(delta.device)))
+    return out, counts
+
+
+def power_backward(pos, cfg, dl_dpk, weights=None):
+    """dL/dx for dL/dP_b (a8): (n, 3) float32 (fp32) or float64 (fp64, fixed64)."""
+    fmt = _pos_format(pos)
+    n = pos.shape[0]
+    w = _weights(weights, n, pos.device)
+    dl = dl_dpk.to(device=pos.device, dtype=torch.float64).contiguous()
+    out = torch.empty((n, 3), dtype=torch.float32 if cfg.prec == "fp32" else torch.float64, device=pos.device)
+    ws = workspace(cfg, n, ffi.PK_WS_BACKWARD, pos.device)
+    check(ffi.lib().pk_power_backward(ctypes.byref(cfg.c()), _p(pos), fmt, _p(w), n, _p(dl), _p(out), _p(ws), ws.numel(),
+                                      _stream(pos.device)))
+    return out
+
+
+def batch_workspace(cfg, batch, max_group_particles, device):
+    size = ffi.lib().pk_batch_workspace_size(ctypes.byref(cfg.c()), int(batch), int(max_group_particles))
+    if size == 0:
+        raise ffi.PkError(ffi.PK_EINVAL, ffi.last_error())
+    return torch.empty(size, dtype=torch.uint8, device=device)
+
+
+def max_group_particles(offsets, batch):
+    offs = [int(v) for v in offsets]
+    return max(offs[min(g + batch, len(offs) - 1)] - offs[g] for g in range(0, len(offs) - 1, batch))
+
+
+def batch_power(cells, offsets, cfg, batch=64, ws=None, out=None):
+    """P(k) of many catalogues (a9). cells: (n,4) int32 pk_cellpos; offsets: host int64 sequence of
+    n_cat + 1 catalogue boundaries. Returns (pk, nmodes) of shape (n_cat, nbins)."""
+    if _pos_format(cells) != ffi.PK_POS_CELL_F32OFF:
+        raise ValueError("batch_power takes pk_cellpos records")
+    import numpy as np
+
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    ncat = len(offs) - 1
+    if out is None:
+        pk = torch.empty((ncat, cfg.nb), dtype=torch.float64, device=cells.device)
+        nm = torch.empty((ncat, cfg.nb), dtype=torch.int64, device=cells.device)
+    else:
+        pk, nm = out
+    if ws is None:
+        ws = batch_workspace(cfg, batch, max_group_particles(offs, batch), cells.device)
+    check(ffi.lib().pk_batch_power(ctypes.byref(cfg.c()), ncat, offs.ctypes.data_as(ctypes.c_void_p), _p(cells), _p(pk), _p(nm),
+                                   int(batch), _p(ws), ws.numel(), _stream(cells.device)))
+    return pk, nm
+
+
+def device_error(device=None):
+    """Reads and clears the device error word (PK_DERR_* bits) after synchronising the stream."""
+    return int(ffi.lib().pk_device_error(_stream(device)))
+
+
+class PowerSpectrum(torch.autograd.Function):
+    """P(k) (pk_power) with the hand-written adjoint (pk_power_backward) as its backward."""
+
+    @staticmethod
+    def forward(ctx, pos, cfg, weights=None):
+        pk, _, _ = power(pos, cfg, weights)
+        ctx.save_for_backward(pos, weights if weights is not None else torch.empty(0, device=pos.device))
+        ctx.cfg = cfg
+        ctx.has_w = weights is not None
+        return pk
+
+    @staticmethod
+    def backward(ctx, grad_pk):
+        pos, w = ctx.saved_tensors
+        g = power_backward(pos, ctx.cfg, torch.nan_to_num(grad_pk, nan=0.0), w if ctx.has_w else None)
+        return g.to(pos.dtype), None, None
+
+
+def power_spectrum(pos, cfg, weights=None):
+    """Differentiable P(k) of FP64 positions."""
+    return PowerSpectrum.apply(pos, cfg, weights)

@@ -1,0 +1,565 @@
+// C ABI of libpk (include/pk.h): argument validation, workspace layout, the cuFFT plan cache and the
+// host-side sequencing of the kernels of each entry point.
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "host.cuh"
+
+namespace pk {
+
+// ---- errors -------------------------------------------------------------------------------------------
+
+static thread_local std::string t_err;
+
+pk_status fail(pk_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return st;
+}
+
+pk_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(PK_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+void clear_err() { t_err.clear(); }
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches += k; }
+
+// ---- stage timing ---------------------------------------------------------------------------------------
+
+constexpr int kProfMarks = 6;
+static thread_local bool t_prof = false;
+static thread_local cudaEvent_t t_ev[kProfMarks] = {};
+static thread_local bool t_ev_rec[kProfMarks] = {};
+
+void prof_mark(int k, cudaStream_t s) {
+  if (!t_prof || k < 0 || k >= kProfMarks) return;
+  if (!t_ev[k] && cudaEventCreate(&t_ev[k]) != cudaSuccess) return;
+  if (cudaEventRecord(t_ev[k], s) == cudaSuccess) t_ev_rec[k] = true;
+}
+
+int num_sms() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 132;
+  cache[dev] = n;
+  return n;
+}
+
+// ---- validation -----------------------------------------------------------------------------------------
+
+pk_status validate(const pk_config* c) {
+  if (!c) return fail(PK_EINVAL, "cfg is NULL");
+  if (c->ng < 8 || c->ng > 1024 || (c->ng & 1)) return fail(PK_EINVAL, "ng must be even and in [8, 1024] (got %d)", c->ng);
+  if (c->order < 1 || c->order > 4) return fail(PK_EINVAL, "order must be 1..4 (got %d)", c->order);
+  if (c->interlace != 0 && c->interlace != 1) return fail(PK_EINVAL, "interlace must be 0 or 1");
+  if (c->prec < PK_FP64 || c->prec > PK_FIXED64) return fail(PK_EINVAL, "prec must be PK_FP64, PK_FP32 or PK_FIXED64");
+  if (!(c->box > 0.0) || !std::isfinite(c->box)) return fail(PK_EINVAL, "box must be finite and > 0");
+  if (c->bin_lo2 < 0 || c->bin_w2 < 1 || c->nbins < 1 || c->nbins > 2048)
+    return fail(PK_EINVAL, "bins: need bin_lo2 >= 0, bin_w2 >= 1, 1 <= nbins <= 2048");
+  if (int64_t(c->bin_lo2) + int64_t(c->bin_w2) * c->nbins > (int64_t(1) << 30)) return fail(PK_EINVAL, "bin edges too large");
+  if (c->subtract_shot != 0 && c->subtract_shot != 1) return fail(PK_EINVAL, "subtract_shot must be 0 or 1");
+  return PK_OK;
+}
+
+// ---- cuFFT plans ------------------------------------------------------------------------------------------
+
+static std::mutex g_plan_mu;
+static std::map<std::tuple<int, int, int, int>, PlanEntry> g_plans;  // (device, ng, type, batch)
+
+// kind: 0 R2C, 1 D2Z, 2 C2R, 3 Z2D; in-place on the padded layout [ng][ng][ng+2] (reals).
+pk_status get_plan(int ng, int kind, int batch, PlanEntry* out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto key = std::make_tuple(dev, ng, kind, batch);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) {
+    *out = it->second;
+    return PK_OK;
+  }
+  PlanEntry e;
+  cufftHandle h = 0;
+  if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cufftCreate failed");
+  e.h = int(h);
+  if (cufftSetAutoAllocation(h, 0) != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cufftSetAutoAllocation failed");
+  long long n[3] = {ng, ng, ng};
+  long long rem[3] = {ng, ng, ng + 2};
+  long long cem[3] = {ng, ng, ng / 2 + 1};
+  const long long rdist = (long long)ng * ng * (ng + 2), cdist = (long long)ng * ng * (ng / 2 + 1);
+  static const cufftType types[4] = {CUFFT_R2C, CUFFT_D2Z, CUFFT_C2R, CUFFT_Z2D};
+  const bool fwd = kind < 2;
+  size_t work = 0;
+  cufftResult r = cufftMakePlanMany64(h, 3, n, fwd ? rem : cem, 1, fwd ? rdist : cdist, fwd ? cem : rem, 1,
+                                      fwd ? cdist : rdist, types[kind], batch, &work);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(h);
+    return fail(PK_ECUFFT, "cufftMakePlanMany64 failed (%d) for ng=%d kind=%d batch=%d", int(r), ng, kind, batch);
+  }
+  e.work = work;
+  g_plans[key] = e;
+  *out = e;
+  return PK_OK;
+}
+
+pk_status exec_plan(const PlanEntry& p, int kind, void* data, void* work, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (cufftSetStream(p.h, s) != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cufftSetStream failed");
+  if (cufftSetWorkArea(p.h, work) != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cufftSetWorkArea failed");
+  cufftResult r;
+  switch (kind) {
+    case 0: r = cufftExecR2C(p.h, static_cast<cufftReal*>(data), static_cast<cufftComplex*>(data)); break;
+    case 1: r = cufftExecD2Z(p.h, static_cast<cufftDoubleReal*>(data), static_cast<cufftDoubleComplex*>(data)); break;
+    case 2: r = cufftExecC2R(p.h, static_cast<cufftComplex*>(data), static_cast<cufftReal*>(data)); break;
+    default: r = cufftExecZ2D(p.h, static_cast<cufftDoubleComplex*>(data), static_cast<cufftDoubleReal*>(data)); break;
+  }
+  if (r != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cuFFT exec failed (%d)", int(r));
+  return PK_OK;
+}
+
+// ---- shared sequencing ----------------------------------------------------------------------------------
+
+
+pk_status carve_grid_stage(const pk_config* c, Carver& cv, GridStage* g) {
+  const bool dbl = c->prec != PK_FP32;
+  const int ngrid = c->interlace ? 2 : 1;
+  g->kind = dbl ? 1 : 0;
+  g->grids = cv.take<char>(size_t(ngrid) * padded_count(c->ng) * (dbl ? 8 : 4));
+  g->tables = cv.take<char>(estimate_table_bytes(c->ng, dbl));
+  g->wsums = cv.take<double>(3);
+  g->bin_sum = cv.take<double>(c->nbins);
+  g->bin_k = cv.take<double>(c->nbins);
+  g->bin_cnt = cv.take<unsigned long long>(c->nbins);
+  pk_status st = get_plan(c->ng, g->kind, ngrid, &g->plan);
+  if (st != PK_OK) return st;
+  g->fft_work = cv.take<char>(std::max<size_t>(g->plan.work, 256));
+  return PK_OK;
+}
+
+// FFT of the padded grids, then the fused estimate (and optional finalisation into pk outputs).
+pk_status run_fft_estimate(const pk_config* c, GridStage& g, void* delta_out, double* pk_out, double* kmean, int64_t* nmodes,
+                           cudaStream_t s) {
+  prof_mark(3, s);
+  pk_status st = exec_plan(g.plan, g.kind, g.grids, g.fft_work, s);
+  if (st != PK_OK) return st;
+  prof_mark(4, s);
+  const bool dbl = c->prec != PK_FP32;
+  EstimateArgs a;
+  a.ng = c->ng;
+  a.order = c->order;
+  a.interlace = c->interlace;
+  a.nbins = pk_out ? c->nbins : 0;
+  a.bin_lo2 = c->bin_lo2;
+  a.bin_w2 = c->bin_w2;
+  a.box = c->box;
+  a.wsums = g.wsums;
+  a.bin_sum = g.bin_sum;
+  a.bin_k = g.bin_k;
+  a.bin_cnt = g.bin_cnt;
+  a.delta_out = delta_out;
+  cudaError_t e;
+  if (pk_out) {
+    if ((e = cudaMemsetAsync(g.bin_sum, 0, sizeof(double) * c->nbins, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(g.bin_k, 0, sizeof(double) * c->nbins, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(g.bin_cnt, 0, sizeof(unsigned long long) * c->nbins, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  }
+  const size_t gbytes = size_t(padded_count(c->ng)) * (dbl ? 8 : 4);
+  const void* G1 = g.grids;
+  const void* G2 = c->interlace ? static_cast<const char*>(g.grids) + gbytes : nullptr;
+  e = dbl ? launch_estimate<double>(G1, G2, g.tables, a, s) : launch_estimate<float>(G1, G2, g.tables, a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "estimate");
+  if (pk_out) {
+    if ((e = launch_finalize(a, c->subtract_shot, pk_out, kmean, nmodes, s)) != cudaSuccess) return cuda_fail(e, "finalize");
+  }
+  prof_mark(5, s);
+  return PK_OK;
+}
+
+
+void carve_bin_stage(const pk_config* c, int64_t n, bool need_cells, Carver& cv, BinStage* b) {
+  const int nt = tiles_per_axis(c->ng);
+  const int64_t ntiles = int64_t(nt) * nt * nt;
+  b->cells = need_cells ? cv.take<pk_cellpos>(size_t(std::max<int64_t>(n, 1))) : nullptr;
+  b->counts = cv.take<unsigned long long>(size_t(ntiles));
+  b->scan = cv.take<long long>(scan_scratch_bytes(ntiles) / sizeof(long long) + 1);
+}
+
+// Positions in either format -> binned layout (sorted, wsorted, offsets).
+pk_status run_bin(const pk_config* c, const void* pos, int fmt, const float* w, int64_t n, BinStage& b, pk_cellpos* sorted,
+                  float* wsorted, int64_t* offsets, cudaStream_t s) {
+  const pk_cellpos* cells = static_cast<const pk_cellpos*>(pos);
+  cudaError_t e;
+  if (fmt == PK_POS_F64_XYZ) {
+    if ((e = launch_prepare(static_cast<const double*>(pos), n, c->ng, c->box, b.cells, s)) != cudaSuccess)
+      return cuda_fail(e, "prepare");
+    cells = b.cells;
+  }
+  const int nt = tiles_per_axis(c->ng);
+  if ((e = launch_bin(cells, w, n, c->ng, kTileCells, nt, sorted, wsorted, offsets, b.counts, b.scan, s)) != cudaSuccess)
+    return cuda_fail(e, "bin");
+  if (fmt != PK_POS_F64_XYZ) {  // user-supplied packed cells: validate the sorted copy in place
+    if ((e = launch_check_cells(sorted, n, c->ng, s)) != cudaSuccess) return cuda_fail(e, "check cells");
+  }
+  return PK_OK;
+}
+
+pk_status run_weight_sums(const float* w, int64_t n, double* sums, cudaStream_t s) {
+  cudaError_t e = w ? launch_weight_sums(w, n, sums, s) : launch_set_sums(sums, double(n), double(n), s);
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "weight sums");
+}
+
+// Mass assignment into `grids` (two consecutive grids of ng*ng*ldz elements when interlaced):
+// PK_FP64 from positions in any order (direct FP64 atomics); PK_FP32 / PK_FIXED64 from the binned
+// layout (sorted, offsets). wsums (device) holds the weight sums (fixed-point scale).
+pk_status run_assign_into(const pk_config* c, const void* pos, int fmt, const pk_cellpos* sorted, const float* w,
+                          const int64_t* offsets, int64_t n, const double* wsums, void* grids, int ldz, cudaStream_t s) {
+  const bool two = c->interlace != 0;
+  const int64_t per = int64_t(c->ng) * c->ng * ldz;
+  const size_t all = size_t(per) * (two ? 2 : 1);
+  cudaError_t e;
+  if (c->prec == PK_FP64) {
+    double* g1 = static_cast<double*>(grids);
+    if ((e = cudaMemsetAsync(g1, 0, all * 8, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    prof_mark(2, s);
+    e = launch_assign_direct_f64(c->order, pos, fmt, w, n, c->ng, c->box, two, g1, two ? g1 + per : nullptr, ldz, s);
+    if (e != cudaSuccess) return cuda_fail(e, "assign (fp64)");
+  } else if (c->prec == PK_FP32) {
+    float* g1 = static_cast<float*>(grids);
+    if ((e = cudaMemsetAsync(g1, 0, all * 4, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    prof_mark(2, s);
+    e = launch_assign_tile_f32(c->order, sorted, w, offsets, n, c->ng, two, g1, two ? g1 + per : nullptr, ldz, s);
+    if (e != cudaSuccess) return cuda_fail(e, "assign (fp32)");
+  } else {
+    unsigned long long* g1 = static_cast<unsigned long long*>(grids);
+    if ((e = cudaMemsetAsync(g1, 0, all * 8, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    prof_mark(2, s);
+    e = launch_assign_tile_fixed(c->order, sorted, w, offsets, n, c->ng, two, wsums, g1, two ? g1 + per : nullptr, ldz, s);
+    if (e != cudaSuccess) return cuda_fail(e, "assign (fixed)");
+    if ((e = launch_fixed_to_double(g1, int64_t(all), wsums, s)) != cudaSuccess) return cuda_fail(e, "fixed->double");
+  }
+  return PK_OK;
+}
+
+pk_status carve_forward(const pk_config* c, int64_t n, Carver& cv, ForwardStage* f) {
+  pk_status st = carve_grid_stage(c, cv, &f->g);
+  if (st != PK_OK) return st;
+  if (c->prec != PK_FP64) {
+    carve_bin_stage(c, n, true, cv, &f->b);
+    f->sorted = cv.take<pk_cellpos>(size_t(std::max<int64_t>(n, 1)));
+    f->wsorted = cv.take<float>(size_t(std::max<int64_t>(n, 1)));
+    const int nt = tiles_per_axis(c->ng);
+    f->offsets = cv.take<int64_t>(size_t(int64_t(nt) * nt * nt + 1));
+  }
+  return PK_OK;
+}
+
+// Weight sums, binning (FP32/FIXED64) and assignment into the padded grids of f.g (not transformed).
+pk_status run_forward_grids(const pk_config* c, const void* pos, int fmt, const float* w, int64_t n, ForwardStage& f,
+                            cudaStream_t s) {
+  prof_mark(0, s);
+  pk_status st = run_weight_sums(w, n, f.g.wsums, s);
+  if (st != PK_OK) return st;
+  if (c->prec == PK_FP64) {
+    prof_mark(1, s);
+    return run_assign_into(c, pos, fmt, nullptr, w, nullptr, n, f.g.wsums, f.g.grids, c->ng + 2, s);
+  }
+  if ((st = run_bin(c, pos, fmt, w, n, f.b, f.sorted, w ? f.wsorted : nullptr, f.offsets, s)) != PK_OK) return st;
+  prof_mark(1, s);
+  return run_assign_into(c, nullptr, PK_POS_CELL_F32OFF, f.sorted, w ? f.wsorted : nullptr, f.offsets, n, f.g.wsums,
+                         f.g.grids, c->ng + 2, s);
+}
+
+}  // namespace pk
+
+using namespace pk;
+
+// ---- entry points -----------------------------------------------------------------------------------------
+
+extern "C" {
+
+void pk_default_config(pk_config* cfg, int32_t ng, double box) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->ng = ng;
+  cfg->order = 4;
+  cfg->interlace = 1;
+  cfg->prec = PK_FP32;
+  cfg->box = box;
+  cfg->bin_lo2 = 1;
+  cfg->bin_w2 = 2;
+  cfg->nbins = ng / 2;
+  cfg->subtract_shot = 0;
+}
+
+int32_t pk_tiles_per_axis(const pk_config* cfg, int32_t* tile_cells) {
+  if (tile_cells) *tile_cells = kTileCells;
+  if (!cfg || cfg->ng < 1) return 0;
+  return tiles_per_axis(cfg->ng);
+}
+
+const char* pk_last_error(void) { return t_err.c_str(); }
+
+int32_t pk_profile_enable(int32_t on) {
+  const bool was = t_prof;
+  t_prof = on != 0;
+  for (int k = 0; k < kProfMarks; ++k) t_ev_rec[k] = false;
+  return was ? 1 : 0;
+}
+
+int32_t pk_profile_read(double* ms, int32_t max_stages) {
+  int got = 0;
+  for (int k = 0; k + 1 < kProfMarks && got < max_stages; ++k) {
+    float v = 0.0f;
+    if (t_ev_rec[k] && t_ev_rec[k + 1] && cudaEventSynchronize(t_ev[k + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&v, t_ev[k], t_ev[k + 1]) == cudaSuccess)
+      ms[got] = double(v);
+    else
+      ms[got] = -1.0;
+    ++got;
+  }
+  for (int k = 0; k < kProfMarks; ++k) t_ev_rec[k] = false;
+  return got;
+}
+
+int64_t pk_profile_launches(void) { return int64_t(g_launches.load()); }
+
+int32_t pk_device_error(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned v = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  if (take_err_prepare(&v) != 0 || take_err_assign(&v) != 0) return -1;
+  return int32_t(v);
+}
+
+static size_t assign_ws(const pk_config* c, int64_t n) {
+  Carver cv(nullptr);
+  cv.take<double>(3);
+  if (c->prec != PK_FP64) {
+    BinStage b;
+    carve_bin_stage(c, n, true, cv, &b);
+    cv.take<pk_cellpos>(size_t(std::max<int64_t>(n, 1)));
+    cv.take<float>(size_t(std::max<int64_t>(n, 1)));
+    const int nt = tiles_per_axis(c->ng);
+    cv.take<int64_t>(size_t(int64_t(nt) * nt * nt + 1));
+  }
+  return cv.size();
+}
+
+size_t pk_workspace_size(const pk_config* cfg, int64_t n, int32_t kind) {
+  clear_err();
+  if (validate(cfg) != PK_OK) return 0;
+  if (n < 0) {
+    fail(PK_EINVAL, "n < 0");
+    return 0;
+  }
+  Carver cv(nullptr);
+  size_t out = 0;
+  switch (kind) {
+    case PK_WS_ASSIGN:
+      return assign_ws(cfg, n);
+    case PK_WS_FFT_ESTIMATE:
+    case PK_WS_POWER_BINNED: {
+      GridStage g;
+      if (carve_grid_stage(cfg, cv, &g) != PK_OK) return 0;
+      return cv.size();
+    }
+    case PK_WS_POWER: {
+      ForwardStage f;
+      if (carve_forward(cfg, n, cv, &f) != PK_OK) return 0;
+      return cv.size();
+    }
+    case PK_WS_BIN: {
+      BinStage b;
+      carve_bin_stage(cfg, n, true, cv, &b);
+      return cv.size();
+    }
+    case PK_WS_BACKWARD:
+      return backward_ws(cfg, n, &out) == PK_OK ? out : 0;
+    case PK_WS_BISPECTRUM:
+    case PK_WS_BISPECTRUM_COUNTS:
+      if (n < 1 || n > 64) {
+        fail(PK_EINVAL, "nshells must be 1..64");
+        return 0;
+      }
+      return bispectrum_ws(cfg, int(n), kind == PK_WS_BISPECTRUM_COUNTS, &out) == PK_OK ? out : 0;
+    default:
+      fail(PK_EINVAL, "unknown workspace kind %d", kind);
+      return 0;
+  }
+}
+
+pk_status pk_prepare(const pk_config* cfg, const double* pos_dev, int64_t n, pk_cellpos* out_dev, void* stream) {
+  clear_err();
+  pk_status st = validate(cfg);
+  if (st != PK_OK) return st;
+  if (n < 0 || (n > 0 && (!pos_dev || !out_dev))) return fail(PK_EINVAL, "bad positions/output");
+  cudaError_t e = launch_prepare(pos_dev, n, cfg->ng, cfg->box, out_dev, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PK_OK : cuda_fail(e, "prepare");
+}
+
+pk_status pk_bin(const pk_config* cfg, const void* pos_dev, int32_t pos_format, const float* w_dev, int64_t n,
+                 pk_cellpos* sorted_dev, float* w_sorted_dev, int64_t* tile_offsets_dev, void* ws, size_t ws_bytes,
+                 void* stream) {
+  clear_err();
+  pk_status st = validate(cfg);
+  if (st != PK_OK) return st;
+  if (pos_format != PK_POS_F64_XYZ && pos_format != PK_POS_CELL_F32OFF) return fail(PK_EINVAL, "bad pos_format");
+  if (n < 0 || (n > 0 && (!pos_dev || !sorted_dev)) || !tile_offsets_dev) return fail(PK_EINVAL, "bad pointers");
+  if (w_dev && !w_sorted_dev) return fail(PK_EINVAL, "w_sorted_dev required when w_dev is given");
+  const size_t need = pk_workspace_size(cfg, n, PK_WS_BIN);
+  if (!ws || ws_bytes < need) return fail(PK_ESIZE, "workspace %zu < %zu bytes", ws_bytes, need);
+  Carver cv(ws);
+  BinStage b;
+  carve_bin_stage(cfg, n, true, cv, &b);
+  return run_bin(cfg, pos_dev, pos_format, w_dev, n, b, sorted_dev, w_dev ? w_sorted_dev : nullptr, tile_offsets_dev,
+                 static_cast<cudaStream_t>(stream));
+}
+
+pk_status pk_assign(const pk_config* cfg, const void* pos_dev, int32_t pos_format, const float* w_dev, int64_t n,
+                    void* grid1_dev, void* grid2_dev, void* ws, size_t ws_bytes, void* stream) {
+  clear_err();
+  pk_status st = validate(cfg);
+  if (st != PK_OK) return st;
+  if (pos_format != PK_POS_F64_XYZ && pos_format != PK_POS_CELL_F32OFF) return fail(PK_EINVAL, "bad pos_format");
+  if (n < 0 || (n > 0 && !pos_dev) || !grid1_dev) return fail(PK_EINVAL, "bad pointers");
+  const size_t need = pk_workspace_size(cfg, n, PK_WS_ASSIGN);
+  if (!ws || ws_bytes < need) return fail(PK_ESIZE, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pk_config c = *cfg;
+  if (!grid2_dev) c.interlace = 0;
+  const int64_t per = int64_t(c.ng) * c.ng * c.ng;
+  const size_t esz = c.prec == PK_FP32 ? 4 : 8;
+  Carver cv(ws);
+  double* sums = cv.take<double>(3);
+  if ((st = run_weight_sums(w_dev, n, sums, s)) != PK_OK) return st;
+  cudaError_t e = cudaMemsetAsync(grid1_dev, 0, size_t(per) * esz, s);
+  if (e == cudaSuccess && c.interlace) e = cudaMemsetAsync(grid2_dev, 0, size_t(per) * esz, s);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  if (c.prec == PK_FP64) {
+    e = launch_assign_direct_f64(c.order, pos_dev, pos_format, w_dev, n, c.ng, c.box, c.interlace != 0,
+                                 static_cast<double*>(grid1_dev), static_cast<double*>(c.interlace ? grid2_dev : nullptr),
+                                 c.ng, s);
+    return e == cudaSuccess ? PK_OK : cuda_fail(e, "assign (fp64)");
+  }
+  BinStage b;
+  carve_bin_stage(&c, n, true, cv, &b);
+  pk_cellpos* sorted = cv.take<pk_cellpos>(size_t(std::max<int64_t>(n, 1)));
+  float* wsorted = cv.take<float>(size_t(std::max<int64_t>(n, 1)));
+  const int nt = tiles_per_axis(c.ng);
+  int64_t* offsets = cv.take<int64_t>(size_t(int64_t(nt) * nt * nt + 1));
+  if ((st = run_bin(&c, pos_dev, pos_format, w_dev, n, b, sorted, w_dev ? wsorted : nullptr, offsets, s)) != PK_OK) return st;
+  const float* ws_w = w_dev ? wsorted : nullptr;
+  if (c.prec == PK_FP32) {
+    e = launch_assign_tile_f32(c.order, sorted, ws_w, offsets, n, c.ng, c.interlace != 0, static_cast<float*>(grid1_dev),
+                               static_cast<float*>(c.interlace ? grid2_dev : nullptr), c.ng, s);
+    return e == cudaSuccess ? PK_OK : cuda_fail(e, "assign (fp32)");
+  }
+  // PK_FIXED64: integer sums in the 8-byte output arrays, converted to double in place.
+  unsigned long long* g1 = static_cast<unsigned long long*>(grid1_dev);
+  unsigned long long* g2 = static_cast<unsigned long long*>(c.interlace ? grid2_dev : nullptr);
+  e = launch_assign_tile_fixed(c.order, sorted, ws_w, offsets, n, c.ng, c.interlace != 0, sums, g1, g2, c.ng, s);
+  if (e != cudaSuccess) return cuda_fail(e, "assign (fixed)");
+  if ((e = launch_fixed_to_double(g1, per, sums, s)) != cudaSuccess) return cuda_fail(e, "fixed->double");
+  if (g2 && (e = launch_fixed_to_double(g2, per, sums, s)) != cudaSuccess) return cuda_fail(e, "fixed->double");
+  return PK_OK;
+}
+
+pk_status pk_fft_estimate(const pk_config* cfg, const void* grid1_dev, const void* grid2_dev, double wsum, void* delta_k_dev,
+                          void* ws, size_t ws_bytes, void* stream) {
+  clear_err();
+  pk_status st = validate(cfg);
+  if (st != PK_OK) return st;
+  if (!grid1_dev || !delta_k_dev || (cfg->interlace && !grid2_dev)) return fail(PK_EINVAL, "bad pointers");
+  if (!(wsum > 0.0) || !std::isfinite(wsum)) return fail(PK_EINVAL, "wsum must be finite and > 0");
+  const size_t need = pk_workspace_size(cfg, 0, PK_WS_FFT_ESTIMATE);
+  if (!ws || ws_bytes < need) return fail(PK_ESIZE, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  GridStage g;
+  if ((st = carve_grid_stage(cfg, cv, &g)) != PK_OK) return st;
+  const bool dbl = cfg->prec != PK_FP32;
+  const int64_t rows = int64_t(cfg->ng) * cfg->ng;
+  const int64_t per = padded_count(cfg->ng);
+  cudaError_t e;
+  if (dbl) {
+    double* d = static_cast<double*>(g.grids);
+    e = launch_copy_rows<double>(static_cast<const double*>(grid1_dev), cfg->ng, d, cfg->ng + 2, cfg->ng, rows, s);
+    if (e == cudaSuccess && cfg->interlace)
+      e = launch_copy_rows<double>(static_cast<const double*>(grid2_dev), cfg->ng, d + per, cfg->ng + 2, cfg->ng, rows, s);
+  } else {
+    float* d = static_cast<float*>(g.grids);
+    e = launch_copy_rows<float>(static_cast<const float*>(grid1_dev), cfg->ng, d, cfg->ng + 2, cfg->ng, rows, s);
+    if (e == cudaSuccess && cfg->interlace)
+      e = launch_copy_rows<float>(static_cast<const float*>(grid2_dev), cfg->ng, d + per, cfg->ng + 2, cfg->ng, rows, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "copy grids");
+  if ((e = launch_set_sums(g.wsums, wsum, wsum, s)) != cudaSuccess) return cuda_fail(e, "set sums");
+  return run_fft_estimate(cfg, g, delta_k_dev, nullptr, nullptr, nullptr, s);
+}
+
+pk_status pk_power(const pk_config* cfg, const void* pos_dev, int32_t pos_format, const float* w_dev, int64_t n,
+                   double* pk_dev, double* kmean_dev, int64_t* nmodes_dev, void* delta_k_dev, void* ws, size_t ws_bytes,
+                   void* stream) {
+  clear_err();
+  pk_status st = validate(cfg);
+  if (st != PK_OK) return st;
+  if (pos_format != PK_POS_F64_XYZ && pos_format != PK_POS_CELL_F32OFF) return fail(PK_EINVAL, "bad pos_format");
+  if (n < 1 || !pos_dev) return fail(PK_EINVAL, "need at least one particle");
+  if (!pk_dev || !kmean_dev || !nmodes_dev) return fail(PK_EINVAL, "pk, kmean and nmodes outputs are required");
+  const size_t need = pk_workspace_size(cfg, n, PK_WS_POWER);
+  if (!ws || ws_bytes < need) return fail(PK_ESIZE, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  ForwardStage f;
+  if ((st = carve_forward(cfg, n, cv, &f)) != PK_OK) return st;
+  if ((st = run_forward_grids(cfg, pos_dev, pos_format, w_dev, n, f, s)) != PK_OK) return st;
+  return run_fft_estimate(cfg, f.g, delta_k_dev, pk_dev, kmean_dev, nmodes_dev, s);
+}
+
+pk_status pk_power_binned(const pk_config* cfg, const pk_cellpos* sorted_dev, const float* w_sorted_dev,
+                          const int64_t* tile_offsets_dev, int64_t n, double* pk_dev, double* kmean_dev, int64_t* nmodes_dev,
+                          void* delta_k_dev, void* ws, size_t ws_bytes, void* stream) {
+  clear_err();
+  pk_status st = validate(cfg);
+  if (st != PK_OK) return st;
+  if (n < 1 || !sorted_dev || !tile_offsets_dev) return fail(PK_EINVAL, "need at least one particle and tile offsets");
+  if (!pk_dev || !kmean_dev || !nmodes_dev) return fail(PK_EINVAL, "pk, kmean and nmodes outputs are required");
+  const size_t need = pk_workspace_size(cfg, n, PK_WS_POWER_BINNED);
+  if (!ws || ws_bytes < need) return fail(PK_ESIZE, "workspace %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  GridStage g;
+  if ((st = carve_grid_stage(cfg, cv, &g)) != PK_OK) return st;
+  prof_mark(0, s);
+  if ((st = run_weight_sums(w_sorted_dev, n, g.wsums, s)) != PK_OK) return st;
+  prof_mark(1, s);
+  if (cfg->prec == PK_FP64)
+    st = run_assign_into(cfg, sorted_dev, PK_POS_CELL_F32OFF, nullptr, w_sorted_dev, nullptr, n, g.wsums, g.grids, cfg->ng + 2, s);
+  else
+    st = run_assign_into(cfg, nullptr, PK_POS_CELL_F32OFF, sorted_dev, w_sorted_dev, tile_offsets_dev, n, g.wsums, g.grids,
+                         cfg->ng + 2, s);
+  if (st != PK_OK) return st;
+  return run_fft_estimate(cfg, g, delta_k_dev, pk_dev, kmean_dev, nmodes_dev, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+// a5 window deconvolution + interlacing combine + |delta|^2 shell binning, fused in one pass over the
+// half-complex transforms of the two grids; a6 finalisation of P(k).
+//
+// For a stored mode n (slots i_x, i_y, i_z <= N/2) with G_g the DFT of mass grid g:
+//   delta(n)  = [G_1(n) + e^{+i pi (n_x+n_y+n_z)/N} G_2(n)] / (2 sum(w) W(n))       (eq:intdelta, eq:windowcorrection)
+//   W(n)      = prod_i sinc^p(pi n_i/N)                                               (eq:intkerFT)
+// The Hermitian partner -n (not stored when 0 < i_z < N/2) has G_g(-n) = conj G_g(n) but its own
+// phase: on a Nyquist slot (i = N/2, n_i = -N/2) the partner index is again -N/2, so its phase is
+// e^{-i pi/2}, not the conjugate. Both are evaluated from the same loads, so every mode of the full
+// N^3 grid is binned exactly once. P(n) = V |delta(n)|^2 (Sec. 2.2 estimator); bins by the exact
+// integer test e_b^2 <= 4|n|^2 < e_{b+1}^2. Each warp takes one (i_x, i_y) row with lanes along i_z
+// (coalesced loads), reduces runs of equal bins with a shuffle scan and adds the run sums to
+// per-block FP64 shared-memory bins, flushed once per block.
+#include "internal.cuh"
+
+namespace pk {
+
+template <typename R>
+struct C2 {
+  R x, y;
+};
+
+template <typename R>
+__device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ C2<R> conj(C2<R> a) {
+  return {a.x, -a.y};
+}
+
+// Per-slot tables: 1/W_1d(n), cos and sin of pi n/N (n the signed index of the slot).
+template <typename R>
+__global__ void k_tables(R* tab, int ng, int order) {
+  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < ng; i += blockDim.x * gridDim.x) {
+    const int n = signed_mode(i, ng);
+    const double x = 3.14159265358979323846 * double(n) / double(ng);
+    const double s = n == 0 ? 1.0 : sin(x) / x;
+    double w = 1.0;
+    for (int k = 0; k < order; ++k) w *= s;
+    tab[i] = R(1.0 / w);
+    tab[ng + i] = R(cos(x));
+    tab[2 * ng + i] = R(sin(x));
+  }
+}
+
+size_t estimate_table_bytes(int ng, bool dbl) { return size_t(3) * ng * (dbl ? 8 : 4); }
+
+__device__ __forceinline__ int bin_of(long long v4, int lo2, int w2, int nbins) {
+  if (v4 == 0) return -1;
+  const float r = sqrtf(float(v4));
+  int b = int(floorf((r - float(lo2)) / float(w2)));
+  // exact correction with integers
+  if (b < 0) b = 0;
+  long long e = (long long)lo2 + (long long)b * w2;
+  while (b > 0 && e * e > v4) { --b; e -= w2; }
+  if (e * e > v4) return -1;
+  long long e1 = e + w2;
+  while (e1 * e1 <= v4) { ++b; e1 += w2; if (b >= nbins) return -1; }
+  return b < nbins ? b : -1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, const C2<R>* __restrict__ G2,
+                                                  const R* __restrict__ tab_g, EstimateArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  {
+    const int cat = blockIdx.y;
+    G1 += cat * a.cat_stride;
+    if (G2) G2 += cat * a.cat_stride;
+    a.wsums += 3 * cat;
+    a.bin_sum += int64_t(cat) * a.nbins;
+    a.bin_k += int64_t(cat) * a.nbins;
+    a.bin_cnt += int64_t(cat) * a.nbins;
+  }
+  const int ng = a.ng;
+  R* tab = reinterpret_cast<R*>(smem_raw);  // 3 ng
+  double* s_sum = reinterpret_cast<double*>(smem_raw + ((size_t(3) * ng * sizeof(R) + 15) / 16) * 16);
+  double* s_k = s_sum + a.nbins;
+  unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_k + a.nbins);
+  for (int i = threadIdx.x; i < 3 * ng; i += blockDim.x) tab[i] = tab_g[i];
+  for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+    s_sum[i] = 0.0;
+    s_k[i] = 0.0;
+    s_cnt[i] = 0ull;
+  }
+  __syncthreads();
+  const R* winv = tab;
+  const R* pc = tab + ng;
+  const R* ps = tab + 2 * ng;
+  const int lane = threadIdx.x & 31;
+  const int half = ng / 2;
+  const int lz = half + 1;
+  const double vol = a.box * a.box * a.box;
+  const R wsum = R(a.wsums[0]);
+  const R norm = a.interlace ? R(0.5) / wsum : R(1) / wsum;
+  const int64_t rows = int64_t(ng) * ng;
+  const int64_t warp_g = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  C2<R>* dout = static_cast<C2<R>*>(a.delta_out);
+  for (int64_t row = warp_g; row < rows; row += nwarps) {
+    const int ix = int(row / ng), iy = int(row - int64_t(ix) * ng);
+    const int nx = signed_mode(ix, ng), ny = signed_mode(iy, ng);
+    const R wxy = winv[ix] * winv[iy];
+    const C2<R> phx = {pc[ix], ps[ix]}, phy = {pc[iy], ps[iy]};
+    const C2<R> phxy = cmul(phx, phy);
+    // partner phase per axis: conjugate except on the Nyquist slot
+    const C2<R> phxy_p = cmul(ix == half ? phx : conj(phx), iy == half ? phy : conj(phy));
+    const long long nxy2 = (long long)nx * nx + (long long)ny * ny;
+    for (int z0 = 0; z0 < lz; z0 += 32) {
+      const int iz = z0 + lane;
+      const bool live = iz < lz;
+      int b = -1;
+      R val = R(0), ks = R(0);
+      int cnt = 0;
+      if (live) {
+        const int nz = iz == half ? -half : iz;
+        const long long n2 = nxy2 + (long long)nz * nz;
+        const int64_t idx = row * lz + iz;
+        C2<R> d = {R(0), R(0)};
+        if (n2 != 0) {
+          const R c = norm * wxy * winv[iz];
+          const C2<R> g1 = G1[idx];
+          const bool partner = iz > 0 && iz < half;
+          C2<R> dp;
+          if (a.interlace) {
+            const C2<R> g2 = G2[idx];
+            const C2<R> phz = {pc[iz], ps[iz]};
+            const C2<R> t = cmul(cmul(phxy, phz), g2);
+            d = {(g1.x + t.x) * c, (g1.y + t.y) * c};
+            const C2<R> tp = cmul(cmul(phxy_p, conj(phz)), conj(g2));
+            dp = {(g1.x + tp.x) * c, (-g1.y + tp.y) * c};
+          } else {
+            d = {g1.x * c, g1.y * c};
+            dp = conj(d);
+          }
+          b = bin_of(4 * n2, a.bin_lo2, a.bin_w2, a.nbins);
+          if (b >= 0) {
+            val = d.x * d.x + d.y * d.y;
+            cnt = 1;
+            if (partner) {
+              val += dp.x * dp.x + dp.y * dp.y;
+              cnt = 2;
+            }
+            val *= R(vol);
+            ks = R(cnt) * sqrt(R(n2));
+          }
+        }
+        if (dout) dout[idx] = d;
+      }
+      if (a.nbins == 0) continue;
+      // segmented inclusive scan over runs of equal b (each lane adds only within its own run, so a
+      // run's sum never passes through another run's partial sums)
+      const int bprev = __shfl_up_sync(0xffffffffu, b, 1);
+      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || bprev != b);
+      const int start = 31 - __clz(heads & ((2u << lane) - 1u));
+      R sv = val, sk = ks;
+      int sc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const R tv = __shfl_up_sync(0xffffffffu, sv, o);
+        const R tk = __shfl_up_sync(0xffffffffu, sk, o);
+        const int tc = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane - o >= start) {
+          sv += tv;
+          sk += tk;
+          sc += tc;
+        }
+      }
+      const int bnext = __shfl_down_sync(0xffffffffu, b, 1);
+      const bool end = lane == 31 || bnext != b;
+      if (end && b >= 0) {
+        atomicAdd(&s_sum[b], double(sv));
+        atomicAdd(&s_k[b], double(sk));
+        atomicAdd(&s_cnt[b], (unsigned long long)sc);
+      }
+    }
+  }
+  __syncthreads();
+  if (a.nbins == 0) return;
+  for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+    if (s_cnt[i]) {
+      atomicAdd(&a.bin_sum[i], s_sum[i]);
+      atomicAdd(&a.bin_k[i], s_k[i]);
+      atomicAdd(&a.bin_cnt[i], s_cnt[i]);
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_estimate(const void* G1, const void* G2, void* tables, const EstimateArgs& a, cudaStream_t s) {
+  k_tables<R><<<(a.ng + 255) / 256, 256, 0, s>>>(static_cast<R*>(tables), a.ng, a.order); count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = ((size_t(3) * a.ng * sizeof(R) + 15) / 16) * 16 + size_t(a.nbins) * 24;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_estimate<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t rows = int64_t(a.ng) * a.ng;
+  const int bx = int(std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, std::max<int64_t>(1, int64_t(num_sms()) * 8 / a.ncat))));
+  const dim3 blocks(bx, a.ncat);
+  k_estimate<R><<<blocks, 256, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
+                                          static_cast<const R*>(tables), a); count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_estimate<float>(const void*, const void*, void*, const EstimateArgs&, cudaStream_t);
+template cudaError_t launch_estimate<double>(const void*, const void*, void*, const EstimateArgs&, cudaStream_t);
+
+__global__ void k_finalize(EstimateArgs a, int subtract_shot, double* pk, double* kmean, int64_t* nmodes) {
+  {
+    const int cat = blockIdx.y;
+    a.wsums += 3 * cat;
+    a.bin_sum += int64_t(cat) * a.nbins;
+    a.bin_k += int64_t(cat) * a.nbins;
+    a.bin_cnt += int64_t(cat) * a.nbins;
+    pk += int64_t(cat) * a.nbins;
+    if (kmean) kmean += int64_t(cat) * a.nbins;
+    nmodes += int64_t(cat) * a.nbins;
+  }
+  const double kf = 2.0 * 3.14159265358979323846 / a.box;
+  const double vol = a.box * a.box * a.box;
+  const double shot = vol * a.wsums[1] / (a.wsums[0] * a.wsums[0]);
+  for (int b = threadIdx.x + blockIdx.x * blockDim.x; b < a.nbins; b += blockDim.x * gridDim.x) {
+    const unsigned long long m = a.bin_cnt[b];
+    nmodes[b] = int64_t(m);
+    if (m == 0) {
+      pk[b] = __longlong_as_double(0x7ff8000000000000ll);
+      if (kmean) kmean[b] = __longlong_as_double(0x7ff8000000000000ll);
+    } else {
+      pk[b] = a.bin_sum[b] / double(m) - (subtract_shot ? shot : 0.0);
+      if (kmean) kmean[b] = kf * a.bin_k[b] / double(m);
+    }
+  }
+}
+
+cudaError_t launch_finalize(const EstimateArgs& a, int subtract_shot, double* pk, double* kmean, int64_t* nmodes,
+                            cudaStream_t s) {
+  k_finalize<<<dim3((a.nbins + 255) / 256, a.ncat), 256, 0, s>>>(a, subtract_shot, pk, kmean, nmodes); count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace pk

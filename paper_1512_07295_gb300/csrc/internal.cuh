@@ -1,0 +1,81 @@
+// Host-side declarations shared by the translation units of libpk.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace pk {
+
+int num_sms();  // SM count of the current device (cached per device)
+void count_launch(int k = 1);  // number of kernels this library launched (pk_profile_launches)
+
+// Per-translation-unit device error words (see PK_ERR_ACCESSOR): OR into *acc and clear.
+int take_err_prepare(unsigned* acc);
+int take_err_assign(unsigned* acc);
+
+// Tile edge (cells) of the binned layout for a grid of side ng, and tiles per axis.
+constexpr int kTileCells = 8;
+inline int tiles_per_axis(int ng) { return (ng + kTileCells - 1) / kTileCells; }
+
+// prepare.cu
+cudaError_t launch_prepare(const double* pos, int64_t n, int ng, double box, pk_cellpos* out, cudaStream_t s);
+cudaError_t launch_check_cells(pk_cellpos* p, int64_t n, int ng, cudaStream_t s);
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t launch_exclusive_scan(const unsigned long long* in, int64_t n, int64_t* out, long long* scratch, cudaStream_t s);
+cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int tcells, int ntile, pk_cellpos* sorted,
+                       float* wsorted, int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s);
+
+constexpr int kMaxBatch = 128;
+struct CatRanges {  // particle ranges of the catalogues of one batch group (absolute indices)
+  int64_t off[kMaxBatch + 1];
+  int nb;
+  int ng;
+};
+cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, int tcells, int ntile, pk_cellpos* sorted,
+                             int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s);
+
+// assign.cu -- grid layout: node (x, y, z) at element (x * ng + y) * ldz + z of each grid.
+cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
+                                     bool interlace, double* g1, double* g2, int ldz, cudaStream_t s);
+cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                   bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
+// Batch: ncat catalogues (unit weights, interlaced), catalogue c's tile offsets at toff + c * ntiles and
+// its two grids at grids + c * 2 * ng*ng*ldz.
+cudaError_t launch_assign_tile_batch(int order, const pk_cellpos* p, const int64_t* toff, int64_t n, int ng, int ncat,
+                                     float* grids, int ldz, cudaStream_t s);
+// PK_FIXED64: the scale 2^F is derived on the device from wsums[2] = sum |w|.
+cudaError_t launch_assign_tile_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n,
+                                     int ng, bool interlace, const double* wsums, unsigned long long* g1,
+                                     unsigned long long* g2, int ldz, cudaStream_t s);
+cudaError_t launch_fixed_to_double(unsigned long long* g, int64_t count, const double* wsums, cudaStream_t s);
+// wsums (3 doubles): [sum w, sum w^2, sum |w|]
+cudaError_t launch_weight_sums(const float* w, int64_t n, double* sums, cudaStream_t s);
+cudaError_t launch_set_sums(double* sums, double s1, double s2, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_rows(const T* src, int src_ld, T* dst, int dst_ld, int ng, int64_t rows, cudaStream_t s);
+
+// estimate.cu
+struct EstimateArgs {
+  int ng, order, interlace, nbins, bin_lo2, bin_w2;
+  double box;
+  const double* wsums;  // device: [sum w, sum w^2, sum |w|]
+  double* bin_sum;      // device accumulators (nbins each), zeroed by the caller
+  double* bin_k;
+  unsigned long long* bin_cnt;
+  void* delta_out;      // optional half-complex delta(n)
+  // batches (blockIdx.y = catalogue c): G1, G2 advance by c * cat_stride complex elements, wsums by 3c,
+  // the bin accumulators and outputs by c * nbins
+  int ncat = 1;
+  int64_t cat_stride = 0;
+};
+size_t estimate_table_bytes(int ng, bool dbl);
+template <typename R>
+cudaError_t launch_estimate(const void* G1, const void* G2, void* tables, const EstimateArgs& a, cudaStream_t s);
+cudaError_t launch_finalize(const EstimateArgs& a, int subtract_shot, double* pk, double* kmean, int64_t* nmodes,
+                            cudaStream_t s);
+
+}  // namespace pk

@@ -1,0 +1,277 @@
+// a1 position preparation and a2 counting sort of particles by cell tile.
+//
+// a1 (Sec. 2.3, s = (x_j - x)/H): an FP64 position is wrapped into [0, L) (periodic box) and split
+// into the integer cell c = floor(x/H) and the offset f = x/H - c in [0, 1), stored as FP32.
+// a2: particles are grouped by tile of T^3 cells with a counting sort (histogram, exclusive scan,
+// scatter). Histogram and scatter use warp-aggregated atomics: consecutive particles of a spatially
+// ordered catalogue share a tile, and one atomic per distinct tile per warp replaces 32.
+#include "internal.cuh"
+
+namespace pk {
+
+PK_ERR_ACCESSOR(take_err_prepare)
+
+__device__ __forceinline__ pk_cellpos prepare_one(const double* p, int ng, double box, double scale) {
+  pk_cellpos r;
+  int c[3];
+  float fo[3];
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double x = p[a];
+    if (!isfinite(x)) { bad = true; x = 0.0; }
+    x = fmod(x, box);
+    if (x < 0.0) x += box;
+    const double u = x * scale;
+    double fl = floor(u);
+    int ci = int(fl);
+    double f = u - fl;
+    if (ci >= ng) { ci -= ng; }
+    float ff = float(f);
+    if (ff >= 1.0f) {  // f rounded up to 1 in FP32: the particle sits on the next node
+      ff = 0.0f;
+      ci = ci + 1 == ng ? 0 : ci + 1;
+    }
+    c[a] = ci;
+    fo[a] = ff;
+  }
+  if (bad) {
+    raise_err(PK_DERR_NONFINITE);
+    c[0] = c[1] = c[2] = 0;
+    fo[0] = fo[1] = fo[2] = 0.0f;
+  }
+  r.cell = pack_cell(c[0], c[1], c[2]);
+  r.fx = fo[0];
+  r.fy = fo[1];
+  r.fz = fo[2];
+  return r;
+}
+
+__global__ void k_prepare(const double* __restrict__ pos, int64_t n, int ng, double box, pk_cellpos* __restrict__ out) {
+  const double scale = double(ng) / box;
+  for (int64_t i = gtid(); i < n; i += gstride()) out[i] = prepare_one(pos + 3 * i, ng, box, scale);
+}
+
+__device__ __forceinline__ int tile_key(uint32_t cell, int tcells, int ntile) {
+  const int tx = cell_x(cell) / tcells, ty = cell_y(cell) / tcells, tz = cell_z(cell) / tcells;
+  return (tx * ntile + ty) * ntile + tz;
+}
+
+// Validates a packed particle (coordinates < N, offsets in [0,1)); invalid ones are reported and
+// mapped to cell 0 so that every later index stays in bounds.
+__device__ __forceinline__ pk_cellpos checked(pk_cellpos r, int ng) {
+  const bool ok = cell_x(r.cell) < ng && cell_y(r.cell) < ng && cell_z(r.cell) < ng && (r.cell >> 30) == 0 &&
+                  r.fx >= 0.0f && r.fx < 1.0f && r.fy >= 0.0f && r.fy < 1.0f && r.fz >= 0.0f && r.fz < 1.0f;
+  if (!ok) {
+    raise_err(PK_DERR_CELLRANGE);
+    r.cell = 0;
+    r.fx = r.fy = r.fz = 0.0f;
+  }
+  return r;
+}
+
+__global__ void k_check_cells(pk_cellpos* __restrict__ p, int64_t n, int ng) {
+  for (int64_t i = gtid(); i < n; i += gstride()) p[i] = checked(p[i], ng);
+}
+
+// Warp-aggregated increment of ctr[key]; returns the value this lane would have seen alone.
+__device__ __forceinline__ unsigned long long agg_inc(unsigned long long* ctr, int key, unsigned active) {
+  const unsigned peers = __match_any_sync(active, key);
+  const int leader = __ffs(peers) - 1;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ctr + key, (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void k_tile_hist(const pk_cellpos* __restrict__ p, int64_t n, int tcells, int ntile,
+                            unsigned long long* __restrict__ counts) {
+  const int64_t stride = gstride();
+  const int64_t nround = (n + 31) / 32 * 32;
+  for (int64_t i = gtid(); i < nround; i += stride) {
+    const bool live = i < n;
+    const unsigned active = __ballot_sync(0xffffffffu, live);
+    if (live) agg_inc(counts, tile_key(p[i].cell, tcells, ntile), active);
+  }
+}
+
+__global__ void k_tile_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, int64_t n, int tcells,
+                               int ntile, const int64_t* __restrict__ offsets, unsigned long long* __restrict__ cursor,
+                               pk_cellpos* __restrict__ out, float* __restrict__ wout) {
+  const int64_t stride = gstride();
+  const int64_t nround = (n + 31) / 32 * 32;
+  for (int64_t i = gtid(); i < nround; i += stride) {
+    const bool live = i < n;
+    const unsigned active = __ballot_sync(0xffffffffu, live);
+    if (live) {
+      const pk_cellpos r = p[i];
+      const int key = tile_key(r.cell, tcells, ntile);
+      const int64_t dst = offsets[key] + int64_t(agg_inc(cursor, key, active));
+      out[dst] = r;
+      if (wout) wout[dst] = w[i];
+    }
+  }
+}
+
+// Batched binning: blockIdx.y = catalogue c of the group, particles r.off[c] .. r.off[c+1]-1 of p,
+// key c * ntiles + tile. Sorted output indices count from the group's first particle.
+__global__ void k_tile_hist_batch(const pk_cellpos* __restrict__ p, CatRanges r, int tcells, int ntile,
+                                  unsigned long long* __restrict__ counts) {
+  const int c = blockIdx.y;
+  const int64_t beg = r.off[c], cnt = r.off[c + 1] - beg;
+  const int base = c * ntile * ntile * ntile;
+  const int64_t nround = (cnt + 31) / 32 * 32;
+  for (int64_t k = gtid(); k < nround; k += gstride()) {
+    const bool live = k < cnt;
+    const unsigned active = __ballot_sync(0xffffffffu, live);
+    if (live) agg_inc(counts, base + tile_key(checked(p[beg + k], r.ng).cell, tcells, ntile), active);
+  }
+}
+
+__global__ void k_tile_scatter_batch(const pk_cellpos* __restrict__ p, CatRanges r, int tcells, int ntile,
+                                     const int64_t* __restrict__ offsets, unsigned long long* __restrict__ cursor,
+                                     pk_cellpos* __restrict__ out) {
+  const int c = blockIdx.y;
+  const int64_t beg = r.off[c], cnt = r.off[c + 1] - beg;
+  const int base = c * ntile * ntile * ntile;
+  const int64_t nround = (cnt + 31) / 32 * 32;
+  for (int64_t k = gtid(); k < nround; k += gstride()) {
+    const bool live = k < cnt;
+    const unsigned active = __ballot_sync(0xffffffffu, live);
+    if (live) {
+      const pk_cellpos rec = checked(p[beg + k], r.ng);
+      const int key = base + tile_key(rec.cell, tcells, ntile);
+      out[offsets[key] + int64_t(agg_inc(cursor, key, active))] = rec;
+    }
+  }
+}
+
+// Exclusive scan of int64 counts, three phases over blocks of kScanBlock elements.
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long* total) {
+  __shared__ long long warp_sums[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    long long s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    if (lane < nw) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const long long before = wid > 0 ? warp_sums[wid - 1] : 0;
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void k_scan_blocks(const unsigned long long* __restrict__ in, int64_t n, long long* __restrict__ block_sums) {
+  const int64_t i = int64_t(blockIdx.x) * kScanBlock + threadIdx.x;
+  long long v = i < n ? (long long)in[i] : 0;
+  long long tot;
+  block_exclusive_scan(v, &tot);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(long long* __restrict__ block_sums, int nblocks) {
+  // one block: sequential chunks of kScanBlock
+  long long carry = 0;
+  for (int base = 0; base < nblocks; base += kScanBlock) {
+    const int i = base + threadIdx.x;
+    const long long v = i < nblocks ? block_sums[i] : 0;
+    long long tot;
+    const long long ex = block_exclusive_scan(v, &tot);
+    if (i < nblocks) block_sums[i] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_apply(const unsigned long long* __restrict__ in, int64_t n, const long long* __restrict__ block_sums,
+                             int64_t* __restrict__ out, int64_t total_slot) {
+  const int64_t i = int64_t(blockIdx.x) * kScanBlock + threadIdx.x;
+  const long long v = i < n ? (long long)in[i] : 0;
+  const long long ex = block_exclusive_scan(v, nullptr);
+  if (i < n) out[i] = block_sums[blockIdx.x] + ex;
+  if (i == n - 1) out[total_slot] = block_sums[blockIdx.x] + ex + v;
+}
+
+// ---- host launchers -----------------------------------------------------------------------------
+
+cudaError_t launch_prepare(const double* pos, int64_t n, int ng, double box, pk_cellpos* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, int64_t(num_sms()) * 16);
+  k_prepare<<<int(blocks), threads, 0, s>>>(pos, n, ng, box, out); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_cells(pk_cellpos* p, int64_t n, int ng, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, int64_t(num_sms()) * 16);
+  k_check_cells<<<int(blocks), threads, 0, s>>>(p, n, ng); count_launch();
+  return cudaGetLastError();
+}
+
+size_t scan_scratch_bytes(int64_t n) { return size_t((n + kScanBlock - 1) / kScanBlock) * sizeof(long long); }
+
+cudaError_t launch_exclusive_scan(const unsigned long long* in, int64_t n, int64_t* out, long long* scratch, cudaStream_t s) {
+  const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  k_scan_blocks<<<int(nb), kScanBlock, 0, s>>>(in, n, scratch); count_launch();
+  k_scan_sums<<<1, kScanBlock, 0, s>>>(scratch, int(nb)); count_launch();
+  k_scan_apply<<<int(nb), kScanBlock, 0, s>>>(in, n, scratch, out, n); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int tcells, int ntile, pk_cellpos* sorted,
+                       float* wsorted, int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s) {
+  const int64_t ntiles = int64_t(ntile) * ntile * ntile;
+  cudaError_t e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, int64_t(num_sms()) * 16));
+  if (n > 0) {
+    k_tile_hist<<<int(blocks), threads, 0, s>>>(cells, n, tcells, ntile, counts); count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = launch_exclusive_scan(counts, ntiles, offsets, scan_scratch, s)) != cudaSuccess) return e;
+  if (n > 0) {
+    if ((e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    k_tile_scatter<<<int(blocks), threads, 0, s>>>(cells, w, n, tcells, ntile, offsets, counts, sorted, wsorted); count_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, int tcells, int ntile, pk_cellpos* sorted,
+                             int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s) {
+  const int64_t ntiles = int64_t(ntile) * ntile * ntile * r.nb;
+  cudaError_t e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  int64_t maxc = 1;
+  for (int c = 0; c < r.nb; ++c) maxc = std::max<int64_t>(maxc, r.off[c + 1] - r.off[c]);
+  const dim3 blocks(unsigned(std::max<int64_t>(1, std::min<int64_t>((maxc + 255) / 256, std::max(1, num_sms() * 16 / r.nb)))),
+                    unsigned(r.nb));
+  (void)ng;
+  k_tile_hist_batch<<<blocks, 256, 0, s>>>(p, r, tcells, ntile, counts); count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_exclusive_scan(counts, ntiles, offsets, scan_scratch, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  k_tile_scatter_batch<<<blocks, 256, 0, s>>>(p, r, tcells, ntile, offsets, counts, sorted); count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace pk
