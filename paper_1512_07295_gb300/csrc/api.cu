@@ -150,6 +150,7 @@ pk_status carve_grid_stage(const pk_config* c, Carver& cv, GridStage* g) {
   g->bin_sum = cv.take<double>(c->nbins);
   g->bin_k = cv.take<double>(c->nbins);
   g->bin_cnt = cv.take<unsigned long long>(c->nbins);
+  g->bin_aux = cv.take<double>(c->nbins);
   pk_status st = get_plan(c->ng, g->kind, ngrid, &g->plan);
   if (st != PK_OK) return st;
   g->fft_work = cv.take<char>(std::max<size_t>(g->plan.work, 256));
@@ -177,6 +178,8 @@ pk_status run_fft_estimate(const pk_config* c, GridStage& g, void* delta_out, do
   a.bin_k = g.bin_k;
   a.bin_cnt = g.bin_cnt;
   a.delta_out = delta_out;
+  a.det_pass = c->prec == PK_FIXED64 ? 1 : 0;
+  a.det_scale = g.bin_aux;
   cudaError_t e;
   if (pk_out) {
     if ((e = cudaMemsetAsync(g.bin_sum, 0, sizeof(double) * c->nbins, s)) != cudaSuccess) return cuda_fail(e, "memset");

@@ -149,46 +149,126 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
         if (dout) dout[idx] = d;
       }
       if (a.nbins == 0) continue;
-      // segmented inclusive scan over runs of equal b (each lane adds only within its own run, so a
-      // run's sum never passes through another run's partial sums)
+      // segmented inclusive scan over runs of equal b (each lane combines only within its own run, so
+      // a run's result never passes through another run's partial sums)
       const int bprev = __shfl_up_sync(0xffffffffu, b, 1);
       const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || bprev != b);
       const int start = 31 - __clz(heads & ((2u << lane) - 1u));
-      R sv = val, sk = ks;
-      int sc = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const R tv = __shfl_up_sync(0xffffffffu, sv, o);
-        const R tk = __shfl_up_sync(0xffffffffu, sk, o);
-        const int tc = __shfl_up_sync(0xffffffffu, sc, o);
-        if (lane - o >= start) {
-          sv += tv;
-          sk += tk;
-          sc += tc;
-        }
-      }
       const int bnext = __shfl_down_sync(0xffffffffu, b, 1);
       const bool end = lane == 31 || bnext != b;
-      if (end && b >= 0) {
-        atomicAdd(&s_sum[b], double(sv));
-        atomicAdd(&s_k[b], double(sk));
-        atomicAdd(&s_cnt[b], (unsigned long long)sc);
+      if (a.det_pass == 0) {
+        R sv = val, sk = ks;
+        int sc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const R tv = __shfl_up_sync(0xffffffffu, sv, o);
+          const R tk = __shfl_up_sync(0xffffffffu, sk, o);
+          const int tc = __shfl_up_sync(0xffffffffu, sc, o);
+          if (lane - o >= start) {
+            sv += tv;
+            sk += tk;
+            sc += tc;
+          }
+        }
+        if (end && b >= 0) {
+          atomicAdd(&s_sum[b], double(sv));
+          atomicAdd(&s_k[b], double(sk));
+          atomicAdd(&s_cnt[b], (unsigned long long)sc);
+        }
+      } else if (a.det_pass == 1) {  // deterministic mode, pass 1: per-bin maximum and mode count
+        double sv = double(val);
+        int sc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const double tv = __shfl_up_sync(0xffffffffu, sv, o);
+          const int tc = __shfl_up_sync(0xffffffffu, sc, o);
+          if (lane - o >= start) {
+            sv = fmax(sv, tv);
+            sc += tc;
+          }
+        }
+        if (end && b >= 0) {
+          atomicMax(reinterpret_cast<unsigned long long*>(&s_sum[b]), (unsigned long long)__double_as_longlong(sv));
+          atomicAdd(&s_cnt[b], (unsigned long long)sc);
+        }
+      } else {  // pass 2: exact int64 sums of the values quantised at the bin's scale, and of |n| at 2^20
+        long long q = b >= 0 ? llrint(double(val) * a.det_scale[b]) : 0ll;
+        long long kq = b >= 0 ? llrint(double(ks) * 1048576.0) : 0ll;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long tq = __shfl_up_sync(0xffffffffu, q, o);
+          const long long tk = __shfl_up_sync(0xffffffffu, kq, o);
+          if (lane - o >= start) {
+            q += tq;
+            kq += tk;
+          }
+        }
+        if (end && b >= 0) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&s_sum[b]), (unsigned long long)q);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&s_k[b]), (unsigned long long)kq);
+        }
       }
     }
   }
   __syncthreads();
   if (a.nbins == 0) return;
   for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
-    if (s_cnt[i]) {
-      atomicAdd(&a.bin_sum[i], s_sum[i]);
-      atomicAdd(&a.bin_k[i], s_k[i]);
-      atomicAdd(&a.bin_cnt[i], s_cnt[i]);
+    if (a.det_pass == 0) {
+      if (s_cnt[i]) {
+        atomicAdd(&a.bin_sum[i], s_sum[i]);
+        atomicAdd(&a.bin_k[i], s_k[i]);
+        atomicAdd(&a.bin_cnt[i], s_cnt[i]);
+      }
+    } else if (a.det_pass == 1) {
+      if (s_cnt[i]) {
+        atomicMax(reinterpret_cast<unsigned long long*>(&a.bin_sum[i]), (unsigned long long)__double_as_longlong(s_sum[i]));
+        atomicAdd(&a.bin_cnt[i], s_cnt[i]);
+      }
+    } else {
+      const unsigned long long v = __double_as_longlong(s_sum[i]), k = __double_as_longlong(s_k[i]);
+      if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&a.bin_sum[i]), v);
+      if (k) atomicAdd(reinterpret_cast<unsigned long long*>(&a.bin_k[i]), k);
     }
   }
 }
 
+// Deterministic mode, between the passes: scale_b = 2^F_b with F_b = 62 - ceil(log2(max_b M_b)), so
+// that the int64 sum of a bin's quantised values cannot overflow; then clears the sum accumulators.
+__global__ void k_det_scale(EstimateArgs a) {
+  for (int b = threadIdx.x + blockIdx.x * blockDim.x; b < a.nbins; b += blockDim.x * gridDim.x) {
+    const double mx = __longlong_as_double((long long)reinterpret_cast<unsigned long long*>(a.bin_sum)[b]);
+    const double m = double(a.bin_cnt[b]);
+    int f = 0;
+    if (mx > 0.0 && m > 0.0) f = 62 - int(ceil(log2(mx * m)));
+    a.det_scale[b] = ldexp(1.0, f);
+    a.bin_sum[b] = 0.0;
+    a.bin_k[b] = 0.0;
+  }
+}
+
+template <typename R>
+cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, const EstimateArgs& a, cudaStream_t s);
+
 template <typename R>
 cudaError_t launch_estimate(const void* G1, const void* G2, void* tables, const EstimateArgs& a, cudaStream_t s) {
+  if (a.det_pass == 0 || a.nbins == 0) {
+    EstimateArgs b = a;
+    b.det_pass = 0;
+    return launch_estimate_pass<R>(G1, G2, tables, b, s);
+  }
+  EstimateArgs b = a;
+  b.det_pass = 1;
+  cudaError_t e = launch_estimate_pass<R>(G1, G2, tables, b, s);
+  if (e != cudaSuccess) return e;
+  k_det_scale<<<dim3((a.nbins + 255) / 256, a.ncat), 256, 0, s>>>(b); count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  b.det_pass = 2;
+  b.delta_out = nullptr;
+  return launch_estimate_pass<R>(G1, G2, tables, b, s);
+}
+
+template <typename R>
+cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, const EstimateArgs& a, cudaStream_t s) {
   k_tables<R><<<(a.ng + 255) / 256, 256, 0, s>>>(static_cast<R*>(tables), a.ng, a.order); count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -228,8 +308,13 @@ __global__ void k_finalize(EstimateArgs a, int subtract_shot, double* pk, double
       pk[b] = __longlong_as_double(0x7ff8000000000000ll);
       if (kmean) kmean[b] = __longlong_as_double(0x7ff8000000000000ll);
     } else {
-      pk[b] = a.bin_sum[b] / double(m) - (subtract_shot ? shot : 0.0);
-      if (kmean) kmean[b] = kf * a.bin_k[b] / double(m);
+      double sum = a.bin_sum[b], ksum = a.bin_k[b];
+      if (a.det_pass) {  // exact integer sums of the deterministic mode
+        sum = double((long long)reinterpret_cast<const unsigned long long*>(a.bin_sum)[b]) / a.det_scale[b];
+        ksum = double((long long)reinterpret_cast<const unsigned long long*>(a.bin_k)[b]) / 1048576.0;
+      }
+      pk[b] = sum / double(m) - (subtract_shot ? shot : 0.0);
+      if (kmean) kmean[b] = kf * ksum / double(m);
     }
   }
 }

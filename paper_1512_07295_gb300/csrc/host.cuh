@@ -49,6 +49,7 @@ struct GridStage {
   double* bin_sum = nullptr;
   double* bin_k = nullptr;
   unsigned long long* bin_cnt = nullptr;
+  double* bin_aux = nullptr;  // per-bin fixed-point scales of the deterministic mode
   void* fft_work = nullptr;
   PlanEntry plan;
   int kind = 0;

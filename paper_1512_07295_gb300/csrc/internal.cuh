@@ -71,6 +71,10 @@ struct EstimateArgs {
   // the bin accumulators and outputs by c * nbins
   int ncat = 1;
   int64_t cat_stride = 0;
+  // deterministic mode (PK_FIXED64): 1 = the two-pass exact int64 bin sums are used; det_scale
+  // (nbins doubles, device) holds the per-bin fixed-point scales between the passes
+  int det_pass = 0;
+  double* det_scale = nullptr;
 };
 size_t estimate_table_bytes(int ng, bool dbl);
 template <typename R>
