@@ -43,6 +43,11 @@ cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const 
                                      bool interlace, double* g1, double* g2, int ldz, cudaStream_t s);
 cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
+// FP32 column-walk assignment (assign_walk.cu), same layout and binned input as the tiled kernel;
+// ncat > 1: catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids g + c * cat_stride.
+cudaError_t launch_assign_walk_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                   bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
+                                   int64_t cat_stride = 0);
 // Batch: ncat catalogues (unit weights, interlaced), catalogue c's tile offsets at toff + c * ntiles and
 // its two grids at grids + c * 2 * ng*ng*ldz.
 cudaError_t launch_assign_tile_batch(int order, const pk_cellpos* p, const int64_t* toff, int64_t n, int ng, int ncat,
