@@ -3,15 +3,17 @@
 // The scatter is FP32-FMA bound: a particle adds p^3 products to each grid. Accumulating them one by
 // one in shared memory (k_assign_tile) serialises on shared atomics; here the products are summed in
 // registers and only completed planes leave the thread:
-//  - one block per tile of T^3 cells (particles binned by tile, pk_bin), staged in shared memory in
-//    chunks and sorted there by "key cell" (a counting sort): the key cell is the cell whose fixed
-//    stencil (nodes key + S0 .. key + S0 + p - 1 on each axis) covers the particle on that grid;
-//    key = cell + delta with delta in {0, 1}, so each grid has (T+1)^2 key columns of T+1 key cells;
-//  - one thread per (grid, key column) walks its column in x with a window of p x p x p register
-//    accumulators (planes key+S0 .. key+S0+p-1); after each x step the oldest plane is complete and
-//    is added (16 shared atomics for PCS) to a shared-memory region of (T+4)^3 nodes per grid;
+//  - one block per tile of T^3 cells (particles binned by tile, pk_bin), staged in shared memory
+//    (whole tile when it fits, else in chunks) and sorted there by "key cell" with a counting sort;
+//    the key cell is the cell whose fixed stencil (nodes key + S0 .. key + S0 + p - 1 per axis)
+//    covers the particle on that grid, key = cell + delta, delta in {0, 1}, so each grid has
+//    (T+1)^2 key columns of T+1 key cells;
+//  - warps 0-2 walk grid 1's key columns, warps 3-5 grid 2's, one column per thread, in x, with a
+//    window of p x p x p register accumulators (planes key+S0 .. key+S0+p-1); after each x step
+//    the oldest plane is complete and is added to a shared-memory region of (T+4)^3 nodes per grid;
 //  - after the tile, the region is added to the grid in global memory.
-// Per particle and grid: p weights per axis, p^2 products w_y w_z and p^3 FMAs, all in registers.
+// Per particle and grid: p weights per axis, p^2 products w_x w_y and p^3 multiply-adds, issued as
+// packed two-lane FP32 FMAs (fma.rn.f32x2) along z for PCS and CIC.
 #include "internal.cuh"
 
 namespace pk {
@@ -24,8 +26,25 @@ constexpr int NCOL = K * K;    // key columns per grid
 constexpr int NKEY = K * K * K;
 constexpr int RS = T + 4;  // region edge (nodes -1 .. T+2)
 constexpr int RVOL = RS * RS * RS;
-constexpr int CHUNK = 2048;  // particles staged per pass
-constexpr int THREADS = 192;
+constexpr int THREADS = 192;  // 6 warps
+constexpr int WPG = 96;       // walker slots per grid (3 warps, 81 used)
+constexpr int NWARP = THREADS / 32;
+constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
+
+template <bool W>
+__host__ __device__ constexpr int chunk() {
+  return W ? 2048 : 4096;
+}
+
+template <bool W>
+struct Smem {
+  int4 sp[chunk<W>()];
+  unsigned short perm[2][chunk<W>()];
+  int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
+  float reg[2][RVOL];
+  int scan[2][NWARP];
+  float sw[W ? chunk<W>() : 1];
+};
 
 // Stencil start relative to the key cell: PCS and TSC start one node below it.
 template <int P>
@@ -51,13 +70,16 @@ __device__ __forceinline__ int key_delta(float f, float* t) {
   }
 }
 
-// Grid g's key delta and offset for in-cell offset f (grid 2 samples the particle shifted by H/2).
-template <int P>
-__device__ __forceinline__ int grid_key(int g, float f, float* t) {
-  if (g == 0) return key_delta<P>(f, t);
-  float f2;
-  const int d2 = half_shift(f, &f2);
-  return d2 + key_delta<P>(f2, t);
+// Grid G's key delta and offset for in-cell offset f (grid 2 samples the particle shifted by H/2).
+template <int P, int G>
+__device__ __forceinline__ int grid_key(float f, float* t) {
+  if constexpr (G == 0) {
+    return key_delta<P>(f, t);
+  } else {
+    float f2;
+    const int d2 = half_shift(f, &f2);
+    return d2 + key_delta<P>(f2, t);
+  }
 }
 
 // Weights of the p stencil nodes from the offset t (PCS returned times 6: the 1/216 of the three
@@ -90,23 +112,187 @@ __host__ __device__ constexpr float weight_scale() {
   return P == 4 ? 1.0f / 216.0f : 1.0f;
 }
 
-struct Smem {
-  int4 sp[CHUNK];
-  unsigned short rank[2][CHUNK];
-  unsigned short perm[2][CHUNK];
-  int hist[2][NKEY + 1];
-  float reg[2][RVOL];
-  float sw[CHUNK];  // staged weights (only when weights are given)
+// Packed pairs of FP32 values in one 64-bit register (PTX .f32x2 arithmetic, sm_100 family).
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pack2(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(f2x v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ void fma2(f2x& d, f2x a, f2x b) { asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b)); }
+
+// Register window of one walker: plane a (x node key+S0+a) x row b (y) x column c (z).
+// Even p: z pairs packed in 64-bit registers; odd p: scalars.
+template <int P, bool PACK = (P % 2 == 0)>
+struct Window;
+
+template <int P>
+struct Window<P, true> {
+  f2x v[P][P][P / 2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b)
+#pragma unroll
+        for (int h = 0; h < P / 2; ++h) v[a][b][h] = 0ull;
+  }
+  __device__ __forceinline__ void add(const float* wx, const float* wy, const float* wz) {
+    f2x z2[P / 2];
+#pragma unroll
+    for (int h = 0; h < P / 2; ++h) z2[h] = pack2(wz[2 * h], wz[2 * h + 1]);
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      const f2x xa = pack2(wx[a], wx[a]);
+#pragma unroll
+      for (int b = 0; b < P; ++b) {
+        const f2x xy = mul2(xa, pack2(wy[b], wy[b]));
+#pragma unroll
+        for (int h = 0; h < P / 2; ++h) fma2(v[a][b][h], xy, z2[h]);
+      }
+    }
+  }
+  // add plane a to the region at (rx, ry0 + b, rz0 + c)
+  __device__ __forceinline__ void flush(int a, float* reg, int rx, int ry0, int rz0) const {
+#pragma unroll
+    for (int b = 0; b < P; ++b)
+#pragma unroll
+      for (int h = 0; h < P / 2; ++h) {
+        const float2 q = unpack2(v[a][b][h]);
+        float* dst = reg + (rx * walk::RS + ry0 + b) * walk::RS + rz0 + 2 * h;
+        atomicAdd(dst, q.x);
+        atomicAdd(dst + 1, q.y);
+      }
+  }
+  __device__ __forceinline__ void shift() {
+#pragma unroll
+    for (int a = 0; a + 1 < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b)
+#pragma unroll
+        for (int h = 0; h < P / 2; ++h) v[a][b][h] = v[a + 1][b][h];
+#pragma unroll
+    for (int b = 0; b < P; ++b)
+#pragma unroll
+      for (int h = 0; h < P / 2; ++h) v[P - 1][b][h] = 0ull;
+  }
 };
+
+template <int P>
+struct Window<P, false> {
+  float v[P][P][P];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b)
+#pragma unroll
+        for (int c = 0; c < P; ++c) v[a][b][c] = 0.0f;
+  }
+  __device__ __forceinline__ void add(const float* wx, const float* wy, const float* wz) {
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b) {
+        const float xy = wx[a] * wy[b];
+#pragma unroll
+        for (int c = 0; c < P; ++c) v[a][b][c] = fmaf(xy, wz[c], v[a][b][c]);
+      }
+  }
+  __device__ __forceinline__ void flush(int a, float* reg, int rx, int ry0, int rz0) const {
+#pragma unroll
+    for (int b = 0; b < P; ++b)
+#pragma unroll
+      for (int c = 0; c < P; ++c) atomicAdd(reg + (rx * walk::RS + ry0 + b) * walk::RS + rz0 + c, v[a][b][c]);
+  }
+  __device__ __forceinline__ void shift() {
+#pragma unroll
+    for (int a = 0; a + 1 < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b)
+#pragma unroll
+        for (int c = 0; c < P; ++c) v[a][b][c] = v[a + 1][b][c];
+#pragma unroll
+    for (int b = 0; b < P; ++b)
+#pragma unroll
+      for (int c = 0; c < P; ++c) v[P - 1][b][c] = 0.0f;
+  }
+};
+
+// One walker: key column col of grid G over x = 0..K-1; bucket (col, x) holds the particles
+// perm[hist[key-1] .. hist[key]) after the scatter (hist = bucket ends).
+template <int P, int G, bool W>
+__device__ __forceinline__ void walk_column(Smem<W>& S, int col) {
+  const int* ends = S.hist[G];
+  const int kbase = col * K;
+  const int cbeg = kbase == 0 ? 0 : ends[kbase - 1];
+  if (cbeg == ends[kbase + K - 1]) return;  // empty column
+  const int ky = col / K, kz = col - ky * K;
+  const int ry0 = ky + s0<P>() + 1, rz0 = kz + s0<P>() + 1;  // region row/col of stencil offset 0
+  float* reg = S.reg[G];
+  const unsigned short* perm = S.perm[G];
+  Window<P> win;
+  win.zero();
+  int jb = cbeg;
+#pragma unroll
+  for (int x = 0; x < K; ++x) {
+    const int je = ends[kbase + x];
+    int4 rn = make_int4(0, 0, 0, 0);
+    float wn = 1.0f;
+    if (jb < je) {
+      const int i = perm[jb];
+      rn = S.sp[i];
+      if (W) wn = S.sw[i];
+    }
+    for (int j = jb; j < je; ++j) {
+      const int4 r = rn;
+      const float wgt = wn * weight_scale<P>();
+      if (j + 1 < je) {  // prefetch the next particle of the bucket
+        const int i = perm[j + 1];
+        rn = S.sp[i];
+        if (W) wn = S.sw[i];
+      }
+      float tx, ty, tz;
+      grid_key<P, G>(__int_as_float(r.y), &tx);
+      grid_key<P, G>(__int_as_float(r.z), &ty);
+      grid_key<P, G>(__int_as_float(r.w), &tz);
+      float wx[P], wy[P], wz[P];
+      weights<P>(tx, wx);
+      weights<P>(ty, wy);
+      weights<P>(tz, wz);
+#pragma unroll
+      for (int a = 0; a < P; ++a) wx[a] *= wgt;
+      win.add(wx, wy, wz);
+    }
+    jb = je;
+    // node plane x + s0 is complete: add it to the region and shift the window
+    win.flush(0, reg, x + s0<P>() + 1, ry0, rz0);
+    win.shift();
+  }
+  // the remaining planes K + s0 .. K + s0 + P - 2
+#pragma unroll
+  for (int a = 0; a + 1 < P; ++a) win.flush(a, reg, K + a + s0<P>() + 1, ry0, rz0);
+}
 
 }  // namespace walk
 
-template <int P>
-__global__ void __launch_bounds__(walk::THREADS) k_assign_walk(const pk_cellpos* __restrict__ p, const float* __restrict__ w,
-                                                               const int64_t* __restrict__ toff, int64_t n, int ng, int ntile,
-                                                               int interlace, float* __restrict__ g1, float* __restrict__ g2,
-                                                               int ldz, int64_t cat_stride) {
+template <int P, bool W>
+__global__ void __launch_bounds__(walk::THREADS, 2)
+    k_assign_walk(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
+                  int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
+                  int64_t cat_stride) {
   using namespace walk;
+  constexpr int CH = chunk<W>();
   {  // blockIdx.y selects a catalogue of a batch: its grids and its tile offsets
     const int cat = blockIdx.y;
     g1 += cat * cat_stride;
@@ -114,153 +300,106 @@ __global__ void __launch_bounds__(walk::THREADS) k_assign_walk(const pk_cellpos*
     toff += int64_t(cat) * ntile * ntile * ntile;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  Smem<W>& S = *reinterpret_cast<Smem<W>*>(smem_raw);
   const int ngrid = interlace ? 2 : 1;
   const int ntiles = ntile * ntile * ntile;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
     if (beg >= end) continue;
     const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
     for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0.0f;
-    for (int64_t c0 = beg; c0 < end; c0 += CHUNK) {
-      const int m = int(min(int64_t(CHUNK), end - c0));
-      for (int i = tid; i < ngrid * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
+    for (int64_t c0 = beg; c0 < end; c0 += CH) {
+      const int m = int(min(int64_t(CH), end - c0));
+      for (int i = tid; i < 2 * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
       __syncthreads();
-      // stage the chunk and histogram the key cells of both grids
+      // stage the chunk and count the key cells of both grids
       for (int i = tid; i < m; i += THREADS) {
         const int4 r = reinterpret_cast<const int4*>(p)[c0 + i];
         S.sp[i] = r;
-        if (w) S.sw[i] = w[c0 + i];
+        if (W) S.sw[i] = w[c0 + i];
         const uint32_t cell = uint32_t(r.x);
         const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        const float f[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-        const bool ok = lx >= 0 && lx < T && ly >= 0 && ly < T && lz >= 0 && lz < T;
-        if (!ok) raise_err(PK_DERR_CELLRANGE);
-        for (int g = 0; g < ngrid; ++g) {
-          unsigned short rk = 0xffff;
-          if (ok) {
-            float t;
-            const int dx = grid_key<P>(g, f[0], &t), dy = grid_key<P>(g, f[1], &t), dz = grid_key<P>(g, f[2], &t);
-            const int key = ((ly + dy) * K + (lz + dz)) * K + (lx + dx);
-            rk = (unsigned short)atomicAdd(&S.hist[g][key], 1);
-          }
-          S.rank[g][i] = rk;
+        if ((cell >> 30) == 0 && lx >= 0 && lx < T && ly >= 0 && ly < T && lz >= 0 && lz < T) {
+          float t;
+          const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
+          atomicAdd(&S.hist[0][((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K +
+                               (lx + grid_key<P, 0>(fx, &t))], 1);
+          if (interlace)
+            atomicAdd(&S.hist[1][((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K +
+                                 (lx + grid_key<P, 1>(fx, &t))], 1);
+        } else {
+          raise_err(PK_DERR_CELLRANGE);
+          S.sp[i].x = -1;  // marks the particle as skipped
         }
       }
       __syncthreads();
-      // exclusive scan of each grid's key histogram (one warp per grid); hist[g][NKEY] becomes the total
+      // block-wide exclusive scan of both histograms (NKEY + 1 entries each)
       {
-        const int warp = tid >> 5, lane = tid & 31;
-        if (warp < ngrid) {
-          int carry = 0;
-          for (int base = 0; base < NKEY + 1; base += 32) {
-            const int idx = base + lane;
-            const int v = idx < NKEY + 1 ? S.hist[warp][idx] : 0;
-            int x = v;
+        int v0[SCAN_PER_THREAD], v1[SCAN_PER_THREAD];
+        int s0v = 0, s1v = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int y = __shfl_up_sync(0xffffffffu, x, o);
-              if (lane >= o) x += y;
-            }
-            if (idx < NKEY + 1) S.hist[warp][idx] = carry + x - v;
-            carry += __shfl_sync(0xffffffffu, x, 31);
+        for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+          const int idx = tid * SCAN_PER_THREAD + k;
+          v0[k] = idx <= NKEY ? S.hist[0][idx] : 0;
+          v1[k] = idx <= NKEY ? S.hist[1][idx] : 0;
+          s0v += v0[k];
+          s1v += v1[k];
+        }
+        int x0 = s0v, x1 = s1v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+          if (lane >= o) {
+            x0 += y0;
+            x1 += y1;
           }
+        }
+        if (lane == 31) {
+          S.scan[0][warp] = x0;
+          S.scan[1][warp] = x1;
+        }
+        __syncthreads();
+        int e0 = x0 - s0v, e1 = x1 - s1v;
+        for (int q = 0; q < warp; ++q) {
+          e0 += S.scan[0][q];
+          e1 += S.scan[1][q];
+        }
+#pragma unroll
+        for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+          const int idx = tid * SCAN_PER_THREAD + k;
+          if (idx <= NKEY) {
+            S.hist[0][idx] = e0;
+            S.hist[1][idx] = e1;
+          }
+          e0 += v0[k];
+          e1 += v1[k];
         }
       }
       __syncthreads();
-      // scatter particle indices into key order
+      // scatter particle indices into key order; hist[key] advances to the bucket's end
       for (int i = tid; i < m; i += THREADS) {
         const int4 r = S.sp[i];
+        if (r.x < 0) continue;
         const uint32_t cell = uint32_t(r.x);
         const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        const float f[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-        for (int g = 0; g < ngrid; ++g) {
-          const unsigned short rk = S.rank[g][i];
-          if (rk == 0xffff) continue;
-          float t;
-          const int dx = grid_key<P>(g, f[0], &t), dy = grid_key<P>(g, f[1], &t), dz = grid_key<P>(g, f[2], &t);
-          const int key = ((ly + dy) * K + (lz + dz)) * K + (lx + dx);
-          S.perm[g][S.hist[g][key] + rk] = (unsigned short)i;
+        float t;
+        const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
+        const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + (lx + grid_key<P, 0>(fx, &t));
+        S.perm[0][atomicAdd(&S.hist[0][k1], 1)] = (unsigned short)i;
+        if (interlace) {
+          const int k2 =
+              ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + (lx + grid_key<P, 1>(fx, &t));
+          S.perm[1][atomicAdd(&S.hist[1][k2], 1)] = (unsigned short)i;
         }
       }
       __syncthreads();
-      // walk: one thread per (grid, key column)
-      if (tid < ngrid * NCOL) {
-        const int g = tid / NCOL, col = tid - g * NCOL;
-        const int ky = col / K, kz = col - ky * K;
-        const int* hist = S.hist[g] + col * K;
-        if (hist[0] != hist[K]) {
-          float acc[P][P][P];
-#pragma unroll
-          for (int a = 0; a < P; ++a)
-#pragma unroll
-            for (int b = 0; b < P; ++b)
-#pragma unroll
-              for (int c = 0; c < P; ++c) acc[a][b][c] = 0.0f;
-          float* reg = S.reg[g];
-          const int ry0 = ky + s0<P>() + 1, rz0 = kz + s0<P>() + 1;  // region row/col of stencil offset 0
-          const unsigned short* perm = S.perm[g];
-#pragma unroll
-          for (int x = 0; x < K; ++x) {
-            const int jb = hist[x], je = hist[x + 1];
-            for (int j = jb; j < je; ++j) {
-              const int i = perm[j];
-              const int4 r = S.sp[i];
-              float tx, ty, tz;
-              grid_key<P>(g, __int_as_float(r.y), &tx);
-              grid_key<P>(g, __int_as_float(r.z), &ty);
-              grid_key<P>(g, __int_as_float(r.w), &tz);
-              float wx[P], wy[P], wz[P];
-              weights<P>(tx, wx);
-              weights<P>(ty, wy);
-              weights<P>(tz, wz);
-              const float wgt = (w ? S.sw[i] : 1.0f) * weight_scale<P>();
-#pragma unroll
-              for (int a = 0; a < P; ++a) wx[a] *= wgt;
-#pragma unroll
-              for (int b = 0; b < P; ++b)
-#pragma unroll
-                for (int c = 0; c < P; ++c) {
-                  const float yz = wy[b] * wz[c];
-#pragma unroll
-                  for (int a = 0; a < P; ++a) acc[a][b][c] = fmaf(wx[a], yz, acc[a][b][c]);
-                }
-            }
-            // node plane x + s0 is complete: add it to the region and shift the window
-            const int rx = x + s0<P>() + 1;
-#pragma unroll
-            for (int b = 0; b < P; ++b)
-#pragma unroll
-              for (int c = 0; c < P; ++c) {
-                const float v = acc[0][b][c];
-                if (v != 0.0f) atomicAdd(&reg[(rx * RS + ry0 + b) * RS + rz0 + c], v);
-              }
-#pragma unroll
-            for (int a = 0; a + 1 < P; ++a)
-#pragma unroll
-              for (int b = 0; b < P; ++b)
-#pragma unroll
-                for (int c = 0; c < P; ++c) acc[a][b][c] = acc[a + 1][b][c];
-#pragma unroll
-            for (int b = 0; b < P; ++b)
-#pragma unroll
-              for (int c = 0; c < P; ++c) acc[P - 1][b][c] = 0.0f;
-          }
-          // the remaining planes K + s0 .. K + s0 + P - 2
-#pragma unroll
-          for (int a = 0; a + 1 < P; ++a) {
-            const int rx = K + a + s0<P>() + 1;
-#pragma unroll
-            for (int b = 0; b < P; ++b)
-#pragma unroll
-              for (int c = 0; c < P; ++c) {
-                const float v = acc[a][b][c];
-                if (v != 0.0f) atomicAdd(&reg[(rx * RS + ry0 + b) * RS + rz0 + c], v);
-              }
-          }
-        }
+      // walk: warps 0-2 grid 1, warps 3-5 grid 2 (warp-uniform grid)
+      if (tid < WPG) {
+        if (tid < NCOL) walk_column<P, 0, W>(S, tid);
+      } else if (interlace && tid - WPG < NCOL) {
+        walk_column<P, 1, W>(S, tid - WPG);
       }
       __syncthreads();
     }
@@ -278,23 +417,29 @@ __global__ void __launch_bounds__(walk::THREADS) k_assign_walk(const pk_cellpos*
   }
 }
 
-template <int P>
-static cudaError_t launch_walk_p(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
-                                 float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
+template <int P, bool W>
+static cudaError_t launch_walk_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
+                                  float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
-  size_t smem = sizeof(walk::Smem);
-  if (!w) smem -= sizeof(float) * walk::CHUNK;  // the weights stage is the last member
-  cudaError_t e = cudaFuncSetAttribute(k_assign_walk<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const size_t smem = sizeof(walk::Smem<W>);
+  cudaError_t e = cudaFuncSetAttribute(k_assign_walk<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assign_walk<P>, walk::THREADS, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assign_walk<P, W>, walk::THREADS, smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
-  k_assign_walk<P><<<blocks, walk::THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, cat_stride);
+  k_assign_walk<P, W><<<blocks, walk::THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, cat_stride);
   count_launch();
   return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_walk_p(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
+                                 float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
+  return w ? launch_walk_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
+           : launch_walk_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
 }
 
 cudaError_t launch_assign_walk_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
