@@ -229,6 +229,20 @@ struct Window<P, false> {
   }
 };
 
+// Stencil weights of one particle on grid G (x weights scaled by the particle weight wgt).
+template <int P, int G>
+__device__ __forceinline__ void particle_weights(const int4 r, float wgt, float* wx, float* wy, float* wz) {
+  float tx, ty, tz;
+  grid_key<P, G>(__int_as_float(r.y), &tx);
+  grid_key<P, G>(__int_as_float(r.z), &ty);
+  grid_key<P, G>(__int_as_float(r.w), &tz);
+  weights<P>(tx, wx);
+  weights<P>(ty, wy);
+  weights<P>(tz, wz);
+#pragma unroll
+  for (int a = 0; a < P; ++a) wx[a] *= wgt;
+}
+
 // One walker: key column col of grid G over x = 0..K-1; bucket (col, x) holds the particles
 // perm[hist[key-1] .. hist[key]) after the scatter (hist = bucket ends).
 template <int P, int G, bool W>
@@ -244,35 +258,25 @@ __device__ __forceinline__ void walk_column(Smem<W>& S, int col) {
   Window<P> win;
   win.zero();
   int jb = cbeg;
-#pragma unroll
+#pragma unroll 1
   for (int x = 0; x < K; ++x) {
     const int je = ends[kbase + x];
-    int4 rn = make_int4(0, 0, 0, 0);
-    float wn = 1.0f;
-    if (jb < je) {
-      const int i = perm[jb];
-      rn = S.sp[i];
-      if (W) wn = S.sw[i];
+    // two particles per iteration: their weight chains overlap with each other's multiply-adds
+    int j = jb;
+    for (; j + 1 < je; j += 2) {
+      const int i0 = perm[j], i1 = perm[j + 1];
+      const int4 r0 = S.sp[i0], r1 = S.sp[i1];
+      float wx0[P], wy0[P], wz0[P], wx1[P], wy1[P], wz1[P];
+      particle_weights<P, G>(r0, (W ? S.sw[i0] : 1.0f) * weight_scale<P>(), wx0, wy0, wz0);
+      particle_weights<P, G>(r1, (W ? S.sw[i1] : 1.0f) * weight_scale<P>(), wx1, wy1, wz1);
+      win.add(wx0, wy0, wz0);
+      win.add(wx1, wy1, wz1);
     }
-    for (int j = jb; j < je; ++j) {
-      const int4 r = rn;
-      const float wgt = wn * weight_scale<P>();
-      if (j + 1 < je) {  // prefetch the next particle of the bucket
-        const int i = perm[j + 1];
-        rn = S.sp[i];
-        if (W) wn = S.sw[i];
-      }
-      float tx, ty, tz;
-      grid_key<P, G>(__int_as_float(r.y), &tx);
-      grid_key<P, G>(__int_as_float(r.z), &ty);
-      grid_key<P, G>(__int_as_float(r.w), &tz);
-      float wx[P], wy[P], wz[P];
-      weights<P>(tx, wx);
-      weights<P>(ty, wy);
-      weights<P>(tz, wz);
-#pragma unroll
-      for (int a = 0; a < P; ++a) wx[a] *= wgt;
-      win.add(wx, wy, wz);
+    if (j < je) {
+      const int i0 = perm[j];
+      float wx0[P], wy0[P], wz0[P];
+      particle_weights<P, G>(S.sp[i0], (W ? S.sw[i0] : 1.0f) * weight_scale<P>(), wx0, wy0, wz0);
+      win.add(wx0, wy0, wz0);
     }
     jb = je;
     // node plane x + s0 is complete: add it to the region and shift the window
