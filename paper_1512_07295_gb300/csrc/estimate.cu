@@ -98,8 +98,35 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
   const int64_t warp_g = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   C2<R>* dout = static_cast<C2<R>*>(a.delta_out);
-  for (int64_t row = warp_g; row < rows; row += nwarps) {
-    const int ix = int(row / ng), iy = int(row - int64_t(ix) * ng);
+  // work items: (row, 32-mode chunk of the row); the next item's loads are issued before the current
+  // item is processed so that two loads per lane are in flight
+  const int nchunk = (lz + 31) / 32;
+  const int items = int(rows) * nchunk;  // <= 1024^2 * 17
+  C2<R> g1n = {R(0), R(0)}, g2n = {R(0), R(0)};
+  if (warp_g < items) {
+    const int row = int(warp_g) / nchunk;
+    const int iz = (int(warp_g) - row * nchunk) * 32 + lane;
+    if (iz < lz) {
+      g1n = G1[int64_t(row) * lz + iz];
+      if (a.interlace) g2n = G2[int64_t(row) * lz + iz];
+    }
+  }
+  for (int item = int(warp_g); item < items; item += int(nwarps)) {
+    const C2<R> g1c = g1n, g2c = g2n;
+    {
+      const int nxt = item + int(nwarps);
+      if (nxt < items) {
+        const int row = nxt / nchunk;
+        const int iz = (nxt - row * nchunk) * 32 + lane;
+        if (iz < lz) {
+          g1n = G1[int64_t(row) * lz + iz];
+          if (a.interlace) g2n = G2[int64_t(row) * lz + iz];
+        }
+      }
+    }
+    const int row = item / nchunk;
+    const int z0 = (item - row * nchunk) * 32;
+    const int ix = row / ng, iy = row - ix * ng;
     const int nx = signed_mode(ix, ng), ny = signed_mode(iy, ng);
     const R wxy = winv[ix] * winv[iy];
     const C2<R> phx = {pc[ix], ps[ix]}, phy = {pc[iy], ps[iy]};
@@ -107,7 +134,7 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
     // partner phase per axis: conjugate except on the Nyquist slot
     const C2<R> phxy_p = cmul(ix == half ? phx : conj(phx), iy == half ? phy : conj(phy));
     const long long nxy2 = (long long)nx * nx + (long long)ny * ny;
-    for (int z0 = 0; z0 < lz; z0 += 32) {
+    {
       const int iz = z0 + lane;
       const bool live = iz < lz;
       int b = -1;
@@ -116,15 +143,15 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
       if (live) {
         const int nz = iz == half ? -half : iz;
         const long long n2 = nxy2 + (long long)nz * nz;
-        const int64_t idx = row * lz + iz;
+        const int64_t idx = int64_t(row) * lz + iz;
         C2<R> d = {R(0), R(0)};
         if (n2 != 0) {
           const R c = norm * wxy * winv[iz];
-          const C2<R> g1 = G1[idx];
+          const C2<R> g1 = g1c;
           const bool partner = iz > 0 && iz < half;
           C2<R> dp;
           if (a.interlace) {
-            const C2<R> g2 = G2[idx];
+            const C2<R> g2 = g2c;
             const C2<R> phz = {pc[iz], ps[iz]};
             const C2<R> t = cmul(cmul(phxy, phz), g2);
             d = {(g1.x + t.x) * c, (g1.y + t.y) * c};
