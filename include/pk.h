@@ -209,6 +209,26 @@ pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* off
                          const pk_cellpos* pos_dev, double* pk_dev, int64_t* nmodes_dev, int32_t batch,
                          void* ws, size_t ws_bytes, void* stream);
 
+/* No-allocation variant of the fused estimate (a5+a6), for callers that cannot allocate device
+ * memory or pass a workspace: code running inside a framework that owns all device memory and
+ * forbids allocation while its kernels run (plugins, custom operators of a graph runtime), services
+ * with a fixed pre-reserved memory budget, host callbacks that must not enter the allocator. The
+ * paper has no counterpart; this is a deployment variant of the same computation as the estimate
+ * stage of pk_power.
+ * Inputs: g1_dev / g2_dev, the DFTs of the two mass grids (as written by any forward real-to-complex
+ * 3-D FFT of the pk_assign grids, unnormalised, sign -i) on the half-complex layout [N][N][N/2+1]
+ * (complex float for PK_FP32, complex double otherwise; g2 ignored without interlacing); wsum and
+ * w2sum, the sums of the weights and of their squares. Outputs as pk_power (pk_dev, kmean_dev,
+ * nmodes_dev, nbins entries each).
+ * Scratch: a fixed file-scope device array of about 56 KB in the library (held by every GPU that
+ * loads the library until the process exits); N above 1024 or nbins above 1024 is rejected with
+ * PK_ESIZE. The first call on a device looks up that array's device address (with the device
+ * current), so make the first call on each device before any stream capture. All calls share the
+ * array: calls that overlap on the GPU (other streams, other host threads) race and give wrong
+ * results; serialise them. Nothing is allocated. */
+pk_status pk_estimate_noalloc(const pk_config* cfg, const void* g1_dev, const void* g2_dev, double wsum, double w2sum,
+                              double* pk_dev, double* kmean_dev, int64_t* nmodes_dev, void* stream);
+
 /* Stage timing for profiling (not part of the method). pk_profile_enable(1) makes the following
  * pk_power / pk_power_binned / pk_power_backward calls on this host thread record CUDA events on
  * their stream at the stage boundaries; pk_profile_read waits for the last recorded event and writes

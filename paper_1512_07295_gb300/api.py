@@ -248,6 +248,15 @@ def batch_power(cells, offsets, cfg, batch=64, ws=None, out=None):
     return pk, nm
 
 
+def estimate_noalloc(g1_hat, g2_hat, cfg, wsum, w2sum):
+    """P(k) from the transforms of the two mass grids without any device allocation by the library
+    (pk_estimate_noalloc). g*_hat: (ng, ng, ng/2+1) complex tensors. Returns (pk, kmean, nmodes)."""
+    pk, km, nm = _outputs(cfg, g1_hat.device)
+    check(ffi.lib().pk_estimate_noalloc(ctypes.byref(cfg.c()), _p(g1_hat), _p(g2_hat), float(wsum), float(w2sum), _p(pk),
+                                        _p(km), _p(nm), _stream(g1_hat.device)))
+    return pk, km, nm
+
+
 def device_error(device=None):
     """Reads and clears the device error word (PK_DERR_* bits) after synchronising the stream."""
     return int(ffi.lib().pk_device_error(_stream(device)))

@@ -57,6 +57,7 @@ SIGNATURES = {
                                     c_void_p]),
     "pk_batch_power": (c_int32, [_CFG, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_size_t,
                                  c_void_p]),
+    "pk_estimate_noalloc": (c_int32, [_CFG, c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pk_profile_enable": (c_int32, [c_int32]),
     "pk_profile_read": (c_int32, [c_void_p, c_int32]),
     "pk_profile_launches": (c_int64, []),
