@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--box", type=float, default=2000.0)
     ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -230,11 +232,15 @@ def main():
     launches0 = lib.pk_profile_launches()
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.profile_range:
+        torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(a.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    if a.profile_range:
+        torch.cuda.profiler.stop()
     launches = lib.pk_profile_launches() - launches0
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
