@@ -136,6 +136,100 @@ def oracle_sample_rate(pos_sample, n_full, box, ng, with_fft=True):
                              "t_full_extrapolated_s": t_full}
 
 
+def _time_cuda(fn, reps, warm=1):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_rows(dev, host64, big_box):
+    """Times the other hot-path rows on their own workloads (one GB300)."""
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs, ffi
+
+    rows = {}
+    # a7: FFT bispectrum, 16 shells of width 4 k_f (up to k_N/2) on N_G = 256, delta of the large catalogue
+    cfg = api.Config(ng=256, box=big_box, prec="fp32")
+    n = host64.shape[0]
+    dpos = host64.to(dev)
+    _, _, _, delta = api.power(dpos, cfg, return_delta=True)
+    del dpos
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    counts = api.bispectrum_counts(cfg, 0, 4, 16, dev)
+    torch.cuda.synchronize()
+    t_counts = time.perf_counter() - t0
+    ws = api.workspace(cfg, 16, ffi.PK_WS_BISPECTRUM, dev)
+    out = torch.empty(api.bispectrum_ntri(16), dtype=torch.float64, device=dev)
+
+    def bisp():
+        check = ffi.lib().pk_bispectrum(api.ctypes.byref(cfg.c()), api._p(delta), 0, 4, 16, api._p(counts), api._p(out),
+                                        api._p(ws), ws.numel(), api._stream(dev))
+        ffi.check(check)
+
+    ms = _time_cuda(bisp, 5)
+    rows["bispectrum"] = {"workload": f"delta of the {n}-particle catalogue on N_G=256, 16 shells of 4 k_f, 508 triangles",
+                          "ms_per_call": ms, "bispectra_per_s": 1e3 / ms, "triangles": int(out.numel()),
+                          "counts_once_s": t_counts}
+    del ws, delta, counts, out
+    torch.cuda.empty_cache()
+    # a8: adjoint, 128^3 Zel'dovich particles, L = 500, N_G = 128, PCS + interlacing, FP32
+    cfg = api.Config(ng=128, box=500.0, prec="fp32")
+    pos = catalogs.zeldovich_torch(128, 500.0, 4.0, seed=6, device=dev)
+    dl = torch.randn(cfg.nb, dtype=torch.float64, device=dev)
+    wsb = api.workspace(cfg, pos.shape[0], ffi.PK_WS_BACKWARD, dev)
+    g = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=dev)
+
+    def back():
+        ffi.check(ffi.lib().pk_power_backward(api.ctypes.byref(cfg.c()), api._p(pos), ffi.PK_POS_F64_XYZ, None, pos.shape[0],
+                                              api._p(dl), api._p(g), api._p(wsb), wsb.numel(), api._stream(dev)))
+
+    ms = _time_cuda(back, 10, 2)
+    rows["adjoint"] = {"workload": "dL/dx of P(k), 128^3 ZA particles, L=500, N_G=128, PCS+interlacing, FP32 (forward grids "
+                                   "recomputed inside)", "ms_per_call": ms, "particles_per_s": pos.shape[0] / (ms * 1e-3)}
+    del wsb, g, pos
+    torch.cuda.empty_cache()
+    # a9: 512 mock catalogues, N_P log-uniform in [1e5, 2e6], L = 1000, N_G = 128, PCS + interlacing, FP32
+    cfg = api.Config(ng=128, box=1000.0, prec="fp32")
+    sizes = catalogs.batch_sizes(512, 1e5, 2e6, seed=4)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    parts = []
+    for i, m in enumerate(sizes):
+        m = int(m)
+        if i % 2 == 0:
+            p64 = torch.rand((m, 3), generator=gen, device=dev, dtype=torch.float64) * 1000.0
+        else:
+            side = int(np.ceil(m ** (1.0 / 3.0)))
+            p64 = catalogs.zeldovich_torch(side, 1000.0, 4.0, seed=1000 + i, device=dev)[:m].contiguous()
+        parts.append(api.prepare(p64, cfg))
+        del p64
+    cells = torch.cat(parts)
+    del parts
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    batch = 128
+    wsc = api.batch_workspace(cfg, batch, api.max_group_particles(offs, batch), dev)
+    pkb = torch.empty((512, cfg.nb), dtype=torch.float64, device=dev)
+    nmb = torch.empty((512, cfg.nb), dtype=torch.int64, device=dev)
+    ms = _time_cuda(lambda: api.batch_power(cells, offs, cfg, batch=batch, ws=wsc, out=(pkb, nmb)), 3)
+    rows["batch"] = {"workload": f"512 catalogues, {int(sizes.sum())} particles, N_P log-uniform in [1e5, 2e6], L=1000, "
+                                 f"N_G=128, PCS+interlacing, FP32, groups of {batch}",
+                     "ms_per_call": ms, "pk_per_s": 512 / (ms * 1e-3), "particles_per_s": float(sizes.sum()) / (ms * 1e-3)}
+    del wsc, cells
+    torch.cuda.empty_cache()
+    return rows
+
+
 def run_reference(a):
     """The reference arm: the FP64 CPU oracle, one bounded sample of the workload per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -348,6 +442,7 @@ def main():
         sample = host64[torch.from_numpy(idx)].numpy()
         rate, det = oracle_sample_rate(sample, n, a.box, a.ng, with_fft=True)
         cores = len(os.sched_getaffinity(0))
+        result["rows"] = measure_rows(dev, host64, a.box)
         result["cpu_baseline"] = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
                                   "sample": f"2^16 random particles of the catalogue assigned to both grids (single-threaded "
                                             f"NumPy) + one full N_G={a.ng} FFT (scipy, {cores} workers), deconvolution and "
