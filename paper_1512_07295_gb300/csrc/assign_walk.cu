@@ -43,8 +43,16 @@ struct Smem {
   int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
   float reg[2][RVOL];
   int scan[2][NWARP];
+  unsigned long long mbar;  // completion barrier of the bulk copy that stages a chunk
   float sw[W ? chunk<W>() : 1];
 };
+
+// Walker lanes: each grid has three warps; warp-in-grid q holds key rows ky = 3q .. 3q+2, lane
+// 9 r + kz for row r and key column kz (lanes 27..31 hold no column). Neighbouring key columns of a
+// row are neighbouring lanes, so a completed plane is summed along z with shuffles before it is
+// added to shared memory.
+constexpr int ROWS_PER_WARP = 3;
+static_assert(K * ROWS_PER_WARP <= 32 && ROWS_PER_WARP * 3 == K, "three warps of three key rows per grid");
 
 // Stencil start relative to the key cell: PCS and TSC start one node below it.
 template <int P>
@@ -174,6 +182,14 @@ struct Window<P, true> {
         atomicAdd(dst + 1, q.y);
       }
   }
+  __device__ __forceinline__ void row(int a, int b, float* out) const {
+#pragma unroll
+    for (int h = 0; h < P / 2; ++h) {
+      const float2 q = unpack2(v[a][b][h]);
+      out[2 * h] = q.x;
+      out[2 * h + 1] = q.y;
+    }
+  }
   __device__ __forceinline__ void shift() {
 #pragma unroll
     for (int a = 0; a + 1 < P; ++a)
@@ -215,6 +231,10 @@ struct Window<P, false> {
 #pragma unroll
       for (int c = 0; c < P; ++c) atomicAdd(reg + (rx * walk::RS + ry0 + b) * walk::RS + rz0 + c, v[a][b][c]);
   }
+  __device__ __forceinline__ void row(int a, int b, float* out) const {
+#pragma unroll
+    for (int c = 0; c < P; ++c) out[c] = v[a][b][c];
+  }
   __device__ __forceinline__ void shift() {
 #pragma unroll
     for (int a = 0; a + 1 < P; ++a)
@@ -243,24 +263,53 @@ __device__ __forceinline__ void particle_weights(const int4 r, float wgt, float*
   for (int a = 0; a < P; ++a) wx[a] *= wgt;
 }
 
-// One walker: key column col of grid G over x = 0..K-1; bucket (col, x) holds the particles
-// perm[hist[key-1] .. hist[key]) after the scatter (hist = bucket ends).
+// Plane a of every lane's window, summed over the key columns of each row with shuffles: node z of
+// the row receives column kz's offset c = z - kz - S0 for kz = z - S0 - c; the lane of column kz
+// collects the sum for node kz + S0 and adds it to the region; nodes past the row's last column are
+// added by the columns that reach them.
+template <int P>
+__device__ __forceinline__ void flush_plane(const Window<P>& win, int a, float* reg, int rx, int ry0, int kz, bool valid) {
+#pragma unroll
+  for (int b = 0; b < P; ++b) {
+    float v[P];
+    win.row(a, b, v);
+    float sum = v[0];
+#pragma unroll
+    for (int d = 1; d < P; ++d) {
+      const float t = __shfl_up_sync(0xffffffffu, v[d], d);
+      if (kz >= d) sum += t;
+    }
+    if (valid) {
+      float* r = reg + (rx * RS + ry0 + b) * RS + kz + s0<P>() + 1;
+      atomicAdd(r, sum);
+#pragma unroll
+      for (int c = 1; c < P; ++c)
+        if (kz + c >= K) atomicAdd(r + c, v[c]);
+    }
+  }
+}
+
+// One warp of walkers of grid G (warp-in-grid q): lane -> key column (ky, kz); each walks its column
+// in x with a register window; bucket (col, x) holds perm[hist[key-1] .. hist[key]) after the
+// scatter (hist = bucket ends). All 32 lanes run the x loop together (the flush shuffles).
 template <int P, int G, bool W>
-__device__ __forceinline__ void walk_column(Smem<W>& S, int col) {
+__device__ __forceinline__ void walk_warp(Smem<W>& S, int q, int lane) {
   const int* ends = S.hist[G];
-  const int kbase = col * K;
-  const int cbeg = kbase == 0 ? 0 : ends[kbase - 1];
-  if (cbeg == ends[kbase + K - 1]) return;  // empty column
-  const int ky = col / K, kz = col - ky * K;
-  const int ry0 = ky + s0<P>() + 1, rz0 = kz + s0<P>() + 1;  // region row/col of stencil offset 0
+  const int r = lane / K, kz = lane - r * K;
+  const bool valid = r < ROWS_PER_WARP;
+  const int ky = ROWS_PER_WARP * q + (valid ? r : 0);
+  const int kbase = (ky * K + kz) * K;
+  int jb = valid ? (kbase == 0 ? 0 : ends[kbase - 1]) : 0;
+  const int cend = valid ? ends[kbase + K - 1] : 0;
+  if (__all_sync(0xffffffffu, jb == cend)) return;  // every column of the warp is empty
+  const int ry0 = ky + s0<P>() + 1;  // region row of stencil offset 0
   float* reg = S.reg[G];
   const unsigned short* perm = S.perm[G];
   Window<P> win;
   win.zero();
-  int jb = cbeg;
 #pragma unroll 1
   for (int x = 0; x < K; ++x) {
-    const int je = ends[kbase + x];
+    const int je = valid ? ends[kbase + x] : 0;
     // two particles per iteration: their weight chains overlap with each other's multiply-adds
     int j = jb;
     for (; j + 1 < je; j += 2) {
@@ -278,14 +327,39 @@ __device__ __forceinline__ void walk_column(Smem<W>& S, int col) {
       particle_weights<P, G>(S.sp[i0], (W ? S.sw[i0] : 1.0f) * weight_scale<P>(), wx0, wy0, wz0);
       win.add(wx0, wy0, wz0);
     }
-    jb = je;
+    if (valid) jb = je;
     // node plane x + s0 is complete: add it to the region and shift the window
-    win.flush(0, reg, x + s0<P>() + 1, ry0, rz0);
+    flush_plane<P>(win, 0, reg, x + s0<P>() + 1, ry0, kz, valid);
     win.shift();
   }
   // the remaining planes K + s0 .. K + s0 + P - 2
 #pragma unroll
-  for (int a = 0; a + 1 < P; ++a) win.flush(a, reg, K + a + s0<P>() + 1, ry0, rz0);
+  for (int a = 0; a + 1 < P; ++a) flush_plane<P>(win, a, reg, K + a + s0<P>() + 1, ry0, kz, valid);
+}
+
+// Bulk copy (TMA) of `bytes` from global to shared memory, completing on the mbarrier at bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(bar));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d), "l"(src),
+               "r"(bytes), "r"(b)
+               : "memory");
+}
+
+// Waits for phase `parity` of the mbarrier, giving up after a bounded number of polls.
+__device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(bar));
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok)
+                 : "r"(b), "r"(parity)
+                 : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 }  // namespace walk
@@ -308,6 +382,12 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
   const int ngrid = interlace ? 2 : 1;
   const int ntiles = ntile * ntile * ntile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  }
+  __syncthreads();
+  unsigned parity = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
     if (beg >= end) continue;
@@ -316,13 +396,23 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
     for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0.0f;
     for (int64_t c0 = beg; c0 < end; c0 += CH) {
       const int m = int(min(int64_t(CH), end - c0));
+      // stage the chunk with one bulk copy (16-byte records, 16-byte aligned)
+      if (tid == 0) bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
+      if (W)
+        for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
       for (int i = tid; i < 2 * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
-      __syncthreads();
-      // stage the chunk and count the key cells of both grids
+      const bool arrived = bulk_wait(&S.mbar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!arrived)) {  // the copy did not complete: report, drain, stop
+        if (tid == 0) {
+          raise_err(PK_DERR_TIMEOUT);
+          bulk_wait(&S.mbar, parity ^ 1u);
+        }
+        return;
+      }
+      // count the key cells of both grids
       for (int i = tid; i < m; i += THREADS) {
-        const int4 r = reinterpret_cast<const int4*>(p)[c0 + i];
-        S.sp[i] = r;
-        if (W) S.sw[i] = w[c0 + i];
+        const int4 r = S.sp[i];
         const uint32_t cell = uint32_t(r.x);
         const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
         if ((cell >> 30) == 0 && lx >= 0 && lx < T && ly >= 0 && ly < T && lz >= 0 && lz < T) {
@@ -400,21 +490,37 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
       }
       __syncthreads();
       // walk: warps 0-2 grid 1, warps 3-5 grid 2 (warp-uniform grid)
-      if (tid < WPG) {
-        if (tid < NCOL) walk_column<P, 0, W>(S, tid);
-      } else if (interlace && tid - WPG < NCOL) {
-        walk_column<P, 1, W>(S, tid - WPG);
-      }
+      if (warp < 3)
+        walk_warp<P, 0, W>(S, warp, lane);
+      else if (interlace)
+        walk_warp<P, 1, W>(S, warp - 3, lane);
       __syncthreads();
     }
-    // add the tile's region (origin: node (cx0-1, cy0-1, cz0-1)) to the grids
-    for (int i = tid; i < ngrid * RVOL; i += THREADS) {
-      const float v = (&S.reg[0][0])[i];
-      if (v != 0.0f) {
-        const int gi = i / RVOL, k = i - gi * RVOL;
-        const int rx = k / (RS * RS), ry = (k / RS) % RS, rz = k % RS;
-        float* gg = gi == 0 ? g1 : g2;
-        atomicAdd(gg + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz + wrap(cz0 - 1 + rz, ng), v);
+    // add the tile's region (origin: node (cx0-1, cy0-1, cz0-1)) to the grids; node pairs whose global
+    // z index is even are added with one 8-byte vector reduction
+    for (int i = tid; i < ngrid * RS * RS * 7; i += THREADS) {
+      const int row = i / 7, item = i - row * 7;
+      const int gi = row / (RS * RS), rr = row - gi * (RS * RS);
+      const int rx = rr / RS, ry = rr - rx * RS;
+      const float* src = &S.reg[gi][(rx * RS + ry) * RS];
+      float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
+      if (item == 0 || item == 6) {
+        const int rz = item == 0 ? 0 : RS - 1;
+        const float v = src[rz];
+        if (v != 0.0f) atomicAdd(gg + wrap(cz0 - 1 + rz, ng), v);
+      } else {
+        const int rz = 2 * item - 1;  // odd: the global z index cz0 - 1 + rz is even
+        const float v0 = src[rz], v1 = src[rz + 1];
+        if (v0 != 0.0f || v1 != 0.0f) {
+          const int z = wrap(cz0 - 1 + rz, ng);
+          float* dst = gg + z;
+          if (z + 1 < ng && (reinterpret_cast<uintptr_t>(dst) & 7u) == 0) {
+            asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(v0), "f"(v1) : "memory");
+          } else {
+            atomicAdd(dst, v0);
+            atomicAdd(gg + wrap(z + 1, ng), v1);
+          }
+        }
       }
     }
     __syncthreads();
