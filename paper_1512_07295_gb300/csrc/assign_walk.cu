@@ -13,7 +13,7 @@
 //    the oldest plane is complete and is added to a shared-memory region of (T+4)^3 nodes per grid;
 //  - after the tile, the region is added to the grid in global memory.
 // Per particle and grid: p weights per axis, p^2 products w_x w_y and p^3 multiply-adds, issued as
-// packed two-lane FP32 FMAs (fma.rn.f32x2) along z for PCS and CIC.
+// packed two-lane FP32 FMAs (fma.rn.f32x2) over pairs of y rows for PCS and CIC.
 #include "internal.cuh"
 
 namespace pk {
@@ -140,67 +140,57 @@ __device__ __forceinline__ f2x mul2(f2x a, f2x b) {
 __device__ __forceinline__ void fma2(f2x& d, f2x a, f2x b) { asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b)); }
 
 // Register window of one walker: plane a (x node key+S0+a) x row b (y) x column c (z).
-// Even p: z pairs packed in 64-bit registers; odd p: scalars.
+// Even p: y pairs packed in 64-bit registers; odd p: scalars.
 template <int P, bool PACK = (P % 2 == 0)>
 struct Window;
 
 template <int P>
 struct Window<P, true> {
-  f2x v[P][P][P / 2];
+  f2x v[P][P / 2][P];  // plane a, y pair (2bp, 2bp+1), z column c
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int a = 0; a < P; ++a)
 #pragma unroll
-      for (int b = 0; b < P; ++b)
+      for (int bp = 0; bp < P / 2; ++bp)
 #pragma unroll
-        for (int h = 0; h < P / 2; ++h) v[a][b][h] = 0ull;
+        for (int c = 0; c < P; ++c) v[a][bp][c] = 0ull;
   }
+  // v[a][bp][c] += (w_x[a] w_y[2bp], w_x[a] w_y[2bp+1]) * w_z[c]: p^2/2 packed products, p^3/2 packed FMAs
   __device__ __forceinline__ void add(const float* wx, const float* wy, const float* wz) {
-    f2x z2[P / 2];
+    f2x y2[P / 2], z2[P];
 #pragma unroll
-    for (int h = 0; h < P / 2; ++h) z2[h] = pack2(wz[2 * h], wz[2 * h + 1]);
+    for (int bp = 0; bp < P / 2; ++bp) y2[bp] = pack2(wy[2 * bp], wy[2 * bp + 1]);
+#pragma unroll
+    for (int c = 0; c < P; ++c) z2[c] = pack2(wz[c], wz[c]);
 #pragma unroll
     for (int a = 0; a < P; ++a) {
       const f2x xa = pack2(wx[a], wx[a]);
 #pragma unroll
-      for (int b = 0; b < P; ++b) {
-        const f2x xy = mul2(xa, pack2(wy[b], wy[b]));
+      for (int bp = 0; bp < P / 2; ++bp) {
+        const f2x xy = mul2(xa, y2[bp]);
 #pragma unroll
-        for (int h = 0; h < P / 2; ++h) fma2(v[a][b][h], xy, z2[h]);
+        for (int c = 0; c < P; ++c) fma2(v[a][bp][c], xy, z2[c]);
       }
     }
   }
-  // add plane a to the region at (rx, ry0 + b, rz0 + c)
-  __device__ __forceinline__ void flush(int a, float* reg, int rx, int ry0, int rz0) const {
-#pragma unroll
-    for (int b = 0; b < P; ++b)
-#pragma unroll
-      for (int h = 0; h < P / 2; ++h) {
-        const float2 q = unpack2(v[a][b][h]);
-        float* dst = reg + (rx * walk::RS + ry0 + b) * walk::RS + rz0 + 2 * h;
-        atomicAdd(dst, q.x);
-        atomicAdd(dst + 1, q.y);
-      }
-  }
   __device__ __forceinline__ void row(int a, int b, float* out) const {
 #pragma unroll
-    for (int h = 0; h < P / 2; ++h) {
-      const float2 q = unpack2(v[a][b][h]);
-      out[2 * h] = q.x;
-      out[2 * h + 1] = q.y;
+    for (int c = 0; c < P; ++c) {
+      const float2 q = unpack2(v[a][b / 2][c]);
+      out[c] = (b & 1) ? q.y : q.x;
     }
   }
   __device__ __forceinline__ void shift() {
 #pragma unroll
     for (int a = 0; a + 1 < P; ++a)
 #pragma unroll
-      for (int b = 0; b < P; ++b)
+      for (int bp = 0; bp < P / 2; ++bp)
 #pragma unroll
-        for (int h = 0; h < P / 2; ++h) v[a][b][h] = v[a + 1][b][h];
+        for (int c = 0; c < P; ++c) v[a][bp][c] = v[a + 1][bp][c];
 #pragma unroll
-    for (int b = 0; b < P; ++b)
+    for (int bp = 0; bp < P / 2; ++bp)
 #pragma unroll
-      for (int h = 0; h < P / 2; ++h) v[P - 1][b][h] = 0ull;
+      for (int c = 0; c < P; ++c) v[P - 1][bp][c] = 0ull;
   }
 };
 
@@ -310,14 +300,35 @@ __device__ __forceinline__ void walk_warp(Smem<W>& S, int q, int lane) {
 #pragma unroll 1
   for (int x = 0; x < K; ++x) {
     const int je = valid ? ends[kbase + x] : 0;
-    // two particles per iteration: their weight chains overlap with each other's multiply-adds
+    // two particles per iteration (their weight chains overlap each other's multiply-adds); the next
+    // pair's records are loaded before the current pair is accumulated
     int j = jb;
-    for (; j + 1 < je; j += 2) {
+    int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
+    float s0w = 1.0f, s1w = 1.0f;
+    if (j + 1 < je) {
       const int i0 = perm[j], i1 = perm[j + 1];
-      const int4 r0 = S.sp[i0], r1 = S.sp[i1];
+      r0 = S.sp[i0];
+      r1 = S.sp[i1];
+      if (W) {
+        s0w = S.sw[i0];
+        s1w = S.sw[i1];
+      }
+    }
+    for (; j + 1 < je; j += 2) {
+      const int4 c0 = r0, c1 = r1;
+      const float c0w = s0w, c1w = s1w;
+      if (j + 3 < je) {
+        const int i0 = perm[j + 2], i1 = perm[j + 3];
+        r0 = S.sp[i0];
+        r1 = S.sp[i1];
+        if (W) {
+          s0w = S.sw[i0];
+          s1w = S.sw[i1];
+        }
+      }
       float wx0[P], wy0[P], wz0[P], wx1[P], wy1[P], wz1[P];
-      particle_weights<P, G>(r0, (W ? S.sw[i0] : 1.0f) * weight_scale<P>(), wx0, wy0, wz0);
-      particle_weights<P, G>(r1, (W ? S.sw[i1] : 1.0f) * weight_scale<P>(), wx1, wy1, wz1);
+      particle_weights<P, G>(c0, c0w * weight_scale<P>(), wx0, wy0, wz0);
+      particle_weights<P, G>(c1, c1w * weight_scale<P>(), wx1, wy1, wz1);
       win.add(wx0, wy0, wz0);
       win.add(wx1, wy1, wz1);
     }
