@@ -139,6 +139,34 @@ __device__ __forceinline__ f2x mul2(f2x a, f2x b) {
 }
 __device__ __forceinline__ void fma2(f2x& d, f2x a, f2x b) { asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b)); }
 
+// Per-particle operands of the window update. Even p: the y weights as P/2 packed pairs and the x
+// and z weights broadcast into both halves of a pair; odd p: scalar weights.
+template <int P, bool PACK = (P % 2 == 0)>
+struct Operands;
+template <int P>
+struct Operands<P, true> {
+  f2x xa[P], y2[P / 2], z2[P];
+};
+template <int P>
+struct Operands<P, false> {
+  float wx[P], wy[P], wz[P];
+};
+
+// Where stencil row b sits among the packed pairs of an even order: pair ypair(b), high half if
+// yhigh(b). PCS pairs rows (1, 2) and (3, 0), the layout its packed weight evaluation yields.
+template <int P>
+__host__ __device__ constexpr int ypair(int b) {
+  return P == 4 ? ((b == 1 || b == 2) ? 0 : 1) : b / 2;
+}
+template <int P>
+__host__ __device__ constexpr bool yhigh(int b) {
+  return P == 4 ? (b == 0 || b == 2) : (b & 1) != 0;
+}
+__device__ __forceinline__ float half2x(f2x v, bool high) {
+  const float2 q = unpack2(v);
+  return high ? q.y : q.x;
+}
+
 // Register window of one walker: plane a (x node key+S0+a) x row b (y) x column c (z).
 // Even p: y pairs packed in 64-bit registers; odd p: scalars.
 template <int P, bool PACK = (P % 2 == 0)>
@@ -146,7 +174,7 @@ struct Window;
 
 template <int P>
 struct Window<P, true> {
-  f2x v[P][P / 2][P];  // plane a, y pair (2bp, 2bp+1), z column c
+  f2x v[P][P / 2][P];  // plane a, y pair bp, z column c
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int a = 0; a < P; ++a)
@@ -155,30 +183,21 @@ struct Window<P, true> {
 #pragma unroll
         for (int c = 0; c < P; ++c) v[a][bp][c] = 0ull;
   }
-  // v[a][bp][c] += (w_x[a] w_y[2bp], w_x[a] w_y[2bp+1]) * w_z[c]: p^2/2 packed products, p^3/2 packed FMAs
-  __device__ __forceinline__ void add(const float* wx, const float* wy, const float* wz) {
-    f2x y2[P / 2], z2[P];
-#pragma unroll
-    for (int bp = 0; bp < P / 2; ++bp) y2[bp] = pack2(wy[2 * bp], wy[2 * bp + 1]);
-#pragma unroll
-    for (int c = 0; c < P; ++c) z2[c] = pack2(wz[c], wz[c]);
+  // v[a][bp][c] += (w_x[a] y-pair bp) * w_z[c]: p^2/2 packed products, p^3/2 packed FMAs
+  __device__ __forceinline__ void add(const Operands<P>& o) {
 #pragma unroll
     for (int a = 0; a < P; ++a) {
-      const f2x xa = pack2(wx[a], wx[a]);
 #pragma unroll
       for (int bp = 0; bp < P / 2; ++bp) {
-        const f2x xy = mul2(xa, y2[bp]);
+        const f2x xy = mul2(o.xa[a], o.y2[bp]);
 #pragma unroll
-        for (int c = 0; c < P; ++c) fma2(v[a][bp][c], xy, z2[c]);
+        for (int c = 0; c < P; ++c) fma2(v[a][bp][c], xy, o.z2[c]);
       }
     }
   }
   __device__ __forceinline__ void row(int a, int b, float* out) const {
 #pragma unroll
-    for (int c = 0; c < P; ++c) {
-      const float2 q = unpack2(v[a][b / 2][c]);
-      out[c] = (b & 1) ? q.y : q.x;
-    }
+    for (int c = 0; c < P; ++c) out[c] = half2x(v[a][ypair<P>(b)][c], yhigh<P>(b));
   }
   __device__ __forceinline__ void shift() {
 #pragma unroll
@@ -205,21 +224,15 @@ struct Window<P, false> {
 #pragma unroll
         for (int c = 0; c < P; ++c) v[a][b][c] = 0.0f;
   }
-  __device__ __forceinline__ void add(const float* wx, const float* wy, const float* wz) {
+  __device__ __forceinline__ void add(const Operands<P>& o) {
 #pragma unroll
     for (int a = 0; a < P; ++a)
 #pragma unroll
       for (int b = 0; b < P; ++b) {
-        const float xy = wx[a] * wy[b];
+        const float xy = o.wx[a] * o.wy[b];
 #pragma unroll
-        for (int c = 0; c < P; ++c) v[a][b][c] = fmaf(xy, wz[c], v[a][b][c]);
+        for (int c = 0; c < P; ++c) v[a][b][c] = fmaf(xy, o.wz[c], v[a][b][c]);
       }
-  }
-  __device__ __forceinline__ void flush(int a, float* reg, int rx, int ry0, int rz0) const {
-#pragma unroll
-    for (int b = 0; b < P; ++b)
-#pragma unroll
-      for (int c = 0; c < P; ++c) atomicAdd(reg + (rx * walk::RS + ry0 + b) * walk::RS + rz0 + c, v[a][b][c]);
   }
   __device__ __forceinline__ void row(int a, int b, float* out) const {
 #pragma unroll
@@ -239,18 +252,59 @@ struct Window<P, false> {
   }
 };
 
-// Stencil weights of one particle on grid G (x weights scaled by the particle weight wgt).
+// Packed weights of an even order on one axis, as P/2 pairs in the ypair/yhigh layout. PCS
+// evaluates its cubic pieces on (t, 1 - t) together: (t^3, g^3) are the weights of nodes 3 and 0,
+// (3 t^3 - 6 t^2 + 4, 3 g^3 - 6 g^2 + 4) those of nodes 1 and 2 (all times 6).
+template <int P>
+__device__ __forceinline__ void packed_weights(float t, f2x* pr) {
+  if constexpr (P == 4) {
+    const f2x tg = pack2(t, 1.0f - t);
+    const f2x tg2 = mul2(tg, tg);
+    const f2x tg3 = mul2(tg2, tg);
+    f2x w12 = pack2(4.0f, 4.0f);
+    fma2(w12, tg2, pack2(-6.0f, -6.0f));
+    fma2(w12, tg3, pack2(3.0f, 3.0f));
+    pr[0] = w12;
+    pr[1] = tg3;
+  } else {
+    float w[P];
+    weights<P>(t, w);
+#pragma unroll
+    for (int bp = 0; bp < P / 2; ++bp) pr[bp] = pack2(w[2 * bp], w[2 * bp + 1]);
+  }
+}
+
+// Window operands of one particle on grid G (x weights scaled by the particle weight wgt).
 template <int P, int G>
-__device__ __forceinline__ void particle_weights(const int4 r, float wgt, float* wx, float* wy, float* wz) {
+__device__ __forceinline__ Operands<P> particle_operands(const int4 r, float wgt) {
   float tx, ty, tz;
   grid_key<P, G>(__int_as_float(r.y), &tx);
   grid_key<P, G>(__int_as_float(r.z), &ty);
   grid_key<P, G>(__int_as_float(r.w), &tz);
-  weights<P>(tx, wx);
-  weights<P>(ty, wy);
-  weights<P>(tz, wz);
+  Operands<P> o;
+  if constexpr (P % 2 == 0) {
+    f2x px[P / 2], pz[P / 2];
+    packed_weights<P>(tx, px);
+    packed_weights<P>(ty, o.y2);
+    packed_weights<P>(tz, pz);
+    const f2x wg = pack2(wgt, wgt);
 #pragma unroll
-  for (int a = 0; a < P; ++a) wx[a] *= wgt;
+    for (int bp = 0; bp < P / 2; ++bp) px[bp] = mul2(px[bp], wg);
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      const float x = half2x(px[ypair<P>(a)], yhigh<P>(a));
+      const float z = half2x(pz[ypair<P>(a)], yhigh<P>(a));
+      o.xa[a] = pack2(x, x);
+      o.z2[a] = pack2(z, z);
+    }
+  } else {
+    weights<P>(tx, o.wx);
+    weights<P>(ty, o.wy);
+    weights<P>(tz, o.wz);
+#pragma unroll
+    for (int a = 0; a < P; ++a) o.wx[a] *= wgt;
+  }
+  return o;
 }
 
 // Plane a of every lane's window, summed over the key columns of each row with shuffles: node z of
@@ -326,17 +380,14 @@ __device__ __forceinline__ void walk_warp(Smem<W>& S, int q, int lane) {
           s1w = S.sw[i1];
         }
       }
-      float wx0[P], wy0[P], wz0[P], wx1[P], wy1[P], wz1[P];
-      particle_weights<P, G>(c0, c0w * weight_scale<P>(), wx0, wy0, wz0);
-      particle_weights<P, G>(c1, c1w * weight_scale<P>(), wx1, wy1, wz1);
-      win.add(wx0, wy0, wz0);
-      win.add(wx1, wy1, wz1);
+      const Operands<P> o0 = particle_operands<P, G>(c0, c0w * weight_scale<P>());
+      const Operands<P> o1 = particle_operands<P, G>(c1, c1w * weight_scale<P>());
+      win.add(o0);
+      win.add(o1);
     }
     if (j < je) {
       const int i0 = perm[j];
-      float wx0[P], wy0[P], wz0[P];
-      particle_weights<P, G>(S.sp[i0], (W ? S.sw[i0] : 1.0f) * weight_scale<P>(), wx0, wy0, wz0);
-      win.add(wx0, wy0, wz0);
+      win.add(particle_operands<P, G>(S.sp[i0], (W ? S.sw[i0] : 1.0f) * weight_scale<P>()));
     }
     if (valid) jb = je;
     // node plane x + s0 is complete: add it to the region and shift the window
@@ -421,22 +472,26 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
         }
         return;
       }
-      // count the key cells of both grids
+      // count the key cells of both grids; the record's cell word is replaced by the two keys
+      // (grid 1 in the low half, grid 2 in the high half), or by -1 for a particle that is skipped
       for (int i = tid; i < m; i += THREADS) {
         const int4 r = S.sp[i];
         const uint32_t cell = uint32_t(r.x);
         const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        if ((cell >> 30) == 0 && lx >= 0 && lx < T && ly >= 0 && ly < T && lz >= 0 && lz < T) {
+        if ((cell >> 30) == 0 && unsigned(lx) < unsigned(T) && unsigned(ly) < unsigned(T) && unsigned(lz) < unsigned(T)) {
           float t;
           const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
-          atomicAdd(&S.hist[0][((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K +
-                               (lx + grid_key<P, 0>(fx, &t))], 1);
-          if (interlace)
-            atomicAdd(&S.hist[1][((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K +
-                                 (lx + grid_key<P, 1>(fx, &t))], 1);
+          const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + (lx + grid_key<P, 0>(fx, &t));
+          atomicAdd(&S.hist[0][k1], 1);
+          int k2 = 0;
+          if (interlace) {
+            k2 = ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + (lx + grid_key<P, 1>(fx, &t));
+            atomicAdd(&S.hist[1][k2], 1);
+          }
+          S.sp[i].x = k1 | (k2 << 16);
         } else {
           raise_err(PK_DERR_CELLRANGE);
-          S.sp[i].x = -1;  // marks the particle as skipped
+          S.sp[i].x = -1;
         }
       }
       __syncthreads();
@@ -485,19 +540,10 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
       __syncthreads();
       // scatter particle indices into key order; hist[key] advances to the bucket's end
       for (int i = tid; i < m; i += THREADS) {
-        const int4 r = S.sp[i];
-        if (r.x < 0) continue;
-        const uint32_t cell = uint32_t(r.x);
-        const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        float t;
-        const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
-        const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + (lx + grid_key<P, 0>(fx, &t));
-        S.perm[0][atomicAdd(&S.hist[0][k1], 1)] = (unsigned short)i;
-        if (interlace) {
-          const int k2 =
-              ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + (lx + grid_key<P, 1>(fx, &t));
-          S.perm[1][atomicAdd(&S.hist[1][k2], 1)] = (unsigned short)i;
-        }
+        const int keys = S.sp[i].x;
+        if (keys < 0) continue;
+        S.perm[0][atomicAdd(&S.hist[0][keys & 0xffff], 1)] = (unsigned short)i;
+        if (interlace) S.perm[1][atomicAdd(&S.hist[1][keys >> 16], 1)] = (unsigned short)i;
       }
       __syncthreads();
       // walk: warps 0-2 grid 1, warps 3-5 grid 2 (warp-uniform grid)
