@@ -203,8 +203,10 @@ void carve_bin_stage(const pk_config* c, int64_t n, bool need_cells, Carver& cv,
   const int nt = tiles_per_axis(c->ng);
   const int64_t ntiles = int64_t(nt) * nt * nt;
   b->cells = need_cells ? cv.take<pk_cellpos>(size_t(std::max<int64_t>(n, 1))) : nullptr;
-  b->counts = cv.take<unsigned long long>(size_t(ntiles));
-  b->scan = cv.take<long long>(scan_scratch_bytes(ntiles) / sizeof(long long) + 1);
+  const int64_t nkeys = ntiles * kSlabs;
+  b->counts = cv.take<unsigned long long>(size_t(nkeys));
+  b->sub = cv.take<int64_t>(size_t(nkeys + 1));
+  b->scan = cv.take<long long>(scan_scratch_bytes(nkeys) / sizeof(long long) + 1);
 }
 
 // Positions in either format -> binned layout (sorted, wsorted, offsets).
@@ -218,11 +220,8 @@ pk_status run_bin(const pk_config* c, const void* pos, int fmt, const float* w, 
     cells = b.cells;
   }
   const int nt = tiles_per_axis(c->ng);
-  if ((e = launch_bin(cells, w, n, c->ng, kTileCells, nt, sorted, wsorted, offsets, b.counts, b.scan, s)) != cudaSuccess)
+  if ((e = launch_bin(cells, w, n, c->ng, nt, sorted, wsorted, offsets, b.counts, b.sub, b.scan, s)) != cudaSuccess)
     return cuda_fail(e, "bin");
-  if (fmt != PK_POS_F64_XYZ) {  // user-supplied packed cells: validate the sorted copy in place
-    if ((e = launch_check_cells(sorted, n, c->ng, s)) != cudaSuccess) return cuda_fail(e, "check cells");
-  }
   return PK_OK;
 }
 
@@ -350,7 +349,7 @@ int32_t pk_device_error(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned v = 0;
   if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
-  if (take_err_prepare(&v) != 0 || take_err_assign(&v) != 0) return -1;
+  if (take_err_prepare(&v) != 0 || take_err_assign(&v) != 0 || take_err_walk(&v) != 0) return -1;
   return int32_t(v);
 }
 

@@ -1,39 +1,64 @@
 // a3 mass assignment, FP32, column walk with register windows (eq:delgrid on both grids of Sec. 3.1).
 //
-// The scatter is FP32-FMA bound: a particle adds p^3 products to each grid. Accumulating them one by
-// one in shared memory (k_assign_tile) serialises on shared atomics; here the products are summed in
-// registers and only completed planes leave the thread:
-//  - one block per tile of T^3 cells (particles binned by tile, pk_bin), staged in shared memory
-//    (whole tile when it fits, else in chunks) and sorted there by "key cell" with a counting sort;
-//    the key cell is the cell whose fixed stencil (nodes key + S0 .. key + S0 + p - 1 per axis)
-//    covers the particle on that grid, key = cell + delta, delta in {0, 1}, so each grid has
-//    (T+1)^2 key columns of T+1 key cells;
-//  - warps 0-2 walk grid 1's key columns, warps 3-5 grid 2's, one column per thread, in x, with a
-//    window of p x p x p register accumulators (planes key+S0 .. key+S0+p-1); after each x step
-//    the oldest plane is complete and is added to a shared-memory region of (T+4)^3 nodes per grid;
-//  - after the tile, the region is added to the grid in global memory.
+// A particle adds p^3 products to each grid. Accumulating them one by one in shared memory
+// (k_assign_tile) serialises on shared atomics; here the products are summed in registers and only
+// completed planes leave the thread:
+//  - one block per tile of T^3 cells at a time; the tile's particles (binned by tile and, inside
+//    the tile, by half-cell slab along x: pk_bin) are staged in shared memory in pieces and sorted
+//    there by "key cell" with a counting sort; the key cell is the cell whose fixed stencil (nodes
+//    key + S0 .. key + S0 + p - 1 per axis) covers the particle on that grid, key = cell + delta,
+//    delta in {0, 1};
+//  - each lane owns one key column (k_y, k_z) of one grid and walks it in x with a window of
+//    p x p x p register accumulators (planes key+S0 .. key+S0+p-1); after each x step the oldest
+//    plane is complete, is summed along z across the lanes of the key row with shuffles and is
+//    added to a shared-memory region of (T+4)^3 nodes per grid (32-bit fixed point); the walk of a
+//    tile resumes across its pieces, which the slab order makes possible;
+//  - after the tile, the region is added to the grids in global memory.
 // Per particle and grid: p weights per axis, p^2 products w_x w_y and p^3 multiply-adds, issued as
 // packed two-lane FP32 FMAs (fma.rn.f32x2) over pairs of y rows for PCS and CIC.
 #include "internal.cuh"
 
 namespace pk {
 
+PK_ERR_ACCESSOR(take_err_walk)
+
 namespace walk {
 
 constexpr int T = kTileCells;  // tile edge (cells)
 constexpr int K = T + 1;       // key cells per axis and grid
-constexpr int NCOL = K * K;    // key columns per grid
 constexpr int NKEY = K * K * K;
 constexpr int RS = T + 4;  // region edge (nodes -1 .. T+2)
 constexpr int RVOL = RS * RS * RS;
-constexpr int THREADS = 192;  // 6 warps
-constexpr int WPG = 96;       // walker slots per grid (3 warps, 81 used)
-constexpr int NWARP = THREADS / 32;
-constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
+constexpr int MAXWARP = 6;
+
+// Key columns per row (and key cells per axis) that grid G uses: the unshifted grid of an even
+// order keys on floor(u), so its keys stay inside the tile's T cells; the shifted grid, and odd
+// orders (nearest-node keys), reach one cell further.
+template <int P, int G>
+__host__ __device__ constexpr int kspan() {
+  return (G == 0 && P % 2 == 0) ? T : K;
+}
+// Walker lanes: lane = KZ r + kz for key row r of the warp and key column kz (KZ = kspan); 8-column
+// rows give four rows per warp (all 32 lanes hold a column), 9-column rows three (lanes 27..31 hold
+// none). Neighbouring key columns of a row are neighbouring lanes, so a completed plane is summed
+// along z with shuffles before it is added to shared memory.
+template <int P, int G>
+__host__ __device__ constexpr int rows_per_warp() {
+  return 32 / kspan<P, G>();
+}
+template <int P, int G>
+__host__ __device__ constexpr int warps_of_grid() {
+  return kspan<P, G>() / rows_per_warp<P, G>();
+}
+template <int P>
+__host__ __device__ constexpr int threads() {
+  return 32 * (warps_of_grid<P, 0>() + warps_of_grid<P, 1>());
+}
+static_assert(T == 8 && K == 9, "the lane layout assumes 8-cell tiles");
 
 template <bool W>
 __host__ __device__ constexpr int chunk() {
-  return W ? 2048 : 4096;
+  return W ? 1024 : 2048;
 }
 
 template <bool W>
@@ -41,18 +66,13 @@ struct Smem {
   int4 sp[chunk<W>()];
   unsigned short perm[2][chunk<W>()];
   int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
-  float reg[2][RVOL];
-  int scan[2][NWARP];
+  int reg[2][RVOL];  // the tile's node region, fixed point at the tile's scale
+  float red[MAXWARP];
+  int kmin[2], kmax[2];  // range of key x per grid over the staged chunk
+  int scan[2][MAXWARP];
   unsigned long long mbar;  // completion barrier of the bulk copy that stages a chunk
   float sw[W ? chunk<W>() : 1];
 };
-
-// Walker lanes: each grid has three warps; warp-in-grid q holds key rows ky = 3q .. 3q+2, lane
-// 9 r + kz for row r and key column kz (lanes 27..31 hold no column). Neighbouring key columns of a
-// row are neighbouring lanes, so a completed plane is summed along z with shuffles before it is
-// added to shared memory.
-constexpr int ROWS_PER_WARP = 3;
-static_assert(K * ROWS_PER_WARP <= 32 && ROWS_PER_WARP * 3 == K, "three warps of three key rows per grid");
 
 // Stencil start relative to the key cell: PCS and TSC start one node below it.
 template <int P>
@@ -152,15 +172,14 @@ struct Operands<P, false> {
   float wx[P], wy[P], wz[P];
 };
 
-// Where stencil row b sits among the packed pairs of an even order: pair ypair(b), high half if
-// yhigh(b). PCS pairs rows (1, 2) and (3, 0), the layout its packed weight evaluation yields.
+// Where stencil row b sits among the packed pairs of an even order: pair b / 2, high half if b is odd.
 template <int P>
 __host__ __device__ constexpr int ypair(int b) {
-  return P == 4 ? ((b == 1 || b == 2) ? 0 : 1) : b / 2;
+  return b / 2;
 }
 template <int P>
 __host__ __device__ constexpr bool yhigh(int b) {
-  return P == 4 ? (b == 0 || b == 2) : (b & 1) != 0;
+  return (b & 1) != 0;
 }
 __device__ __forceinline__ float half2x(f2x v, bool high) {
   const float2 q = unpack2(v);
@@ -252,26 +271,15 @@ struct Window<P, false> {
   }
 };
 
-// Packed weights of an even order on one axis, as P/2 pairs in the ypair/yhigh layout. PCS
-// evaluates its cubic pieces on (t, 1 - t) together: (t^3, g^3) are the weights of nodes 3 and 0,
-// (3 t^3 - 6 t^2 + 4, 3 g^3 - 6 g^2 + 4) those of nodes 1 and 2 (all times 6).
+// Weights of an even order on one axis as P/2 packed pairs (nodes 2bp, 2bp + 1). (Evaluating the
+// PCS pieces on (t, 1 - t) as packed pairs takes fewer instructions but a longer dependency chain,
+// and measured slower.)
 template <int P>
 __device__ __forceinline__ void packed_weights(float t, f2x* pr) {
-  if constexpr (P == 4) {
-    const f2x tg = pack2(t, 1.0f - t);
-    const f2x tg2 = mul2(tg, tg);
-    const f2x tg3 = mul2(tg2, tg);
-    f2x w12 = pack2(4.0f, 4.0f);
-    fma2(w12, tg2, pack2(-6.0f, -6.0f));
-    fma2(w12, tg3, pack2(3.0f, 3.0f));
-    pr[0] = w12;
-    pr[1] = tg3;
-  } else {
-    float w[P];
-    weights<P>(t, w);
+  float w[P];
+  weights<P>(t, w);
 #pragma unroll
-    for (int bp = 0; bp < P / 2; ++bp) pr[bp] = pack2(w[2 * bp], w[2 * bp + 1]);
-  }
+  for (int bp = 0; bp < P / 2; ++bp) pr[bp] = pack2(w[2 * bp], w[2 * bp + 1]);
 }
 
 // Window operands of one particle on grid G (x weights scaled by the particle weight wgt).
@@ -310,9 +318,11 @@ __device__ __forceinline__ Operands<P> particle_operands(const int4 r, float wgt
 // Plane a of every lane's window, summed over the key columns of each row with shuffles: node z of
 // the row receives column kz's offset c = z - kz - S0 for kz = z - S0 - c; the lane of column kz
 // collects the sum for node kz + S0 and adds it to the region; nodes past the row's last column are
-// added by the columns that reach them.
-template <int P>
-__device__ __forceinline__ void flush_plane(const Window<P>& win, int a, float* reg, int rx, int ry0, int kz, bool valid) {
+// added by the columns that reach them. The region holds fixed-point integers (value x scale, rounded
+// to nearest): integer shared-memory atomics run about three times faster than FP32 ones.
+template <int P, int KZ>
+__device__ __forceinline__ void flush_plane(const Window<P>& win, int a, int* reg, int rx, int ry0, int kz, bool valid,
+                                            float scale) {
 #pragma unroll
   for (int b = 0; b < P; ++b) {
     float v[P];
@@ -324,79 +334,93 @@ __device__ __forceinline__ void flush_plane(const Window<P>& win, int a, float* 
       if (kz >= d) sum += t;
     }
     if (valid) {
-      float* r = reg + (rx * RS + ry0 + b) * RS + kz + s0<P>() + 1;
-      atomicAdd(r, sum);
+      int* r = reg + (rx * RS + ry0 + b) * RS + kz + s0<P>() + 1;
+      atomicAdd(r, __float2int_rn(sum * scale));
 #pragma unroll
       for (int c = 1; c < P; ++c)
-        if (kz + c >= K) atomicAdd(r + c, v[c]);
+        if (kz + c >= KZ) atomicAdd(r + c, __float2int_rn(v[c] * scale));
     }
   }
 }
 
-// One warp of walkers of grid G (warp-in-grid q): lane -> key column (ky, kz); each walks its column
-// in x with a register window; bucket (col, x) holds perm[hist[key-1] .. hist[key]) after the
-// scatter (hist = bucket ends). All 32 lanes run the x loop together (the flush shuffles).
-template <int P, int G, bool W>
-__device__ __forceinline__ void walk_warp(Smem<W>& S, int q, int lane) {
-  const int* ends = S.hist[G];
-  const int r = lane / K, kz = lane - r * K;
-  const bool valid = r < ROWS_PER_WARP;
-  const int ky = ROWS_PER_WARP * q + (valid ? r : 0);
-  const int kbase = (ky * K + kz) * K;
-  int jb = valid ? (kbase == 0 ? 0 : ends[kbase - 1]) : 0;
-  const int cend = valid ? ends[kbase + K - 1] : 0;
-  if (__all_sync(0xffffffffu, jb == cend)) return;  // every column of the warp is empty
-  const int ry0 = ky + s0<P>() + 1;  // region row of stencil offset 0
-  float* reg = S.reg[G];
-  const unsigned short* perm = S.perm[G];
+// State of one warp of walkers across the chunks of a tile: the register window, the next x step to
+// process (xo) and the number of window shifts since a particle was last added (zs; the window is all
+// zero once zs >= P).
+template <int P>
+struct Walker {
   Window<P> win;
-  win.zero();
+  int xo, zs;
+  __device__ __forceinline__ void reset() {
+    win.zero();
+    xo = 0;
+    zs = P;
+  }
+};
+
+// One warp of walkers of grid G (warp-in-grid q) over the staged chunk: lane -> key column (ky, kz);
+// each walks its column in x with its register window; bucket (col, x) holds perm[hist[key-1] ..
+// hist[key]) after the scatter (hist = bucket ends). All 32 lanes run the x loop together (the
+// flush shuffles). A tile's particles arrive ordered by half-cell slab along x, and every grid's key
+// x is a non-decreasing function of that slab, so the chunk's keys lie in [xo, kmax]: steps below
+// kmax are complete after this chunk and are flushed; step kmax stays open for the next chunk (its
+// partial sums stay in the window), unless this is the tile's last chunk, which walks to the end of
+// the span and flushes the remaining planes. Buckets past the grid's key span are empty by
+// construction.
+template <int P, int G, bool W>
+__device__ __forceinline__ void walk_range(Smem<W>& S, Walker<P>& wk, bool last, int q, int lane, float scale) {
+  constexpr int KZ = kspan<P, G>(), R = rows_per_warp<P, G>();
+  const int* ends = S.hist[G];
+  const int r = lane / KZ, kz = lane - r * KZ;
+  const bool valid = r < R;
+  const int ky = R * q + (valid ? r : 0);
+  const int kbase = (ky * K + kz) * K;
+  if (S.kmin[G] < wk.xo && lane == 0) raise_err(PK_DERR_ORDER);  // keys behind the walk: not in slab order
+  const int xe = last ? KZ - 1 : max(wk.xo, S.kmax[G]);
+  int jb = valid ? (kbase + wk.xo == 0 ? 0 : ends[kbase + wk.xo - 1]) : 0;
+  const int ry0 = ky + s0<P>() + 1;  // region row of stencil offset 0
+  int* reg = S.reg[G];
+  const unsigned short* perm = S.perm[G];
+  Window<P>& win = wk.win;
 #pragma unroll 1
-  for (int x = 0; x < K; ++x) {
+  for (int x = wk.xo; x <= xe; ++x) {
     const int je = valid ? ends[kbase + x] : 0;
-    // two particles per iteration (their weight chains overlap each other's multiply-adds); the next
-    // pair's records are loaded before the current pair is accumulated
-    int j = jb;
-    int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
-    float s0w = 1.0f, s1w = 1.0f;
-    if (j + 1 < je) {
-      const int i0 = perm[j], i1 = perm[j + 1];
-      r0 = S.sp[i0];
-      r1 = S.sp[i1];
-      if (W) {
-        s0w = S.sw[i0];
-        s1w = S.sw[i1];
-      }
-    }
-    for (; j + 1 < je; j += 2) {
-      const int4 c0 = r0, c1 = r1;
-      const float c0w = s0w, c1w = s1w;
-      if (j + 3 < je) {
-        const int i0 = perm[j + 2], i1 = perm[j + 3];
+    if (__any_sync(0xffffffffu, jb < je)) {
+      wk.zs = 0;
+      // one particle per iteration; the next record is loaded before the current one is accumulated
+      int j = jb;
+      int4 r0 = make_int4(0, 0, 0, 0);
+      float s0w = 1.0f;
+      if (j < je) {
+        const int i0 = perm[j];
         r0 = S.sp[i0];
-        r1 = S.sp[i1];
-        if (W) {
-          s0w = S.sw[i0];
-          s1w = S.sw[i1];
-        }
+        if (W) s0w = S.sw[i0];
       }
-      const Operands<P> o0 = particle_operands<P, G>(c0, c0w * weight_scale<P>());
-      const Operands<P> o1 = particle_operands<P, G>(c1, c1w * weight_scale<P>());
-      win.add(o0);
-      win.add(o1);
-    }
-    if (j < je) {
-      const int i0 = perm[j];
-      win.add(particle_operands<P, G>(S.sp[i0], (W ? S.sw[i0] : 1.0f) * weight_scale<P>()));
+      for (; j < je; ++j) {
+        const int4 c0 = r0;
+        const float c0w = s0w;
+        if (j + 1 < je) {
+          const int i0 = perm[j + 1];
+          r0 = S.sp[i0];
+          if (W) s0w = S.sw[i0];
+        }
+        win.add(particle_operands<P, G>(c0, c0w * weight_scale<P>()));
+      }
     }
     if (valid) jb = je;
-    // node plane x + s0 is complete: add it to the region and shift the window
-    flush_plane<P>(win, 0, reg, x + s0<P>() + 1, ry0, kz, valid);
-    win.shift();
+    if (x < xe || last) {  // node plane x + s0 is complete: add it to the region and shift the window
+      if (wk.zs < P) flush_plane<P, KZ>(win, 0, reg, x + s0<P>() + 1, ry0, kz, valid, scale);
+      win.shift();
+      ++wk.zs;
+    }
   }
-  // the remaining planes K + s0 .. K + s0 + P - 2
+  if (last) {  // the remaining planes KZ + s0 .. KZ + s0 + P - 2 (plane a is non-zero while a < P - zs)
 #pragma unroll
-  for (int a = 0; a + 1 < P; ++a) flush_plane<P>(win, a, reg, K + a + s0<P>() + 1, ry0, kz, valid);
+    for (int a = 0; a + 1 < P; ++a)
+      if (a < P - wk.zs) flush_plane<P, KZ>(win, a, reg, KZ + a + s0<P>() + 1, ry0, kz, valid, scale);
+    wk.reset();
+  } else {
+    wk.xo = xe;
+  }
 }
 
 // Bulk copy (TMA) of `bytes` from global to shared memory, completing on the mbarrier at bar.
@@ -427,12 +451,14 @@ __device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned pari
 }  // namespace walk
 
 template <int P, bool W>
-__global__ void __launch_bounds__(walk::THREADS, 2)
+__global__ void __launch_bounds__(walk::threads<P>(), 3)
     k_assign_walk(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
                   int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
                   int64_t cat_stride) {
   using namespace walk;
   constexpr int CH = chunk<W>();
+  constexpr int THREADS = threads<P>(), NWARP = THREADS / 32, NW0 = warps_of_grid<P, 0>();
+  constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
   {  // blockIdx.y selects a catalogue of a batch: its grids and its tile offsets
     const int cat = blockIdx.y;
     g1 += cat * cat_stride;
@@ -450,12 +476,31 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
   }
   __syncthreads();
   unsigned parity = 0;
+  Walker<P> wk;
+  wk.reset();
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
     if (beg >= end) continue;
     const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
-    for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0.0f;
+    for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
+    // fixed-point scale 2^e of the region: no node (nor any partial sum of one) exceeds the tile's
+    // total |weight| B, and B 2^e < 2^30 leaves room for the rounding of every addition
+    float bound = float(end - beg);
+    if (W) {
+      float a = 0.0f;
+      for (int64_t i = beg + tid; i < end; i += THREADS) a += fabsf(w[i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) S.red[warp] = a;
+      __syncthreads();
+      bound = 0.0f;
+      for (int q = 0; q < NWARP; ++q) bound += S.red[q];
+      bound *= 1.0001f;  // the FP32 sum's rounding
+    }
+    int ex;
+    frexpf(fmaxf(bound, 1.0f), &ex);  // bound < 2^ex
+    const float scale = ldexpf(1.0f, 30 - ex), inv_scale = ldexpf(1.0f, ex - 30);
     for (int64_t c0 = beg; c0 < end; c0 += CH) {
       const int m = int(min(int64_t(CH), end - c0));
       // stage the chunk with one bulk copy (16-byte records, 16-byte aligned)
@@ -463,6 +508,10 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
       if (W)
         for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
       for (int i = tid; i < 2 * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
+      if (tid < 2) {
+        S.kmin[tid] = K;
+        S.kmax[tid] = -1;
+      }
       const bool arrived = bulk_wait(&S.mbar, parity);
       parity ^= 1u;
       if (__syncthreads_or(!arrived)) {  // the copy did not complete: report, drain, stop
@@ -473,7 +522,9 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
         return;
       }
       // count the key cells of both grids; the record's cell word is replaced by the two keys
-      // (grid 1 in the low half, grid 2 in the high half), or by -1 for a particle that is skipped
+      // (grid 1 in the low half, grid 2 in the high half), or by -1 for a particle that is skipped;
+      // the range of key x per grid is gathered for the walk
+      int lo0 = K, hi0 = -1, lo1 = K, hi1 = -1;
       for (int i = tid; i < m; i += THREADS) {
         const int4 r = S.sp[i];
         const uint32_t cell = uint32_t(r.x);
@@ -481,18 +532,34 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
         if ((cell >> 30) == 0 && unsigned(lx) < unsigned(T) && unsigned(ly) < unsigned(T) && unsigned(lz) < unsigned(T)) {
           float t;
           const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
-          const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + (lx + grid_key<P, 0>(fx, &t));
+          const int kx1 = lx + grid_key<P, 0>(fx, &t);
+          const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + kx1;
           atomicAdd(&S.hist[0][k1], 1);
+          lo0 = min(lo0, kx1);
+          hi0 = max(hi0, kx1);
           int k2 = 0;
           if (interlace) {
-            k2 = ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + (lx + grid_key<P, 1>(fx, &t));
+            const int kx2 = lx + grid_key<P, 1>(fx, &t);
+            k2 = ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + kx2;
             atomicAdd(&S.hist[1][k2], 1);
+            lo1 = min(lo1, kx2);
+            hi1 = max(hi1, kx2);
           }
           S.sp[i].x = k1 | (k2 << 16);
         } else {
           raise_err(PK_DERR_CELLRANGE);
           S.sp[i].x = -1;
         }
+      }
+      lo0 = __reduce_min_sync(0xffffffffu, lo0);
+      hi0 = __reduce_max_sync(0xffffffffu, hi0);
+      lo1 = __reduce_min_sync(0xffffffffu, lo1);
+      hi1 = __reduce_max_sync(0xffffffffu, hi1);
+      if (lane == 0) {
+        atomicMin(&S.kmin[0], lo0);
+        atomicMax(&S.kmax[0], hi0);
+        atomicMin(&S.kmin[1], lo1);
+        atomicMax(&S.kmax[1], hi1);
       }
       __syncthreads();
       // block-wide exclusive scan of both histograms (NKEY + 1 entries each)
@@ -546,28 +613,29 @@ __global__ void __launch_bounds__(walk::THREADS, 2)
         if (interlace) S.perm[1][atomicAdd(&S.hist[1][keys >> 16], 1)] = (unsigned short)i;
       }
       __syncthreads();
-      // walk: warps 0-2 grid 1, warps 3-5 grid 2 (warp-uniform grid)
-      if (warp < 3)
-        walk_warp<P, 0, W>(S, warp, lane);
+      // walk: the first NW0 warps grid 1, the others grid 2 (warp-uniform grid)
+      const bool last = c0 + CH >= end;
+      if (warp < NW0)
+        walk_range<P, 0, W>(S, wk, last, warp, lane, scale);
       else if (interlace)
-        walk_warp<P, 1, W>(S, warp - 3, lane);
+        walk_range<P, 1, W>(S, wk, last, warp - NW0, lane, scale);
       __syncthreads();
     }
-    // add the tile's region (origin: node (cx0-1, cy0-1, cz0-1)) to the grids; node pairs whose global
-    // z index is even are added with one 8-byte vector reduction
+    // add the tile's region (origin: node (cx0-1, cy0-1, cz0-1)), converted back from fixed point, to
+    // the grids; node pairs whose global z index is even are added with one 8-byte vector reduction
     for (int i = tid; i < ngrid * RS * RS * 7; i += THREADS) {
       const int row = i / 7, item = i - row * 7;
       const int gi = row / (RS * RS), rr = row - gi * (RS * RS);
       const int rx = rr / RS, ry = rr - rx * RS;
-      const float* src = &S.reg[gi][(rx * RS + ry) * RS];
+      const int* src = &S.reg[gi][(rx * RS + ry) * RS];
       float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
       if (item == 0 || item == 6) {
         const int rz = item == 0 ? 0 : RS - 1;
-        const float v = src[rz];
+        const float v = float(src[rz]) * inv_scale;
         if (v != 0.0f) atomicAdd(gg + wrap(cz0 - 1 + rz, ng), v);
       } else {
         const int rz = 2 * item - 1;  // odd: the global z index cz0 - 1 + rz is even
-        const float v0 = src[rz], v1 = src[rz + 1];
+        const float v0 = float(src[rz]) * inv_scale, v1 = float(src[rz + 1]) * inv_scale;
         if (v0 != 0.0f || v1 != 0.0f) {
           const int z = wrap(cz0 - 1 + rz, ng);
           float* dst = gg + z;
@@ -593,11 +661,11 @@ static cudaError_t launch_walk_pw(const pk_cellpos* p, const float* w, const int
   cudaError_t e = cudaFuncSetAttribute(k_assign_walk<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assign_walk<P, W>, walk::THREADS, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assign_walk<P, W>, walk::threads<P>(), smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
-  k_assign_walk<P, W><<<blocks, walk::THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, cat_stride);
+  k_assign_walk<P, W><<<blocks, walk::threads<P>(), smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, cat_stride);
   count_launch();
   return cudaGetLastError();
 }

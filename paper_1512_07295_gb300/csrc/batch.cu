@@ -10,6 +10,7 @@ namespace pk {
 struct BatchLayout {
   pk_cellpos* sorted = nullptr;
   unsigned long long* counts = nullptr;
+  int64_t* sub = nullptr;
   int64_t* offsets = nullptr;
   long long* scan = nullptr;
   float* grids = nullptr;
@@ -26,9 +27,10 @@ static pk_status carve_batch(const pk_config* c, int batch, int64_t maxp, Carver
   const int nt = tiles_per_axis(c->ng);
   const int64_t ntiles = int64_t(nt) * nt * nt * batch;
   L->sorted = cv.take<pk_cellpos>(size_t(std::max<int64_t>(maxp, 1)));
-  L->counts = cv.take<unsigned long long>(size_t(ntiles));
+  L->counts = cv.take<unsigned long long>(size_t(ntiles * kSlabs));
+  L->sub = cv.take<int64_t>(size_t(ntiles * kSlabs + 1));
   L->offsets = cv.take<int64_t>(size_t(ntiles + 1));
-  L->scan = cv.take<long long>(scan_scratch_bytes(ntiles) / sizeof(long long) + 1);
+  L->scan = cv.take<long long>(scan_scratch_bytes(ntiles * kSlabs) / sizeof(long long) + 1);
   L->grids = cv.take<float>(size_t(2) * batch * padded_count(c->ng));
   L->tables = cv.take<float>(estimate_table_bytes(c->ng, false) / sizeof(float));
   L->wsums = cv.take<double>(size_t(3) * batch);
@@ -113,7 +115,7 @@ pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* off
     // a2: batched counting sort (sorted indices relative to the group's first particle)
     CatRanges rel = r;
     for (int c = 0; c <= nb; ++c) rel.off[c] = r.off[c] - r.off[0];
-    if ((e = launch_bin_batch(base + r.off[0], rel, ng, kTileCells, nt, L.sorted, L.offsets, L.counts, L.scan, s)) != cudaSuccess)
+    if ((e = launch_bin_batch(base + r.off[0], rel, ng, nt, L.sorted, L.offsets, L.counts, L.sub, L.scan, s)) != cudaSuccess)
       return cuda_fail(e, "batch bin");
     // a3: all catalogues' grid pairs
     if ((e = cudaMemsetAsync(L.grids, 0, size_t(2) * nb * per * sizeof(float), s)) != cudaSuccess) return cuda_fail(e, "memset");

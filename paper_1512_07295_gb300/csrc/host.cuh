@@ -60,7 +60,8 @@ pk_status run_fft_estimate(const pk_config* c, GridStage& g, void* delta_out, do
 
 struct BinStage {
   pk_cellpos* cells = nullptr;
-  unsigned long long* counts = nullptr;
+  unsigned long long* counts = nullptr;  // per (tile, slab) key
+  int64_t* sub = nullptr;                // slab offsets
   long long* scan = nullptr;
 };
 void carve_bin_stage(const pk_config* c, int64_t n, bool need_cells, Carver& cv, BinStage* b);

@@ -16,18 +16,23 @@ void count_launch(int k = 1);  // number of kernels this library launched (pk_pr
 // Per-translation-unit device error words (see PK_ERR_ACCESSOR): OR into *acc and clear.
 int take_err_prepare(unsigned* acc);
 int take_err_assign(unsigned* acc);
+int take_err_walk(unsigned* acc);
 
 // Tile edge (cells) of the binned layout for a grid of side ng, and tiles per axis.
 constexpr int kTileCells = 8;
 inline int tiles_per_axis(int ng) { return (ng + kTileCells - 1) / kTileCells; }
+// Inside a tile the binned particles are ordered by half-cell slab along x, 2 (c_x mod T) + [f_x >= 1/2]:
+// the sort key of a particle is tile * kSlabs + slab.
+constexpr int kSlabs = 2 * kTileCells;
 
 // prepare.cu
 cudaError_t launch_prepare(const double* pos, int64_t n, int ng, double box, pk_cellpos* out, cudaStream_t s);
-cudaError_t launch_check_cells(pk_cellpos* p, int64_t n, int ng, cudaStream_t s);
 size_t scan_scratch_bytes(int64_t n);
 cudaError_t launch_exclusive_scan(const unsigned long long* in, int64_t n, int64_t* out, long long* scratch, cudaStream_t s);
-cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int tcells, int ntile, pk_cellpos* sorted,
-                       float* wsorted, int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s);
+// counts: ntiles * kSlabs entries; sub: ntiles * kSlabs + 1 (slab offsets); scan_scratch for ntiles * kSlabs.
+cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int ntile, pk_cellpos* sorted,
+                       float* wsorted, int64_t* offsets, unsigned long long* counts, int64_t* sub, long long* scan_scratch,
+                       cudaStream_t s);
 
 constexpr int kMaxBatch = 128;
 struct CatRanges {  // particle ranges of the catalogues of one batch group (absolute indices)
@@ -35,8 +40,8 @@ struct CatRanges {  // particle ranges of the catalogues of one batch group (abs
   int nb;
   int ng;
 };
-cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, int tcells, int ntile, pk_cellpos* sorted,
-                             int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s);
+cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, int ntile, pk_cellpos* sorted, int64_t* offsets,
+                             unsigned long long* counts, int64_t* sub, long long* scan_scratch, cudaStream_t s);
 
 // assign.cu -- grid layout: node (x, y, z) at element (x * ng + y) * ldz + z of each grid.
 cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,

@@ -3,8 +3,11 @@
 // a1 (Sec. 2.3, s = (x_j - x)/H): an FP64 position is wrapped into [0, L) (periodic box) and split
 // into the integer cell c = floor(x/H) and the offset f = x/H - c in [0, 1), stored as FP32.
 // a2: particles are grouped by tile of T^3 cells with a counting sort (histogram, exclusive scan,
-// scatter). Histogram and scatter use warp-aggregated atomics: consecutive particles of a spatially
-// ordered catalogue share a tile, and one atomic per distinct tile per warp replaces 32.
+// scatter), and inside a tile by half-cell slab along x (key tile * 2T + 2 (c_x mod T) + [f_x >= 1/2]):
+// the assignment walks a tile's slabs in order and can stage a large tile in several pieces.
+// Histogram and scatter use warp-aggregated atomics: consecutive particles of a spatially ordered
+// catalogue share a key, and one atomic per distinct key per warp replaces 32. Particles are
+// validated on the way (an invalid record is reported and binned as cell 0, offset 0).
 #include "internal.cuh"
 
 namespace pk {
@@ -52,9 +55,11 @@ __global__ void k_prepare(const double* __restrict__ pos, int64_t n, int ng, dou
   for (int64_t i = gtid(); i < n; i += gstride()) out[i] = prepare_one(pos + 3 * i, ng, box, scale);
 }
 
-__device__ __forceinline__ int tile_key(uint32_t cell, int tcells, int ntile) {
-  const int tx = cell_x(cell) / tcells, ty = cell_y(cell) / tcells, tz = cell_z(cell) / tcells;
-  return (tx * ntile + ty) * ntile + tz;
+// Sort key of a (validated) particle: tile and half-cell slab along x.
+__device__ __forceinline__ int bin_key(const pk_cellpos& r, int ntile) {
+  const int cx = cell_x(r.cell), tx = cx / kTileCells, ty = cell_y(r.cell) / kTileCells, tz = cell_z(r.cell) / kTileCells;
+  const int slab = 2 * (cx - tx * kTileCells) + (r.fx >= 0.5f ? 1 : 0);
+  return ((tx * ntile + ty) * ntile + tz) * kSlabs + slab;
 }
 
 // Validates a packed particle (coordinates < N, offsets in [0,1)); invalid ones are reported and
@@ -70,10 +75,6 @@ __device__ __forceinline__ pk_cellpos checked(pk_cellpos r, int ng) {
   return r;
 }
 
-__global__ void k_check_cells(pk_cellpos* __restrict__ p, int64_t n, int ng) {
-  for (int64_t i = gtid(); i < n; i += gstride()) p[i] = checked(p[i], ng);
-}
-
 // Warp-aggregated increment of ctr[key]; returns the value this lane would have seen alone.
 __device__ __forceinline__ unsigned long long agg_inc(unsigned long long* ctr, int key, unsigned active) {
   const unsigned peers = __match_any_sync(active, key);
@@ -85,19 +86,19 @@ __device__ __forceinline__ unsigned long long agg_inc(unsigned long long* ctr, i
   return base + __popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void k_tile_hist(const pk_cellpos* __restrict__ p, int64_t n, int tcells, int ntile,
+__global__ void k_tile_hist(const pk_cellpos* __restrict__ p, int64_t n, int ng, int ntile,
                             unsigned long long* __restrict__ counts) {
   const int64_t stride = gstride();
   const int64_t nround = (n + 31) / 32 * 32;
   for (int64_t i = gtid(); i < nround; i += stride) {
     const bool live = i < n;
     const unsigned active = __ballot_sync(0xffffffffu, live);
-    if (live) agg_inc(counts, tile_key(p[i].cell, tcells, ntile), active);
+    if (live) agg_inc(counts, bin_key(checked(p[i], ng), ntile), active);
   }
 }
 
-__global__ void k_tile_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, int64_t n, int tcells,
-                               int ntile, const int64_t* __restrict__ offsets, unsigned long long* __restrict__ cursor,
+__global__ void k_tile_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, int64_t n, int ng, int ntile,
+                               const int64_t* __restrict__ sub, unsigned long long* __restrict__ cursor,
                                pk_cellpos* __restrict__ out, float* __restrict__ wout) {
   const int64_t stride = gstride();
   const int64_t nround = (n + 31) / 32 * 32;
@@ -105,44 +106,49 @@ __global__ void k_tile_scatter(const pk_cellpos* __restrict__ p, const float* __
     const bool live = i < n;
     const unsigned active = __ballot_sync(0xffffffffu, live);
     if (live) {
-      const pk_cellpos r = p[i];
-      const int key = tile_key(r.cell, tcells, ntile);
-      const int64_t dst = offsets[key] + int64_t(agg_inc(cursor, key, active));
+      const pk_cellpos r = checked(p[i], ng);
+      const int key = bin_key(r, ntile);
+      const int64_t dst = sub[key] + int64_t(agg_inc(cursor, key, active));
       out[dst] = r;
       if (wout) wout[dst] = w[i];
     }
   }
 }
 
+// Tile offsets from the slab offsets: offsets[t] = sub[t * kSlabs], t = 0 .. ntiles.
+__global__ void k_tile_offsets(const int64_t* __restrict__ sub, int64_t ntiles, int64_t* __restrict__ offsets) {
+  for (int64_t t = gtid(); t <= ntiles; t += gstride()) offsets[t] = sub[t * kSlabs];
+}
+
 // Batched binning: blockIdx.y = catalogue c of the group, particles r.off[c] .. r.off[c+1]-1 of p,
 // key c * ntiles + tile. Sorted output indices count from the group's first particle.
-__global__ void k_tile_hist_batch(const pk_cellpos* __restrict__ p, CatRanges r, int tcells, int ntile,
+__global__ void k_tile_hist_batch(const pk_cellpos* __restrict__ p, CatRanges r, int ntile,
                                   unsigned long long* __restrict__ counts) {
   const int c = blockIdx.y;
   const int64_t beg = r.off[c], cnt = r.off[c + 1] - beg;
-  const int base = c * ntile * ntile * ntile;
+  const int base = c * ntile * ntile * ntile * kSlabs;
   const int64_t nround = (cnt + 31) / 32 * 32;
   for (int64_t k = gtid(); k < nround; k += gstride()) {
     const bool live = k < cnt;
     const unsigned active = __ballot_sync(0xffffffffu, live);
-    if (live) agg_inc(counts, base + tile_key(checked(p[beg + k], r.ng).cell, tcells, ntile), active);
+    if (live) agg_inc(counts, base + bin_key(checked(p[beg + k], r.ng), ntile), active);
   }
 }
 
-__global__ void k_tile_scatter_batch(const pk_cellpos* __restrict__ p, CatRanges r, int tcells, int ntile,
-                                     const int64_t* __restrict__ offsets, unsigned long long* __restrict__ cursor,
+__global__ void k_tile_scatter_batch(const pk_cellpos* __restrict__ p, CatRanges r, int ntile,
+                                     const int64_t* __restrict__ sub, unsigned long long* __restrict__ cursor,
                                      pk_cellpos* __restrict__ out) {
   const int c = blockIdx.y;
   const int64_t beg = r.off[c], cnt = r.off[c + 1] - beg;
-  const int base = c * ntile * ntile * ntile;
+  const int base = c * ntile * ntile * ntile * kSlabs;
   const int64_t nround = (cnt + 31) / 32 * 32;
   for (int64_t k = gtid(); k < nround; k += gstride()) {
     const bool live = k < cnt;
     const unsigned active = __ballot_sync(0xffffffffu, live);
     if (live) {
       const pk_cellpos rec = checked(p[beg + k], r.ng);
-      const int key = base + tile_key(rec.cell, tcells, ntile);
-      out[offsets[key] + int64_t(agg_inc(cursor, key, active))] = rec;
+      const int key = base + bin_key(rec, ntile);
+      out[sub[key] + int64_t(agg_inc(cursor, key, active))] = rec;
     }
   }
 }
@@ -219,14 +225,6 @@ cudaError_t launch_prepare(const double* pos, int64_t n, int ng, double box, pk_
   return cudaGetLastError();
 }
 
-cudaError_t launch_check_cells(pk_cellpos* p, int64_t n, int ng, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  const int threads = 256;
-  const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, int64_t(num_sms()) * 16);
-  k_check_cells<<<int(blocks), threads, 0, s>>>(p, n, ng); count_launch();
-  return cudaGetLastError();
-}
-
 size_t scan_scratch_bytes(int64_t n) { return size_t((n + kScanBlock - 1) / kScanBlock) * sizeof(long long); }
 
 cudaError_t launch_exclusive_scan(const unsigned long long* in, int64_t n, int64_t* out, long long* scratch, cudaStream_t s) {
@@ -237,40 +235,50 @@ cudaError_t launch_exclusive_scan(const unsigned long long* in, int64_t n, int64
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int tcells, int ntile, pk_cellpos* sorted,
-                       float* wsorted, int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s) {
-  const int64_t ntiles = int64_t(ntile) * ntile * ntile;
-  cudaError_t e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s);
+static cudaError_t launch_tile_offsets(const int64_t* sub, int64_t ntiles, int64_t* offsets, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((ntiles + threads) / threads, int64_t(num_sms()) * 8));
+  k_tile_offsets<<<int(blocks), threads, 0, s>>>(sub, ntiles, offsets); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int ntile, pk_cellpos* sorted,
+                       float* wsorted, int64_t* offsets, unsigned long long* counts, int64_t* sub, long long* scan_scratch,
+                       cudaStream_t s) {
+  const int64_t ntiles = int64_t(ntile) * ntile * ntile, nkeys = ntiles * kSlabs;
+  cudaError_t e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, int64_t(num_sms()) * 16));
   if (n > 0) {
-    k_tile_hist<<<int(blocks), threads, 0, s>>>(cells, n, tcells, ntile, counts); count_launch();
+    k_tile_hist<<<int(blocks), threads, 0, s>>>(cells, n, ng, ntile, counts); count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if ((e = launch_exclusive_scan(counts, ntiles, offsets, scan_scratch, s)) != cudaSuccess) return e;
+  if ((e = launch_exclusive_scan(counts, nkeys, sub, scan_scratch, s)) != cudaSuccess) return e;
+  if ((e = launch_tile_offsets(sub, ntiles, offsets, s)) != cudaSuccess) return e;
   if (n > 0) {
-    if ((e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    k_tile_scatter<<<int(blocks), threads, 0, s>>>(cells, w, n, tcells, ntile, offsets, counts, sorted, wsorted); count_launch();
+    if ((e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    k_tile_scatter<<<int(blocks), threads, 0, s>>>(cells, w, n, ng, ntile, sub, counts, sorted, wsorted); count_launch();
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, int tcells, int ntile, pk_cellpos* sorted,
-                             int64_t* offsets, unsigned long long* counts, long long* scan_scratch, cudaStream_t s) {
-  const int64_t ntiles = int64_t(ntile) * ntile * ntile * r.nb;
-  cudaError_t e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s);
+cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, int ntile, pk_cellpos* sorted, int64_t* offsets,
+                             unsigned long long* counts, int64_t* sub, long long* scan_scratch, cudaStream_t s) {
+  const int64_t ntiles = int64_t(ntile) * ntile * ntile * r.nb, nkeys = ntiles * kSlabs;
+  cudaError_t e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   int64_t maxc = 1;
   for (int c = 0; c < r.nb; ++c) maxc = std::max<int64_t>(maxc, r.off[c + 1] - r.off[c]);
   const dim3 blocks(unsigned(std::max<int64_t>(1, std::min<int64_t>((maxc + 255) / 256, std::max(1, num_sms() * 16 / r.nb)))),
                     unsigned(r.nb));
   (void)ng;
-  k_tile_hist_batch<<<blocks, 256, 0, s>>>(p, r, tcells, ntile, counts); count_launch();
+  k_tile_hist_batch<<<blocks, 256, 0, s>>>(p, r, ntile, counts); count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_exclusive_scan(counts, ntiles, offsets, scan_scratch, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(counts, 0, size_t(ntiles) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-  k_tile_scatter_batch<<<blocks, 256, 0, s>>>(p, r, tcells, ntile, offsets, counts, sorted); count_launch();
+  if ((e = launch_exclusive_scan(counts, nkeys, sub, scan_scratch, s)) != cudaSuccess) return e;
+  if ((e = launch_tile_offsets(sub, ntiles, offsets, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  k_tile_scatter_batch<<<blocks, 256, 0, s>>>(p, r, ntile, sub, counts, sorted); count_launch();
   return cudaGetLastError();
 }
 
