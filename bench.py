@@ -33,6 +33,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "particles/s & P(k)/s (PCS+interlace, N_g=512), % HBM roofline vs plain FP64 path"
+
+# DRAM bytes (read + write) per particle of one k_assign_walk<4,false> launch, from an ncu capture of
+# the 256^3-particle / N_G = 128 case (8 particles per cell, as in the 1024^3 / N_G = 512 workload, so
+# the per-particle traffic carries over). None when the kernel has changed since the capture.
+WALK_TRAFFIC_PER_PARTICLE = None
+WALK_TRAFFIC_SOURCE = None
 RMS_DISP = 4.0
 
 
@@ -50,6 +56,28 @@ def parse():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
+
+
+def replica_seed(rank):
+    """Seed of the catalogue a rank generates: every replica times its own independent realisation."""
+    return 3 + rank
+
+
+def max_over_ranks(ms, device):
+    """The job's time: the largest per-rank time over all ranks (identity on a single process)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, steps, ms_total):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank * steps / (ms_total * 1e-3)
 
 
 def workload_name(a):
@@ -294,7 +322,7 @@ def main():
     cfg = api.Config(ng=a.ng, box=a.box, order=4, interlace=True, prec="fp32")
 
     # ---- input: seeded Zel'dovich catalogue (one independent realisation per rank) ----------------
-    pos64 = catalogs.zeldovich_torch(a.nside, a.box, RMS_DISP, seed=3 + rank, device=dev)
+    pos64 = catalogs.zeldovich_torch(a.nside, a.box, RMS_DISP, seed=replica_seed(rank), device=dev)
     host64 = None
     if not a.no_extras:
         host64 = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
@@ -337,14 +365,10 @@ def main():
         torch.cuda.profiler.stop()
     launches = lib.pk_profile_launches() - launches0
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dev)
     ms_step = ms_total / a.steps
-    value = world * n * a.steps / (ms_total * 1e-3)
-    pk_per_s = world * a.steps / (ms_total * 1e-3)
+    value = job_rate(world, n, a.steps, ms_total)
+    pk_per_s = job_rate(world, 1, a.steps, ms_total)
 
     # ---- per-stage times (same calls, CUDA events at the stage boundaries) ----------------------------
     lib.pk_profile_enable(1)
@@ -369,6 +393,8 @@ def main():
     assign_bytes = 16.0 * n + 2 * 4.0 * a.ng ** 3  # particle records read once, two grids written once
     achieved_tflops = assign_flop / (t_assign_ms * 1e-3) / 1e12
     achieved_gbs = assign_bytes / (t_assign_ms * 1e-3) / 1e9
+    same_density = a.nside ** 3 == 8 * a.ng ** 3
+    traffic = WALK_TRAFFIC_PER_PARTICLE * n if (WALK_TRAFFIC_PER_PARTICLE and same_density) else None
     nh = a.ng * a.ng * (a.ng // 2 + 1)
     path_bytes = 16.0 * n + 2 * (4.0 * a.ng ** 3 + (4.0 * a.ng ** 3 + 8.0 * nh) + 8.0 * nh)
     result = {
@@ -383,10 +409,14 @@ def main():
                               "peak_gbs": hbm_peak, "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak},
         "stages_ms": {"weights": stages[0], "grid_clear": stages[1], "assign": stages[2], "fft": stages[3],
                       "estimate": stages[4]},
-        "roofline": {"kernel": "k_assign_tile<4,float>", "bound": "alu", "achieved": achieved_tflops,
+        "roofline": {"kernel": "k_assign_walk<4,false>", "bound": "alu", "achieved": achieved_tflops,
                      "peak": alu_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops,
-                     "traffic": None, "hbm_achieved_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak,
-                     "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:g} MHz"},
+                     "traffic": traffic, "traffic_source": WALK_TRAFFIC_SOURCE if traffic else None,
+                     "algorithmic_bytes": assign_bytes, "hbm_achieved_gbs": achieved_gbs,
+                     "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                     "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:g} MHz",
+                     "timing": "CUDA events on the library's stream around the assignment launch, mean over "
+                               f"{nprof} steps"},
         "clocks": clk,
         "gpu_launches": int(launches),
     }
