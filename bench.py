@@ -7,8 +7,9 @@ L = 2000 Mpc/h on an N_G = 512 grid, PCS assignment with interlacing, FP32 cell 
 two real FFTs, the fused deconvolution / interlacing / shell reduction and the finalisation.
 
 Printed: one JSON line (rank 0). ``value`` = particles/s (P(k)/s in ``pk_per_s``); ``e2e`` = the same
-metric through pk_power from pinned host FP64 positions (H2D copy, preparation, binning, assignment,
-FFT, estimate, D2H of P(k) inside the timed region); ``roofline`` for the assignment kernel;
+metric through pk_power_host from pinned host FP64 positions (the GPU reads them over the CPU-GPU link
+while preparing them; binning, assignment, FFT, estimate and the D2H of the results inside the timed
+region); ``roofline`` for the assignment kernel;
 ``cpu_baseline`` = the FP64 CPU oracle on a bounded sample; ``fp64_plain`` = the plain FP64 GPU path
 (global FP64 atomics, FP64 FFT) on the same catalogue.
 
@@ -37,8 +38,9 @@ METRIC = "particles/s & P(k)/s (PCS+interlace, N_g=512), % HBM roofline vs plain
 # DRAM bytes (read + write) per particle of one k_assign_walk<4,false> launch, from an ncu capture of
 # the 256^3-particle / N_G = 128 case (8 particles per cell, as in the 1024^3 / N_G = 512 workload, so
 # the per-particle traffic carries over). None when the kernel has changed since the capture.
-WALK_TRAFFIC_PER_PARTICLE = None
-WALK_TRAFFIC_SOURCE = None
+WALK_TRAFFIC_PER_PARTICLE = 300.55e6 / 256 ** 3
+WALK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 256^3 particles / N_G=128 "
+                       "(profiles/k_assign_walk_pcs_interlace_256cube_ng128.md), scaled by the particle count")
 RMS_DISP = 4.0
 
 
@@ -441,15 +443,16 @@ def main():
         del ws64, binned, sorted_, offsets
         torch.cuda.empty_cache()
 
-        # ---- e2e through pk_power from pinned host FP64 positions ----------------------------------
-        wsp = api.workspace(cfg, n, ffi.PK_WS_POWER, dev)
-        dpos = torch.empty((n, 3), dtype=torch.float64, device=dev)
-        pk_host = torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True)
+        # ---- e2e through pk_power_host from pinned host FP64 positions ------------------------------
+        # the GPU reads the positions over the CPU-GPU link while preparing them, and P(k), kmean and
+        # the mode counts come back to pinned host memory, all inside the timed region
+        wsp = api.workspace(cfg, n, ffi.PK_WS_POWER_HOST, dev)
+        host_out = (torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True),
+                    torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True),
+                    torch.empty(cfg.nb, dtype=torch.int64, pin_memory=True))
 
         def e2e_step():
-            dpos.copy_(host64, non_blocking=True)
-            pk, _, _ = api.power(dpos, cfg, ws=wsp)
-            pk_host.copy_(pk, non_blocking=True)
+            api.power_host(host64, cfg, ws=wsp, out=host_out, device=dev)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -461,9 +464,10 @@ def main():
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1) / ke
         result["e2e"] = {"value": n / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": 24 * n,
-                         "d2h_bytes_per_step": 8 * cfg.nb, "ms_per_step": ms_e2e,
-                         "path": "pk_power: pinned host FP64 xyz -> H2D -> prepare -> bin -> assign -> FFT -> estimate -> D2H"}
-        del wsp, dpos
+                         "d2h_bytes_per_step": 24 * cfg.nb, "ms_per_step": ms_e2e,
+                         "path": "pk_power_host: pinned host FP64 xyz read over the CPU-GPU link by the prepare+count "
+                                 "kernel -> bin -> assign -> FFT -> estimate -> D2H of P(k), kmean, counts"}
+        del wsp
         torch.cuda.empty_cache()
 
         # ---- FP64 CPU oracle on a bounded sample ---------------------------------------------------

@@ -101,7 +101,8 @@ typedef enum {
   PK_WS_BIN = 4,
   PK_WS_BACKWARD = 5,
   PK_WS_BISPECTRUM = 6,
-  PK_WS_BISPECTRUM_COUNTS = 7
+  PK_WS_BISPECTRUM_COUNTS = 7,
+  PK_WS_POWER_HOST = 8
 } pk_ws_kind;
 
 /* Fills cfg with the paper's default binning for an N grid: bins centred on b k_f, b = 1..N/2
@@ -166,6 +167,18 @@ pk_status pk_fft_estimate(const pk_config* cfg, const void* grid1_dev, const voi
 pk_status pk_power(const pk_config* cfg, const void* pos_dev, int32_t pos_format, const float* w_dev,
                    int64_t n, double* pk_dev, double* kmean_dev, int64_t* nmodes_dev, void* delta_k_dev,
                    void* ws, size_t ws_bytes, void* stream);
+
+/* a1..a6 end to end from host memory: pk_power for positions pos_host (and optional weights w_host,
+ * float[n]) in HOST memory, with P(k), kmean and the mode counts written to host memory (length
+ * nbins each). Pinned positions (cudaHostAlloc, cudaHostRegister) are read by the GPU directly over
+ * the CPU-GPU link while they are prepared and counted (the FP32 and FIXED64 modes); pageable ones
+ * are copied through the workspace in pieces; weights, and positions in the FP64 mode or the packed
+ * format, are copied to the workspace first. Asynchronous on `stream` like every call: the host
+ * outputs are valid once the stream has synchronised. Device or managed pos_host: PK_EINVAL.
+ * Workspace: pk_workspace_size(cfg, n, PK_WS_POWER_HOST). */
+pk_status pk_power_host(const pk_config* cfg, const void* pos_host, int32_t pos_format, const float* w_host,
+                        int64_t n, double* pk_host, double* kmean_host, int64_t* nmodes_host, void* ws,
+                        size_t ws_bytes, void* stream);
 
 /* Same as pk_power for a catalogue already in the binned layout of pk_bin (sorted_dev,
  * w_sorted_dev or NULL, tile_offsets_dev): the steady-state hot path when one catalogue is measured

@@ -52,9 +52,9 @@ def _stream(device=None):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
-def _pos_format(pos):
-    if not pos.is_cuda or not pos.is_contiguous():
-        raise ValueError("positions must be a contiguous CUDA tensor")
+def _pos_format(pos, on_device=True):
+    if pos.is_cuda != on_device or not pos.is_contiguous():
+        raise ValueError(f"positions must be a contiguous {'CUDA' if on_device else 'CPU'} tensor")
     if pos.dtype == torch.float64 and pos.dim() == 2 and pos.shape[1] == 3:
         return ffi.PK_POS_F64_XYZ
     if pos.dtype == torch.int32 and pos.dim() == 2 and pos.shape[1] == 4:
@@ -155,6 +155,29 @@ def power(pos, cfg, weights=None, return_delta=False, ws=None):
     check(ffi.lib().pk_power(ctypes.byref(cfg.c()), _p(pos), fmt, _p(w), n, _p(pk), _p(km), _p(nm), _p(delta), _p(ws),
                              ws.numel(), _stream(pos.device)))
     return (pk, km, nm, delta) if return_delta else (pk, km, nm)
+
+
+def power_host(pos, cfg, weights=None, ws=None, out=None, device=None):
+    """P(k) end to end from host memory (pk_power_host): pos is an (n, 3) float64 or packed (n, 4)
+    int32 CPU tensor (pinned tensors are read by the GPU directly), weights an optional float32 CPU
+    tensor; returns CPU tensors (pk, kmean, nmodes), valid after the stream has synchronised
+    (``out`` may hold pinned tensors to fill). The workspace lives on ``device``."""
+    fmt = _pos_format(pos, on_device=False)
+    device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    n = pos.shape[0]
+    if weights is not None:
+        weights = weights.to(torch.float32).contiguous()
+        if weights.is_cuda or weights.shape[0] != n:
+            raise ValueError("weights must be a CPU tensor of length n")
+    if ws is None:
+        ws = workspace(cfg, n, ffi.PK_WS_POWER_HOST, device)
+    if out is None:
+        out = (torch.empty(cfg.nb, dtype=torch.float64), torch.empty(cfg.nb, dtype=torch.float64),
+               torch.empty(cfg.nb, dtype=torch.int64))
+    pk, km, cnt = out
+    check(ffi.lib().pk_power_host(ctypes.byref(cfg.c()), _p(pos), fmt, _p(weights), n, _p(pk), _p(km), _p(cnt), _p(ws),
+                                  ws.numel(), _stream(device)))
+    return pk, km, cnt
 
 
 def power_binned(binned, cfg, return_delta=False, ws=None, out=None):

@@ -209,18 +209,36 @@ void carve_bin_stage(const pk_config* c, int64_t n, bool need_cells, Carver& cv,
   b->scan = cv.take<long long>(scan_scratch_bytes(nkeys) / sizeof(long long) + 1);
 }
 
-// Positions in either format -> binned layout (sorted, wsorted, offsets).
+// Positions in either format -> binned layout (sorted, wsorted, offsets). FP64 positions are prepared
+// and counted in one sweep; `pos` is device-accessible (device memory or mapped pinned host memory),
+// or, with `stage`, pageable host memory copied through stage->buf in pieces of stage->cap particles.
 pk_status run_bin(const pk_config* c, const void* pos, int fmt, const float* w, int64_t n, BinStage& b, pk_cellpos* sorted,
-                  float* wsorted, int64_t* offsets, cudaStream_t s) {
-  const pk_cellpos* cells = static_cast<const pk_cellpos*>(pos);
-  cudaError_t e;
-  if (fmt == PK_POS_F64_XYZ) {
-    if ((e = launch_prepare(static_cast<const double*>(pos), n, c->ng, c->box, b.cells, s)) != cudaSuccess)
-      return cuda_fail(e, "prepare");
-    cells = b.cells;
-  }
+                  float* wsorted, int64_t* offsets, cudaStream_t s, const HostStage* stage) {
   const int nt = tiles_per_axis(c->ng);
-  if ((e = launch_bin(cells, w, n, c->ng, nt, sorted, wsorted, offsets, b.counts, b.sub, b.scan, s)) != cudaSuccess)
+  cudaError_t e;
+  if (fmt != PK_POS_F64_XYZ) {
+    if ((e = launch_bin(static_cast<const pk_cellpos*>(pos), w, n, c->ng, nt, sorted, wsorted, offsets, b.counts, b.sub,
+                        b.scan, s)) != cudaSuccess)
+      return cuda_fail(e, "bin");
+    return PK_OK;
+  }
+  const size_t nkeys = size_t(nt) * nt * nt * kSlabs;
+  if ((e = cudaMemsetAsync(b.counts, 0, nkeys * sizeof(unsigned long long), s)) != cudaSuccess) return cuda_fail(e, "memset");
+  const double* p = static_cast<const double*>(pos);
+  if (!stage) {
+    if ((e = launch_prepare_hist(p, 0, n, c->ng, c->box, nt, b.cells, b.counts, s)) != cudaSuccess)
+      return cuda_fail(e, "prepare");
+  } else {
+    for (int64_t i0 = 0; i0 < n; i0 += stage->cap) {
+      const int64_t cnt = std::min<int64_t>(stage->cap, n - i0);
+      if ((e = cudaMemcpyAsync(stage->buf, p + 3 * i0, size_t(cnt) * 3 * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+        return cuda_fail(e, "copy positions");
+      if ((e = launch_prepare_hist(stage->buf, i0, cnt, c->ng, c->box, nt, b.cells, b.counts, s)) != cudaSuccess)
+        return cuda_fail(e, "prepare");
+    }
+  }
+  if ((e = launch_bin_finish(b.cells, w, n, c->ng, nt, sorted, wsorted, offsets, b.counts, b.sub, b.scan, s)) != cudaSuccess)
     return cuda_fail(e, "bin");
   return PK_OK;
 }
@@ -275,9 +293,25 @@ pk_status carve_forward(const pk_config* c, int64_t n, Carver& cv, ForwardStage*
   return PK_OK;
 }
 
+// Workspace of pk_power_host: the forward stage, device copies of the weights (and, in FP64 mode, of
+// the positions), the staging buffer for pageable positions and the device outputs.
+constexpr int64_t kHostStageParticles = int64_t(1) << 22;
+pk_status carve_host(const pk_config* c, int64_t n, Carver& cv, HostLayout* h) {
+  pk_status st = carve_forward(c, n, cv, &h->f);
+  if (st != PK_OK) return st;
+  h->w = cv.take<float>(size_t(std::max<int64_t>(n, 1)));
+  h->stage_cap = std::max<int64_t>(1, std::min<int64_t>(n, kHostStageParticles));
+  h->stage = cv.take<double>(size_t(3 * h->stage_cap));
+  h->pos = c->prec == PK_FP64 ? cv.take<double>(size_t(3 * std::max<int64_t>(n, 1))) : nullptr;
+  h->pk = cv.take<double>(size_t(c->nbins));
+  h->kmean = cv.take<double>(size_t(c->nbins));
+  h->nmodes = cv.take<int64_t>(size_t(c->nbins));
+  return PK_OK;
+}
+
 // Weight sums, binning (FP32/FIXED64) and assignment into the padded grids of f.g (not transformed).
 pk_status run_forward_grids(const pk_config* c, const void* pos, int fmt, const float* w, int64_t n, ForwardStage& f,
-                            cudaStream_t s) {
+                            cudaStream_t s, const HostStage* stage) {
   prof_mark(0, s);
   pk_status st = run_weight_sums(w, n, f.g.wsums, s);
   if (st != PK_OK) return st;
@@ -285,7 +319,7 @@ pk_status run_forward_grids(const pk_config* c, const void* pos, int fmt, const 
     prof_mark(1, s);
     return run_assign_into(c, pos, fmt, nullptr, w, nullptr, n, f.g.wsums, f.g.grids, c->ng + 2, s);
   }
-  if ((st = run_bin(c, pos, fmt, w, n, f.b, f.sorted, w ? f.wsorted : nullptr, f.offsets, s)) != PK_OK) return st;
+  if ((st = run_bin(c, pos, fmt, w, n, f.b, f.sorted, w ? f.wsorted : nullptr, f.offsets, s, stage)) != PK_OK) return st;
   prof_mark(1, s);
   return run_assign_into(c, nullptr, PK_POS_CELL_F32OFF, f.sorted, w ? f.wsorted : nullptr, f.offsets, n, f.g.wsums,
                          f.g.grids, c->ng + 2, s);
@@ -393,6 +427,11 @@ size_t pk_workspace_size(const pk_config* cfg, int64_t n, int32_t kind) {
     case PK_WS_BIN: {
       BinStage b;
       carve_bin_stage(cfg, n, true, cv, &b);
+      return cv.size();
+    }
+    case PK_WS_POWER_HOST: {
+      HostLayout h;
+      if (carve_host(cfg, n, cv, &h) != PK_OK) return 0;
       return cv.size();
     }
     case PK_WS_BACKWARD:
@@ -536,6 +575,62 @@ pk_status pk_power(const pk_config* cfg, const void* pos_dev, int32_t pos_format
   if ((st = carve_forward(cfg, n, cv, &f)) != PK_OK) return st;
   if ((st = run_forward_grids(cfg, pos_dev, pos_format, w_dev, n, f, s)) != PK_OK) return st;
   return run_fft_estimate(cfg, f.g, delta_k_dev, pk_dev, kmean_dev, nmodes_dev, s);
+}
+
+pk_status pk_power_host(const pk_config* cfg, const void* pos_host, int32_t pos_format, const float* w_host, int64_t n,
+                        double* pk_host, double* kmean_host, int64_t* nmodes_host, void* ws, size_t ws_bytes, void* stream) {
+  clear_err();
+  pk_status st = validate(cfg);
+  if (st != PK_OK) return st;
+  if (pos_format != PK_POS_F64_XYZ && pos_format != PK_POS_CELL_F32OFF) return fail(PK_EINVAL, "bad pos_format");
+  if (n < 1 || !pos_host) return fail(PK_EINVAL, "need at least one particle");
+  if (!pk_host || !kmean_host || !nmodes_host) return fail(PK_EINVAL, "pk, kmean and nmodes outputs are required");
+  const size_t need = pk_workspace_size(cfg, n, PK_WS_POWER_HOST);
+  if (!ws || ws_bytes < need) return fail(PK_ESIZE, "workspace %zu < %zu bytes", ws_bytes, need);
+  // where the positions live: pinned host memory is read through its device mapping; device or
+  // managed memory belongs to pk_power
+  cudaPointerAttributes attr;
+  const void* mapped = nullptr;
+  if (cudaPointerGetAttributes(&attr, pos_host) == cudaSuccess) {
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)
+      return fail(PK_EINVAL, "pos_host is device memory: use pk_power");
+    if (attr.type == cudaMemoryTypeHost) mapped = attr.devicePointer;
+  } else {
+    (void)cudaGetLastError();  // not known to CUDA: pageable host memory
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carver cv(ws);
+  HostLayout h;
+  if ((st = carve_host(cfg, n, cv, &h)) != PK_OK) return st;
+  cudaError_t e;
+  const float* w = nullptr;
+  if (w_host) {
+    if ((e = cudaMemcpyAsync(h.w, w_host, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "copy weights");
+    w = h.w;
+  }
+  const size_t rec = pos_format == PK_POS_F64_XYZ ? 3 * sizeof(double) : sizeof(pk_cellpos);
+  if (cfg->prec == PK_FP64 || pos_format != PK_POS_F64_XYZ) {  // copy the positions to the device first
+    void* dst = cfg->prec == PK_FP64 ? static_cast<void*>(h.pos) : static_cast<void*>(h.f.b.cells);
+    if ((e = cudaMemcpyAsync(dst, pos_host, size_t(n) * rec, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "copy positions");
+    st = run_forward_grids(cfg, dst, pos_format, w, n, h.f, s);
+  } else if (mapped) {  // read over the CPU-GPU link while being prepared and counted
+    st = run_forward_grids(cfg, mapped, pos_format, w, n, h.f, s);
+  } else {
+    HostStage stage;
+    stage.buf = h.stage;
+    stage.cap = h.stage_cap;
+    st = run_forward_grids(cfg, pos_host, pos_format, w, n, h.f, s, &stage);
+  }
+  if (st != PK_OK) return st;
+  if ((st = run_fft_estimate(cfg, h.f.g, nullptr, h.pk, h.kmean, h.nmodes, s)) != PK_OK) return st;
+  const size_t nb = size_t(cfg->nbins);
+  if ((e = cudaMemcpyAsync(pk_host, h.pk, nb * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(kmean_host, h.kmean, nb * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(nmodes_host, h.nmodes, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "copy results");
+  return PK_OK;
 }
 
 pk_status pk_power_binned(const pk_config* cfg, const pk_cellpos* sorted_dev, const float* w_sorted_dev,

@@ -65,8 +65,13 @@ struct BinStage {
   long long* scan = nullptr;
 };
 void carve_bin_stage(const pk_config* c, int64_t n, bool need_cells, Carver& cv, BinStage* b);
+// Pageable host FP64 positions are copied through buf (cap particles at a time).
+struct HostStage {
+  double* buf = nullptr;
+  int64_t cap = 0;
+};
 pk_status run_bin(const pk_config* c, const void* pos, int fmt, const float* w, int64_t n, BinStage& b, pk_cellpos* sorted,
-                  float* wsorted, int64_t* offsets, cudaStream_t s);
+                  float* wsorted, int64_t* offsets, cudaStream_t s, const HostStage* stage = nullptr);
 pk_status run_weight_sums(const float* w, int64_t n, double* sums, cudaStream_t s);
 pk_status run_assign_into(const pk_config* c, const void* pos, int fmt, const pk_cellpos* sorted, const float* w,
                           const int64_t* offsets, int64_t n, const double* wsums, void* grids, int ldz, cudaStream_t s);
@@ -82,7 +87,19 @@ struct ForwardStage {
 };
 pk_status carve_forward(const pk_config* c, int64_t n, Carver& cv, ForwardStage* f);
 pk_status run_forward_grids(const pk_config* c, const void* pos, int fmt, const float* w, int64_t n, ForwardStage& f,
-                            cudaStream_t s);
+                            cudaStream_t s, const HostStage* stage = nullptr);
+
+struct HostLayout {
+  ForwardStage f;
+  float* w = nullptr;
+  double* stage = nullptr;
+  int64_t stage_cap = 0;
+  double* pos = nullptr;
+  double* pk = nullptr;
+  double* kmean = nullptr;
+  int64_t* nmodes = nullptr;
+};
+pk_status carve_host(const pk_config* c, int64_t n, Carver& cv, HostLayout* h);
 
 // Optional stage timing (pk_profile_enable / pk_profile_read): prof_mark(k, s) records event k on s
 // when profiling is on. Marks: 0 start, 1 before the grid clear, 2 before the assignment kernel,

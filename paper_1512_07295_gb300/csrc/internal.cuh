@@ -33,6 +33,13 @@ cudaError_t launch_exclusive_scan(const unsigned long long* in, int64_t n, int64
 cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int ntile, pk_cellpos* sorted,
                        float* wsorted, int64_t* offsets, unsigned long long* counts, int64_t* sub, long long* scan_scratch,
                        cudaStream_t s);
+// FP64 positions pos[0 .. cnt) -> cells[i0 .. i0 + cnt), keys counted into counts (cleared by the caller).
+cudaError_t launch_prepare_hist(const double* pos, int64_t i0, int64_t cnt, int ng, double box, int ntile, pk_cellpos* cells,
+                                unsigned long long* counts, cudaStream_t s);
+// Scan of the counted keys, tile offsets and scatter of cells (and weights) into the binned layout.
+cudaError_t launch_bin_finish(const pk_cellpos* cells, const float* w, int64_t n, int ng, int ntile, pk_cellpos* sorted,
+                              float* wsorted, int64_t* offsets, unsigned long long* counts, int64_t* sub,
+                              long long* scan_scratch, cudaStream_t s);
 
 constexpr int kMaxBatch = 128;
 struct CatRanges {  // particle ranges of the catalogues of one batch group (absolute indices)

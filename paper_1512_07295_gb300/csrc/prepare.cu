@@ -115,6 +115,24 @@ __global__ void k_tile_scatter(const pk_cellpos* __restrict__ p, const float* __
   }
 }
 
+// a1 and the counting pass of a2 in one sweep over FP64 positions pos[0 .. cnt) (device memory, or
+// pinned host memory read over the CPU-GPU link): each particle is prepared, written to out[i0 + k]
+// and its sort key counted.
+__global__ void k_prepare_hist(const double* __restrict__ pos, int64_t i0, int64_t cnt, int ng, double box, int ntile,
+                               pk_cellpos* __restrict__ out, unsigned long long* __restrict__ counts) {
+  const double scale = double(ng) / box;
+  const int64_t nround = (cnt + 31) / 32 * 32;
+  for (int64_t k = gtid(); k < nround; k += gstride()) {
+    const bool live = k < cnt;
+    const unsigned active = __ballot_sync(0xffffffffu, live);
+    if (live) {
+      const pk_cellpos r = prepare_one(pos + 3 * k, ng, box, scale);
+      out[i0 + k] = r;
+      agg_inc(counts, bin_key(r, ntile), active);
+    }
+  }
+}
+
 // Tile offsets from the slab offsets: offsets[t] = sub[t * kSlabs], t = 0 .. ntiles.
 __global__ void k_tile_offsets(const int64_t* __restrict__ sub, int64_t ntiles, int64_t* __restrict__ offsets) {
   for (int64_t t = gtid(); t <= ntiles; t += gstride()) offsets[t] = sub[t * kSlabs];
@@ -242,10 +260,19 @@ static cudaError_t launch_tile_offsets(const int64_t* sub, int64_t ntiles, int64
   return cudaGetLastError();
 }
 
+cudaError_t launch_prepare_hist(const double* pos, int64_t i0, int64_t cnt, int ng, double box, int ntile, pk_cellpos* cells,
+                                unsigned long long* counts, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((cnt + threads - 1) / threads, int64_t(num_sms()) * 16);
+  k_prepare_hist<<<int(blocks), threads, 0, s>>>(pos, i0, cnt, ng, box, ntile, cells, counts); count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int ng, int ntile, pk_cellpos* sorted,
                        float* wsorted, int64_t* offsets, unsigned long long* counts, int64_t* sub, long long* scan_scratch,
                        cudaStream_t s) {
-  const int64_t ntiles = int64_t(ntile) * ntile * ntile, nkeys = ntiles * kSlabs;
+  const int64_t nkeys = int64_t(ntile) * ntile * ntile * kSlabs;
   cudaError_t e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int threads = 256;
@@ -254,6 +281,16 @@ cudaError_t launch_bin(const pk_cellpos* cells, const float* w, int64_t n, int n
     k_tile_hist<<<int(blocks), threads, 0, s>>>(cells, n, ng, ntile, counts); count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return launch_bin_finish(cells, w, n, ng, ntile, sorted, wsorted, offsets, counts, sub, scan_scratch, s);
+}
+
+cudaError_t launch_bin_finish(const pk_cellpos* cells, const float* w, int64_t n, int ng, int ntile, pk_cellpos* sorted,
+                              float* wsorted, int64_t* offsets, unsigned long long* counts, int64_t* sub,
+                              long long* scan_scratch, cudaStream_t s) {
+  const int64_t ntiles = int64_t(ntile) * ntile * ntile, nkeys = ntiles * kSlabs;
+  const int threads = 256;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, int64_t(num_sms()) * 16));
+  cudaError_t e;
   if ((e = launch_exclusive_scan(counts, nkeys, sub, scan_scratch, s)) != cudaSuccess) return e;
   if ((e = launch_tile_offsets(sub, ntiles, offsets, s)) != cudaSuccess) return e;
   if (n > 0) {
