@@ -448,6 +448,100 @@ __device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
+// Adds a tile's node regions (origin: node (cx0-1, cy0-1, cz0-1); grid gi at reg + gi RVOL),
+// converted back from fixed point, to the grids; node pairs whose global z index is even are added
+// with one 8-byte vector reduction.
+__device__ __forceinline__ void flush_region(const int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
+                                             float inv_scale, float* g1, float* g2, int tid, int nthreads) {
+  for (int i = tid; i < ngrid * RS * RS * 7; i += nthreads) {
+    const int row = i / 7, item = i - row * 7;
+    const int gi = row / (RS * RS), rr = row - gi * (RS * RS);
+    const int rx = rr / RS, ry = rr - rx * RS;
+    const int* src = reg + gi * RVOL + (rx * RS + ry) * RS;
+    float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
+    if (item == 0 || item == 6) {
+      const int rz = item == 0 ? 0 : RS - 1;
+      const float v = float(src[rz]) * inv_scale;
+      if (v != 0.0f) atomicAdd(gg + wrap(cz0 - 1 + rz, ng), v);
+    } else {
+      const int rz = 2 * item - 1;  // odd: the global z index cz0 - 1 + rz is even
+      const float v0 = float(src[rz]) * inv_scale, v1 = float(src[rz + 1]) * inv_scale;
+      if (v0 != 0.0f || v1 != 0.0f) {
+        const int z = wrap(cz0 - 1 + rz, ng);
+        float* dst = gg + z;
+        if (z + 1 < ng && (reinterpret_cast<uintptr_t>(dst) & 7u) == 0) {
+          asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(v0), "f"(v1) : "memory");
+        } else {
+          atomicAdd(dst, v0);
+          atomicAdd(gg + wrap(z + 1, ng), v1);
+        }
+      }
+    }
+  }
+}
+
+// Fixed-point scale 2^e of a tile's region: no node (nor any partial sum of one) exceeds the tile's
+// total |weight| B, and B 2^e < 2^30 leaves room for the rounding of every addition. With weights,
+// B is summed by the block (red: one float per warp); the caller synchronises before the first use.
+template <bool W>
+__device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t end, float* red, int nwarp, int tid,
+                                           int nthreads, float* scale, float* inv_scale) {
+  float bound = float(end - beg);
+  if (W) {
+    float a = 0.0f;
+    for (int64_t i = beg + tid; i < end; i += nthreads) a += fabsf(w[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((tid & 31) == 0) red[tid >> 5] = a;
+    __syncthreads();
+    bound = 0.0f;
+    for (int q = 0; q < nwarp; ++q) bound += red[q];
+    bound *= 1.0001f;  // the FP32 sum's rounding
+  }
+  int ex;
+  frexpf(fmaxf(bound, 1.0f), &ex);  // bound < 2^ex
+  *scale = ldexpf(1.0f, 30 - ex);
+  *inv_scale = ldexpf(1.0f, ex - 30);
+}
+
+// ---- direct scatter (sparse tiles) ------------------------------------------------------------------
+// A walk pays for every x step of every key column of a tile whether or not its buckets hold
+// particles; on sparse tiles that fixed cost dominates. There, each thread adds its particles' p^3
+// weights per grid straight into the fixed-point region with integer shared atomics instead.
+constexpr int SCATTER_THREADS = 256;
+
+template <bool W>
+struct ScatterSmem {
+  int4 sp[chunk<W>()];
+  int reg[2][RVOL];
+  float red[SCATTER_THREADS / 32];
+  unsigned long long mbar;
+  float sw[W ? chunk<W>() : 1];
+};
+
+// Adds one particle's p^3 weights on grid G to that grid's region (scale: the weight times the
+// region's fixed-point scale). Region nodes of the stencil: key + S0 + 1 .. key + S0 + p per axis.
+template <int P, int G>
+__device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc) {
+  float tx, ty, tz;
+  const int kx = lx + grid_key<P, G>(fx, &tx), ky = ly + grid_key<P, G>(fy, &ty), kz = lz + grid_key<P, G>(fz, &tz);
+  float wx[P], wy[P], wz[P];
+  weights<P>(tx, wx);
+  weights<P>(ty, wy);
+  weights<P>(tz, wz);
+#pragma unroll
+  for (int a = 0; a < P; ++a) wx[a] *= sc;
+  int* base = reg + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
+#pragma unroll
+  for (int a = 0; a < P; ++a)
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      const float xy = wx[a] * wy[b];
+#pragma unroll
+      for (int c = 0; c < P; ++c) atomicAdd(base + (a * RS + b) * RS + c, __float2int_rn(xy * wz[c]));
+    }
+}
+
 }  // namespace walk
 
 template <int P, bool W>
@@ -484,23 +578,8 @@ __global__ void __launch_bounds__(walk::threads<P>(), 3)
     const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
     for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
-    // fixed-point scale 2^e of the region: no node (nor any partial sum of one) exceeds the tile's
-    // total |weight| B, and B 2^e < 2^30 leaves room for the rounding of every addition
-    float bound = float(end - beg);
-    if (W) {
-      float a = 0.0f;
-      for (int64_t i = beg + tid; i < end; i += THREADS) a += fabsf(w[i]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane == 0) S.red[warp] = a;
-      __syncthreads();
-      bound = 0.0f;
-      for (int q = 0; q < NWARP; ++q) bound += S.red[q];
-      bound *= 1.0001f;  // the FP32 sum's rounding
-    }
-    int ex;
-    frexpf(fmaxf(bound, 1.0f), &ex);  // bound < 2^ex
-    const float scale = ldexpf(1.0f, 30 - ex), inv_scale = ldexpf(1.0f, ex - 30);
+    float scale, inv_scale;
+    tile_scale<W>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
     for (int64_t c0 = beg; c0 < end; c0 += CH) {
       const int m = int(min(int64_t(CH), end - c0));
       // stage the chunk with one bulk copy (16-byte records, 16-byte aligned)
@@ -621,35 +700,107 @@ __global__ void __launch_bounds__(walk::threads<P>(), 3)
         walk_range<P, 1, W>(S, wk, last, warp - NW0, lane, scale);
       __syncthreads();
     }
-    // add the tile's region (origin: node (cx0-1, cy0-1, cz0-1)), converted back from fixed point, to
-    // the grids; node pairs whose global z index is even are added with one 8-byte vector reduction
-    for (int i = tid; i < ngrid * RS * RS * 7; i += THREADS) {
-      const int row = i / 7, item = i - row * 7;
-      const int gi = row / (RS * RS), rr = row - gi * (RS * RS);
-      const int rx = rr / RS, ry = rr - rx * RS;
-      const int* src = &S.reg[gi][(rx * RS + ry) * RS];
-      float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
-      if (item == 0 || item == 6) {
-        const int rz = item == 0 ? 0 : RS - 1;
-        const float v = float(src[rz]) * inv_scale;
-        if (v != 0.0f) atomicAdd(gg + wrap(cz0 - 1 + rz, ng), v);
-      } else {
-        const int rz = 2 * item - 1;  // odd: the global z index cz0 - 1 + rz is even
-        const float v0 = float(src[rz]) * inv_scale, v1 = float(src[rz + 1]) * inv_scale;
-        if (v0 != 0.0f || v1 != 0.0f) {
-          const int z = wrap(cz0 - 1 + rz, ng);
-          float* dst = gg + z;
-          if (z + 1 < ng && (reinterpret_cast<uintptr_t>(dst) & 7u) == 0) {
-            asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(v0), "f"(v1) : "memory");
-          } else {
-            atomicAdd(dst, v0);
-            atomicAdd(gg + wrap(z + 1, ng), v1);
-          }
-        }
-      }
-    }
+    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
     __syncthreads();
   }
+}
+
+// a3, FP32, direct scatter: block per tile, pieces staged like the walk's, particles spread over the
+// lanes of a warp q = ceil(m / 32) records apart (different cells, so a warp's atomics seldom meet on
+// one node), fixed-point regions flushed to the grids as in k_assign_walk.
+template <int P, bool W>
+__global__ void __launch_bounds__(walk::SCATTER_THREADS, 4)
+    k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
+                     int64_t n, int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
+                     int64_t cat_stride) {
+  using namespace walk;
+  constexpr int CH = chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
+  {
+    const int cat = blockIdx.y;
+    g1 += cat * cat_stride;
+    if (g2) g2 += cat * cat_stride;
+    toff += int64_t(cat) * ntile * ntile * ntile;
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ScatterSmem<W>& S = *reinterpret_cast<ScatterSmem<W>*>(smem_raw);
+  const int ngrid = interlace ? 2 : 1;
+  const int ntiles = ntile * ntile * ntile;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  }
+  __syncthreads();
+  unsigned parity = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
+    if (beg >= end) continue;
+    const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
+    const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;
+    for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
+    float scale, inv_scale;
+    tile_scale<W>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+    for (int64_t c0 = beg; c0 < end; c0 += CH) {
+      const int m = int(min(int64_t(CH), end - c0));
+      if (tid == 0) bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
+      if (W)
+        for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
+      const bool arrived = bulk_wait(&S.mbar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!arrived)) {  // the copy did not complete: report, drain, stop
+        if (tid == 0) {
+          raise_err(PK_DERR_TIMEOUT);
+          bulk_wait(&S.mbar, parity ^ 1u);
+        }
+        return;
+      }
+      const int q = (m + 31) / 32;
+      for (int i = tid; i < 32 * q; i += THREADS) {
+        const int j = (i & 31) * q + (i >> 5);
+        if (j >= m) continue;
+        const int4 r = S.sp[j];
+        const uint32_t cell = uint32_t(r.x);
+        const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
+        if ((cell >> 30) != 0 || unsigned(lx) >= unsigned(T) || unsigned(ly) >= unsigned(T) || unsigned(lz) >= unsigned(T)) {
+          raise_err(PK_DERR_CELLRANGE);
+          continue;
+        }
+        const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
+        const float sc = (W ? S.sw[j] : 1.0f) * weight_scale<P>() * scale;
+        scatter_particle<P, 0>(S.reg[0], lx, ly, lz, fx, fy, fz, sc);
+        if (interlace) scatter_particle<P, 1>(S.reg[1], lx, ly, lz, fx, fy, fz, sc);
+      }
+      __syncthreads();
+    }
+    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
+    __syncthreads();
+  }
+}
+
+// Mean particles per tile below which the direct scatter replaces the walk. Measured per tile on one
+// GB300: the walk costs about 73 ns + 0.018 ns per particle of block time, the scatter 19 ns + 0.048 ns,
+// so they cross near 1800 particles per tile (8^3 cells).
+constexpr int64_t kScatterMaxMean = 1536;
+
+template <int P, bool W>
+static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
+                                     int64_t cat_stride) {
+  const int ntile = tiles_per_axis(ng);
+  const int ntiles = ntile * ntile * ntile;
+  const size_t smem = sizeof(walk::ScatterSmem<W>);
+  cudaError_t e = cudaFuncSetAttribute(k_assign_scatter<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assign_scatter<P, W>, walk::SCATTER_THREADS, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
+  k_assign_scatter<P, W><<<blocks, walk::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
+                                                                     cat_stride);
+  count_launch();
+  return cudaGetLastError();
 }
 
 template <int P, bool W>
@@ -657,6 +808,8 @@ static cudaError_t launch_walk_pw(const pk_cellpos* p, const float* w, const int
                                   float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
+  if (n < kScatterMaxMean * int64_t(ntiles) * ncat)  // sparse tiles: the direct scatter
+    return launch_scatter_pw<P, W>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
   const size_t smem = sizeof(walk::Smem<W>);
   cudaError_t e = cudaFuncSetAttribute(k_assign_walk<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
