@@ -78,35 +78,121 @@ __global__ void k_shell_indicator(double2* __restrict__ out, int ng, int lo, int
   }
 }
 
-constexpr int kTX = 128;  // x points per staged tile
+constexpr int kTX = 128;       // x points per staged tile
+constexpr int kRow = kTX + 1;  // padded row of a staged field: shells in different banks
 
-// S_t += sum_x I_a(x) I_b(x) I_c(x) over all triangles; fields in the padded real layout.
+// Stages the tile's values of every field: vals[s][k] = I_s(tile * kTX + k) (0 past the grid).
+template <typename R>
+__device__ __forceinline__ void stage_fields(R* vals, const R* __restrict__ fields, int ng, int nshells, int64_t buf_stride,
+                                             int64_t tile, int64_t npts) {
+  for (int i = threadIdx.x; i < nshells * kTX; i += blockDim.x) {
+    const int s = i / kTX, k = i - s * kTX;
+    const int64_t x = tile * kTX + k;
+    R v = R(0);
+    if (x < npts) {
+      const int64_t row = x / ng;
+      v = fields[s * buf_stride + row * (ng + 2) + (x - row * ng)];
+    }
+    vals[s * kRow + k] = v;
+  }
+}
+
+// The triple product with lanes over points: warp w owns a contiguous run of at most kWarpTri
+// triangles (a, b, c) for the whole kernel and keeps one running sum per triangle in each lane. Per
+// staged tile, lane l takes the points l, l + 32, l + 64, l + 96; the products I_a I_b of those points
+// are reloaded only when the pair (a, b) changes (consecutive triangles share it), and every load is a
+// conflict-free row segment. Every kFlushTiles tiles the FP32 lane sums are reduced across the warp
+// into FP64 per-block sums, which are added to S at the end.
+constexpr int kWarpTri = 32;
+constexpr int kTriWarps = 16;
+constexpr int kFlushTiles = 16;
+
+template <typename R>
+__global__ void __launch_bounds__(kTriWarps * 32) k_triple_warp(const R* __restrict__ fields, int ng, int nshells,
+                                                               int64_t buf_stride, const int* __restrict__ tri_g, int ntri,
+                                                               double* __restrict__ S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sblk = reinterpret_cast<double*>(smem_raw);           // [ntri]
+  int* tri = reinterpret_cast<int*>(sblk + ntri);                // [3 ntri]
+  R* vals = reinterpret_cast<R*>(tri + ((3 * ntri + 3) / 4) * 4);  // [nshells][kRow]
+  for (int t = threadIdx.x; t < ntri; t += blockDim.x) sblk[t] = 0.0;
+  for (int t = threadIdx.x; t < 3 * ntri; t += blockDim.x) tri[t] = tri_g[t];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (ntri + kTriWarps - 1) / kTriWarps;  // <= kWarpTri (checked by the launcher)
+  const int t_beg = warp * per, t_cnt = max(0, min(per, ntri - t_beg));
+  R acc[kWarpTri];
+#pragma unroll
+  for (int j = 0; j < kWarpTri; ++j) acc[j] = R(0);
+  const int64_t npts = int64_t(ng) * ng * ng;
+  const int64_t ntiles = (npts + kTX - 1) / kTX;
+  int since_flush = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();
+    stage_fields(vals, fields, ng, nshells, buf_stride, tile, npts);
+    __syncthreads();
+    int pa = -1, pb = -1;
+    R pab[kTX / 32];
+#pragma unroll
+    for (int j = 0; j < kWarpTri; ++j) {
+      if (j < t_cnt) {
+        const int t = t_beg + j;
+        const int a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+        if (a != pa || b != pb) {  // warp-uniform
+          pa = a;
+          pb = b;
+#pragma unroll
+          for (int i = 0; i < kTX / 32; ++i) pab[i] = vals[a * kRow + lane + 32 * i] * vals[b * kRow + lane + 32 * i];
+        }
+        R sum = acc[j];
+#pragma unroll
+        for (int i = 0; i < kTX / 32; ++i) sum += pab[i] * vals[c * kRow + lane + 32 * i];
+        acc[j] = sum;
+      }
+    }
+    if (++since_flush == kFlushTiles) {
+      since_flush = 0;
+#pragma unroll
+      for (int j = 0; j < kWarpTri; ++j) {
+        if (j < t_cnt) {
+          double v = double(acc[j]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) sblk[t_beg + j] += v;
+        }
+        acc[j] = R(0);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kWarpTri; ++j) {
+    if (j < t_cnt) {
+      double v = double(acc[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sblk[t_beg + j] += v;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntri; t += blockDim.x) atomicAdd(&S[t], sblk[t]);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(512) k_triple(const R* __restrict__ fields, int ng, int nshells, int64_t buf_stride,
                                                const int* __restrict__ tri, int ntri, double* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* vals = reinterpret_cast<R*>(smem_raw);  // [nshells][kTX]
-  double* sblk = reinterpret_cast<double*>(smem_raw + size_t(nshells) * kTX * sizeof(R));
+  double* sblk = reinterpret_cast<double*>(smem_raw);  // [ntri]
+  R* vals = reinterpret_cast<R*>(smem_raw + size_t(ntri) * sizeof(double));  // [nshells][kRow]
   for (int t = threadIdx.x; t < ntri; t += blockDim.x) sblk[t] = 0.0;
   const int64_t npts = int64_t(ng) * ng * ng;
   const int64_t ntiles = (npts + kTX - 1) / kTX;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    for (int i = threadIdx.x; i < nshells * kTX; i += blockDim.x) {
-      const int s = i / kTX, k = i - s * kTX;
-      const int64_t x = tile * kTX + k;
-      R v = R(0);
-      if (x < npts) {
-        const int64_t row = x / ng;
-        v = fields[s * buf_stride + row * (ng + 2) + (x - row * ng)];
-      }
-      vals[i] = v;
-    }
+    stage_fields(vals, fields, ng, nshells, buf_stride, tile, npts);
     __syncthreads();
     for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
-      const R* va = vals + tri[3 * t] * kTX;
-      const R* vb = vals + tri[3 * t + 1] * kTX;
-      const R* vc = vals + tri[3 * t + 2] * kTX;
+      const R* va = vals + tri[3 * t] * kRow;
+      const R* vb = vals + tri[3 * t + 1] * kRow;
+      const R* vc = vals + tri[3 * t + 2] * kRow;
       R acc = R(0);
 #pragma unroll 8
       for (int k = 0; k < kTX; ++k) acc += va[k] * vb[k] * vc[k];
@@ -333,7 +419,34 @@ pk_status pk_bispectrum(const pk_config* cfg, const void* delta_k_dev, int32_t s
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "shell filter");
   if ((st = exec_plan(L.plan, L.kind, L.fields, L.work, s)) != PK_OK) return st;
   if ((e = cudaMemsetAsync(L.S, 0, sizeof(double) * ntri, s)) != cudaSuccess) return cuda_fail(e, "memset");
-  const size_t smem = size_t(nshells) * kTX * (dbl ? 8 : 4) + size_t(ntri) * 8;
+  if (ntri <= kTriWarps * kWarpTri) {  // lanes over points, warps over triangles
+    const size_t wsmem = size_t(ntri) * 8 + size_t((3 * ntri + 3) / 4) * 16 + size_t(nshells) * kRow * (dbl ? 8 : 4);
+    int per_sm = 1;
+    if (dbl) {
+      if ((e = cudaFuncSetAttribute(k_triple_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wsmem))) != cudaSuccess)
+        return cuda_fail(e, "triple smem");
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_warp<double>, kTriWarps * 32, wsmem) != cudaSuccess)
+        per_sm = 1;
+      k_triple_warp<double><<<num_sms() * std::max(per_sm, 1), kTriWarps * 32, wsmem, s>>>(
+          static_cast<const double*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S);
+    } else {
+      if ((e = cudaFuncSetAttribute(k_triple_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wsmem))) != cudaSuccess)
+        return cuda_fail(e, "triple smem");
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_warp<float>, kTriWarps * 32, wsmem) != cudaSuccess)
+        per_sm = 1;
+      k_triple_warp<float><<<num_sms() * std::max(per_sm, 1), kTriWarps * 32, wsmem, s>>>(
+          static_cast<const float*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S);
+    }
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "triple product");
+    const double vol = cfg->box * cfg->box * cfg->box;
+    const double scale = vol * vol / (double(ng) * ng * ng);
+    k_bisp_final<<<(ntri + 255) / 256, 256, 0, s>>>(L.S, reinterpret_cast<const long long*>(counts_dev), ntri, scale, B_dev);
+    count_launch();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PK_OK : cuda_fail(e, "bispectrum final");
+  }
+  const size_t smem = size_t(nshells) * kRow * (dbl ? 8 : 4) + size_t(ntri) * 8;
   if (smem > 48 * 1024) {
     e = dbl ? cudaFuncSetAttribute(k_triple<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
             : cudaFuncSetAttribute(k_triple<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -60,6 +60,32 @@ __device__ __forceinline__ int bin_of(long long v4, int lo2, int w2, int nbins) 
   return b < nbins ? b : -1;
 }
 
+// Per-warp private bin accumulators (single pass, non-deterministic mode). Within one warp item the
+// bins of the run ends are distinct (|n| grows with i_z), so a warp updates its own copy without
+// atomics: FP32 mode keeps each sum as an FP32 pair (value, compensation; Neumaier's summation,
+// every term is >= 0), FP64 mode as one double.
+template <typename R>
+struct PrivBin;
+template <>
+struct PrivBin<float> {
+  float2 sum, k;
+  __device__ __forceinline__ static void add(float2& acc, float v) {
+    const float t = acc.x + v;
+    acc.y += (fmaxf(acc.x, v) - t) + fminf(acc.x, v);
+    acc.x = t;
+  }
+  __device__ __forceinline__ static double value(float2 acc) { return double(acc.x) + double(acc.y); }
+  __device__ __forceinline__ static float2 zero() { return make_float2(0.0f, 0.0f); }
+};
+template <>
+struct PrivBin<double> {
+  double sum, k;
+  __device__ __forceinline__ static void add(double& acc, double v) { acc += v; }
+  __device__ __forceinline__ static double value(double acc) { return acc; }
+  __device__ __forceinline__ static double zero() { return 0.0; }
+};
+constexpr int kEstWarps = 8;  // 256 threads
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, const C2<R>* __restrict__ G2,
                                                   const R* __restrict__ tab_g, EstimateArgs a) {
@@ -75,14 +101,25 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
   }
   const int ng = a.ng;
   R* tab = reinterpret_cast<R*>(smem_raw);  // 3 ng
-  double* s_sum = reinterpret_cast<double*>(smem_raw + ((size_t(3) * ng * sizeof(R) + 15) / 16) * 16);
+  unsigned char* bins_raw = smem_raw + ((size_t(3) * ng * sizeof(R) + 15) / 16) * 16;
+  double* s_sum = reinterpret_cast<double*>(bins_raw);
   double* s_k = s_sum + a.nbins;
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_k + a.nbins);
+  PrivBin<R>* pbin = reinterpret_cast<PrivBin<R>*>(bins_raw);  // [kEstWarps][nbins] when a.priv
+  unsigned* pcnt = reinterpret_cast<unsigned*>(pbin + size_t(kEstWarps) * a.nbins);
   for (int i = threadIdx.x; i < 3 * ng; i += blockDim.x) tab[i] = tab_g[i];
-  for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
-    s_sum[i] = 0.0;
-    s_k[i] = 0.0;
-    s_cnt[i] = 0ull;
+  if (a.priv) {
+    for (int i = threadIdx.x; i < kEstWarps * a.nbins; i += blockDim.x) {
+      pbin[i].sum = PrivBin<R>::zero();
+      pbin[i].k = PrivBin<R>::zero();
+      pcnt[i] = 0u;
+    }
+  } else {
+    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+      s_sum[i] = 0.0;
+      s_k[i] = 0.0;
+      s_cnt[i] = 0ull;
+    }
   }
   __syncthreads();
   const R* winv = tab;
@@ -198,9 +235,16 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
           }
         }
         if (end && b >= 0) {
-          atomicAdd(&s_sum[b], double(sv));
-          atomicAdd(&s_k[b], double(sk));
-          atomicAdd(&s_cnt[b], (unsigned long long)sc);
+          if (a.priv) {
+            PrivBin<R>& pb = pbin[(threadIdx.x >> 5) * a.nbins + b];
+            PrivBin<R>::add(pb.sum, sv);
+            PrivBin<R>::add(pb.k, sk);
+            pcnt[(threadIdx.x >> 5) * a.nbins + b] += unsigned(sc);
+          } else {
+            atomicAdd(&s_sum[b], double(sv));
+            atomicAdd(&s_k[b], double(sk));
+            atomicAdd(&s_cnt[b], (unsigned long long)sc);
+          }
         }
       } else if (a.det_pass == 1) {  // deterministic mode, pass 1: per-bin maximum and mode count
         double sv = double(val);
@@ -240,7 +284,21 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
   __syncthreads();
   if (a.nbins == 0) return;
   for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
-    if (a.det_pass == 0) {
+    if (a.priv) {
+      double v = 0.0, k = 0.0;
+      unsigned long long c = 0;
+      for (int q = 0; q < kEstWarps; ++q) {
+        const PrivBin<R>& pb = pbin[q * a.nbins + i];
+        v += PrivBin<R>::value(pb.sum);
+        k += PrivBin<R>::value(pb.k);
+        c += pcnt[q * a.nbins + i];
+      }
+      if (c) {
+        atomicAdd(&a.bin_sum[i], v);
+        atomicAdd(&a.bin_k[i], k);
+        atomicAdd(&a.bin_cnt[i], c);
+      }
+    } else if (a.det_pass == 0) {
       if (s_cnt[i]) {
         atomicAdd(&a.bin_sum[i], s_sum[i]);
         atomicAdd(&a.bin_k[i], s_k[i]);
@@ -299,7 +357,12 @@ cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, c
   k_tables<R><<<(a.ng + 255) / 256, 256, 0, s>>>(static_cast<R*>(tables), a.ng, a.order); count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = ((size_t(3) * a.ng * sizeof(R) + 15) / 16) * 16 + size_t(a.nbins) * 24;
+  EstimateArgs b = a;
+  const size_t tab_bytes = ((size_t(3) * a.ng * sizeof(R) + 15) / 16) * 16;
+  const size_t priv_bytes = size_t(kEstWarps) * a.nbins * (sizeof(PrivBin<R>) + sizeof(unsigned));
+  // private bins while they fit in a quarter of an SM's shared memory (nbins up to ~640 in FP32 mode)
+  b.priv = (a.det_pass == 0 && priv_bytes <= 56 * 1024) ? 1 : 0;
+  const size_t smem = tab_bytes + (b.priv ? priv_bytes : size_t(a.nbins) * 24);
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(k_estimate<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -307,8 +370,8 @@ cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, c
   const int64_t rows = int64_t(a.ng) * a.ng;
   const int bx = int(std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, std::max<int64_t>(1, int64_t(num_sms()) * 8 / a.ncat))));
   const dim3 blocks(bx, a.ncat);
-  k_estimate<R><<<blocks, 256, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
-                                          static_cast<const R*>(tables), a); count_launch();
+  k_estimate<R><<<blocks, kEstWarps * 32, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
+                                                     static_cast<const R*>(tables), b); count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_estimate<float>(const void*, const void*, void*, const EstimateArgs&, cudaStream_t);

@@ -92,6 +92,8 @@ struct EstimateArgs {
   // (nbins doubles, device) holds the per-bin fixed-point scales between the passes
   int det_pass = 0;
   double* det_scale = nullptr;
+  // set by the launcher: per-warp private bins in shared memory instead of shared atomics
+  int priv = 0;
 };
 size_t estimate_table_bytes(int ng, bool dbl);
 template <typename R>

@@ -33,9 +33,11 @@ def test_triangle_counts_brute_force_tiny():
     assert np.array_equal(counts, brute)
 
 
+# 5 shells run the pair-organised triple product; 23 shells (276 shell pairs) the per-triangle one
+@pytest.mark.parametrize("ng,lo,w,ns", [(32, 1, 2, 5), (72, 1, 1, 23)])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
-def test_bispectrum_matches_oracle(prec, tol):
-    box, ng, lo, w, ns = 200.0, 32, 1, 2, 5
+def test_bispectrum_matches_oracle(prec, tol, ng, lo, w, ns):
+    box = 200.0
     pos = catalogs.zeldovich(32, box, rms=8.0, seed=51)
     _, _, _, delta = _ref.power(pos, box, ng, 4)
     ref_b, ref_c = oracle.bispectrum.bispectrum_fft(delta, box, lo, w, ns)
