@@ -101,22 +101,38 @@ __device__ __forceinline__ void stage_fields(R* vals, const R* __restrict__ fiel
 // triangles (a, b, c) for the whole kernel and keeps one running sum per triangle in each lane. Per
 // staged tile, lane l takes the points l, l + 32, l + 64, l + 96; the products I_a I_b of those points
 // are reloaded only when the pair (a, b) changes (consecutive triangles share it), and every load is a
-// conflict-free row segment. Every kFlushTiles tiles the FP32 lane sums are reduced across the warp
-// into FP64 per-block sums, which are added to S at the end.
+// conflict-free row segment. Every kFlushTiles tiles the lane sums are reduced across the warp (FP32,
+// 32 lanes x kFlushTiles x 4 points) and added to a compensated FP32 pair per triangle (Neumaier's
+// summation), which is added to S in FP64 at the end; the loop itself uses no FP64 arithmetic, which
+// this GPU executes at a small fraction of the FP32 rate. The next tile's field values are loaded
+// into registers while the current tile is processed.
 constexpr int kWarpTri = 32;
 constexpr int kTriWarps = 16;
 constexpr int kFlushTiles = 16;
+constexpr int kTriMaxShells = 16;                                                    // ntri <= 512 implies this
+constexpr int kStagePer = (kTriMaxShells * kTX + kTriWarps * 32 - 1) / (kTriWarps * 32);  // staged values per thread
+
+template <typename R>
+__device__ __forceinline__ void comp_add(R* hi, R* lo, R v) {
+  const R t = *hi + v;
+  *lo += (fabs(*hi) >= fabs(v)) ? (*hi - t) + v : (v - t) + *hi;
+  *hi = t;
+}
 
 template <typename R>
 __global__ void __launch_bounds__(kTriWarps * 32) k_triple_warp(const R* __restrict__ fields, int ng, int nshells,
                                                                int64_t buf_stride, const int* __restrict__ tri_g, int ntri,
                                                                double* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sblk = reinterpret_cast<double*>(smem_raw);           // [ntri]
-  int* tri = reinterpret_cast<int*>(sblk + ntri);                // [3 ntri]
-  R* vals = reinterpret_cast<R*>(tri + ((3 * ntri + 3) / 4) * 4);  // [nshells][kRow]
-  for (int t = threadIdx.x; t < ntri; t += blockDim.x) sblk[t] = 0.0;
-  for (int t = threadIdx.x; t < 3 * ntri; t += blockDim.x) tri[t] = tri_g[t];
+  R* shi = reinterpret_cast<R*>(smem_raw);  // [ntri] compensated per-block sums
+  R* slo = shi + ntri;
+  int* tri = reinterpret_cast<int*>(slo + ntri);                 // [ntri] packed a | b << 8 | c << 16
+  R* vals = reinterpret_cast<R*>(tri + ((ntri + 3) / 4) * 4);      // [nshells][kRow]
+  for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
+    shi[t] = R(0);
+    slo[t] = R(0);
+    tri[t] = tri_g[3 * t] | (tri_g[3 * t + 1] << 8) | (tri_g[3 * t + 2] << 16);
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = (ntri + kTriWarps - 1) / kTriWarps;  // <= kWarpTri (checked by the launcher)
   const int t_beg = warp * per, t_cnt = max(0, min(per, ntri - t_beg));
@@ -125,55 +141,76 @@ __global__ void __launch_bounds__(kTriWarps * 32) k_triple_warp(const R* __restr
   for (int j = 0; j < kWarpTri; ++j) acc[j] = R(0);
   const int64_t npts = int64_t(ng) * ng * ng;
   const int64_t ntiles = (npts + kTX - 1) / kTX;
+  const int nval = nshells * kTX;
+  // values of the first tile, then of the next one while the current one is processed
+  R pre[kStagePer];
+  auto load_tile = [&](int64_t tile) {
+#pragma unroll
+    for (int u = 0; u < kStagePer; ++u) {
+      const int i = threadIdx.x + u * kTriWarps * 32;
+      R v = R(0);
+      if (i < nval) {
+        const int sh = i / kTX, k = i - sh * kTX;
+        const int64_t x = tile * kTX + k;
+        if (x < npts) {
+          const int64_t row = x / ng;
+          v = fields[sh * buf_stride + row * (ng + 2) + (x - row * ng)];
+        }
+      }
+      pre[u] = v;
+    }
+  };
+  if (blockIdx.x < ntiles) load_tile(blockIdx.x);
   int since_flush = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    stage_fields(vals, fields, ng, nshells, buf_stride, tile, npts);
+#pragma unroll
+    for (int u = 0; u < kStagePer; ++u) {
+      const int i = threadIdx.x + u * kTriWarps * 32;
+      if (i < nval) {
+        const int sh = i / kTX;
+        vals[sh * kRow + (i - sh * kTX)] = pre[u];
+      }
+    }
     __syncthreads();
-    int pa = -1, pb = -1;
+    if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x);
+    int pab_key = -1;
     R pab[kTX / 32];
 #pragma unroll
     for (int j = 0; j < kWarpTri; ++j) {
       if (j < t_cnt) {
-        const int t = t_beg + j;
-        const int a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
-        if (a != pa || b != pb) {  // warp-uniform
-          pa = a;
-          pb = b;
+        const int code = tri[t_beg + j];
+        const int key = code & 0xffff, c = code >> 16;
+        if (key != pab_key) {  // warp-uniform
+          pab_key = key;
+          const R* ra = vals + (key & 0xff) * kRow + lane;
+          const R* rb = vals + (key >> 8) * kRow + lane;
 #pragma unroll
-          for (int i = 0; i < kTX / 32; ++i) pab[i] = vals[a * kRow + lane + 32 * i] * vals[b * kRow + lane + 32 * i];
+          for (int i = 0; i < kTX / 32; ++i) pab[i] = ra[32 * i] * rb[32 * i];
         }
+        const R* rc = vals + c * kRow + lane;
         R sum = acc[j];
 #pragma unroll
-        for (int i = 0; i < kTX / 32; ++i) sum += pab[i] * vals[c * kRow + lane + 32 * i];
+        for (int i = 0; i < kTX / 32; ++i) sum += pab[i] * rc[32 * i];
         acc[j] = sum;
       }
     }
-    if (++since_flush == kFlushTiles) {
+    if (++since_flush == kFlushTiles || tile + gridDim.x >= ntiles) {
       since_flush = 0;
 #pragma unroll
       for (int j = 0; j < kWarpTri; ++j) {
         if (j < t_cnt) {
-          double v = double(acc[j]);
+          R v = acc[j];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) sblk[t_beg + j] += v;
+          if (lane == 0) comp_add(&shi[t_beg + j], &slo[t_beg + j], v);
         }
         acc[j] = R(0);
       }
     }
   }
-#pragma unroll
-  for (int j = 0; j < kWarpTri; ++j) {
-    if (j < t_cnt) {
-      double v = double(acc[j]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) sblk[t_beg + j] += v;
-    }
-  }
   __syncthreads();
-  for (int t = threadIdx.x; t < ntri; t += blockDim.x) atomicAdd(&S[t], sblk[t]);
+  for (int t = threadIdx.x; t < ntri; t += blockDim.x) atomicAdd(&S[t], double(shi[t]) + double(slo[t]));
 }
 
 template <typename R>
@@ -419,8 +456,8 @@ pk_status pk_bispectrum(const pk_config* cfg, const void* delta_k_dev, int32_t s
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "shell filter");
   if ((st = exec_plan(L.plan, L.kind, L.fields, L.work, s)) != PK_OK) return st;
   if ((e = cudaMemsetAsync(L.S, 0, sizeof(double) * ntri, s)) != cudaSuccess) return cuda_fail(e, "memset");
-  if (ntri <= kTriWarps * kWarpTri) {  // lanes over points, warps over triangles
-    const size_t wsmem = size_t(ntri) * 8 + size_t((3 * ntri + 3) / 4) * 16 + size_t(nshells) * kRow * (dbl ? 8 : 4);
+  if (ntri <= kTriWarps * kWarpTri && nshells <= kTriMaxShells) {  // lanes over points, warps over triangles
+    const size_t wsmem = size_t(2 * ntri) * (dbl ? 8 : 4) + size_t((ntri + 3) / 4) * 16 + size_t(nshells) * kRow * (dbl ? 8 : 4);
     int per_sm = 1;
     if (dbl) {
       if ((e = cudaFuncSetAttribute(k_triple_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wsmem))) != cudaSuccess)
