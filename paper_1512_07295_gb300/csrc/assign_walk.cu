@@ -510,17 +510,25 @@ __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t 
 // weights per grid straight into the fixed-point region with integer shared atomics instead.
 constexpr int SCATTER_THREADS = 256;
 
+// Pieces of the scatter are staged in two buffers: the next piece is copied while this one is used.
+template <bool W>
+__host__ __device__ constexpr int scatter_chunk() {
+  return W ? 512 : 1024;
+}
+
 template <bool W>
 struct ScatterSmem {
-  int4 sp[chunk<W>()];
+  int4 sp[2][scatter_chunk<W>()];
   int reg[2][RVOL];
   float red[SCATTER_THREADS / 32];
-  unsigned long long mbar;
-  float sw[W ? chunk<W>() : 1];
+  unsigned long long mbar[2];
+  float sw[2][W ? scatter_chunk<W>() : 1];
 };
 
 // Adds one particle's p^3 weights on grid G to that grid's region (scale: the weight times the
 // region's fixed-point scale). Region nodes of the stencil: key + S0 + 1 .. key + S0 + p per axis.
+// (Rounding by adding 1.5 2^23 instead of a conversion would cap the scale at 2^21 per unit weight,
+// too coarse on sparse tiles: their nodes then miss the FP32 grid tolerance.)
 template <int P, int G>
 __device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc) {
   float tx, ty, tz;
@@ -705,16 +713,17 @@ __global__ void __launch_bounds__(walk::threads<P>(), 3)
   }
 }
 
-// a3, FP32, direct scatter: block per tile, pieces staged like the walk's, particles spread over the
-// lanes of a warp q = ceil(m / 32) records apart (different cells, so a warp's atomics seldom meet on
-// one node), fixed-point regions flushed to the grids as in k_assign_walk.
+// a3, FP32, direct scatter: a block takes tiles in a grid-stride sequence and their pieces in
+// order, the copy of the next piece overlapping the use of the current one; particles are spread over
+// the lanes of a warp q = ceil(m / 32) records apart (different cells, so a warp's atomics seldom meet
+// on one node); fixed-point regions are flushed to the grids as in k_assign_walk.
 template <int P, bool W>
 __global__ void __launch_bounds__(walk::SCATTER_THREADS, 4)
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
                      int64_t n, int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
                      int64_t cat_stride) {
   using namespace walk;
-  constexpr int CH = chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
+  constexpr int CH = scatter_chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
   {
     const int cat = blockIdx.y;
     g1 += cat * cat_stride;
@@ -726,54 +735,91 @@ __global__ void __launch_bounds__(walk::SCATTER_THREADS, 4)
   const int ngrid = interlace ? 2 : 1;
   const int ntiles = ntile * ntile * ntile;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar));
+  if (tid < 2) {
+    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar[tid]));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   }
   __syncthreads();
-  unsigned parity = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
-    if (beg >= end) continue;
-    const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
-    const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;
-    for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
-    float scale, inv_scale;
-    tile_scale<W>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
-    for (int64_t c0 = beg; c0 < end; c0 += CH) {
-      const int m = int(min(int64_t(CH), end - c0));
-      if (tid == 0) bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
-      if (W)
-        for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
-      const bool arrived = bulk_wait(&S.mbar, parity);
-      parity ^= 1u;
-      if (__syncthreads_or(!arrived)) {  // the copy did not complete: report, drain, stop
-        if (tid == 0) {
-          raise_err(PK_DERR_TIMEOUT);
-          bulk_wait(&S.mbar, parity ^ 1u);
-        }
-        return;
+  // the block's pieces: (tile, first record c0, tile's records [beg, end))
+  struct Piece {
+    int tile;
+    int64_t beg, end, c0;
+  };
+  auto advance = [&](Piece& c) -> bool {  // next piece of this tile, else the first of the next non-empty tile
+    c.c0 += CH;
+    while (c.c0 >= c.end) {
+      c.tile += gridDim.x;
+      if (c.tile >= ntiles) return false;
+      c.beg = max(toff[c.tile], int64_t(0));
+      c.end = min(toff[c.tile + 1], n);
+      c.c0 = c.beg;
+    }
+    return true;
+  };
+  Piece cur;
+  cur.tile = int(blockIdx.x) - int(gridDim.x);
+  cur.beg = cur.end = 0;
+  cur.c0 = -CH;
+  if (!advance(cur)) return;
+  if (tid == 0) bulk_load(S.sp[0], p + cur.c0, unsigned(min(int64_t(CH), cur.end - cur.c0)) * 16u, &S.mbar[0]);
+  Piece nxt = cur;
+  bool has_next = advance(nxt);
+  unsigned parity = 0u;  // bit b: the phase buffer b waits for next
+  int buf = 0;
+  float scale = 1.0f, inv_scale = 1.0f;
+  int cx0 = 0, cy0 = 0, cz0 = 0;
+  while (true) {
+    const int m = int(min(int64_t(CH), cur.end - cur.c0));
+    if (cur.c0 == cur.beg) {  // first piece of a tile: clear the region, take the tile's scale
+      const int tz = cur.tile % ntile, ty = (cur.tile / ntile) % ntile, tx = cur.tile / (ntile * ntile);
+      cx0 = tx * T;
+      cy0 = ty * T;
+      cz0 = tz * T;
+      for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
+      tile_scale<W>(w, cur.beg, cur.end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+    }
+    // the other buffer was released by the synchronisation that ended the previous piece
+    if (has_next && tid == 0)
+      bulk_load(S.sp[buf ^ 1], p + nxt.c0, unsigned(min(int64_t(CH), nxt.end - nxt.c0)) * 16u, &S.mbar[buf ^ 1]);
+    if (W)
+      for (int i = tid; i < m; i += THREADS) S.sw[buf][i] = w[cur.c0 + i];
+    const bool arrived = bulk_wait(&S.mbar[buf], (parity >> buf) & 1u);
+    parity ^= 1u << buf;
+    if (__syncthreads_or(!arrived)) {  // a copy did not complete: report, drain what is in flight, stop
+      if (tid == 0) {
+        raise_err(PK_DERR_TIMEOUT);
+        bulk_wait(&S.mbar[buf], ((parity >> buf) & 1u) ^ 1u);
+        if (has_next) bulk_wait(&S.mbar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
       }
-      const int q = (m + 31) / 32;
-      for (int i = tid; i < 32 * q; i += THREADS) {
-        const int j = (i & 31) * q + (i >> 5);
-        if (j >= m) continue;
-        const int4 r = S.sp[j];
-        const uint32_t cell = uint32_t(r.x);
-        const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        if ((cell >> 30) != 0 || unsigned(lx) >= unsigned(T) || unsigned(ly) >= unsigned(T) || unsigned(lz) >= unsigned(T)) {
-          raise_err(PK_DERR_CELLRANGE);
-          continue;
-        }
-        const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
-        const float sc = (W ? S.sw[j] : 1.0f) * weight_scale<P>() * scale;
-        scatter_particle<P, 0>(S.reg[0], lx, ly, lz, fx, fy, fz, sc);
-        if (interlace) scatter_particle<P, 1>(S.reg[1], lx, ly, lz, fx, fy, fz, sc);
+      return;
+    }
+    const int4* sp = S.sp[buf];
+    const float* sw = S.sw[buf];
+    const int q = (m + 31) / 32;
+    for (int i = tid; i < 32 * q; i += THREADS) {
+      const int j = (i & 31) * q + (i >> 5);
+      if (j >= m) continue;
+      const int4 r = sp[j];
+      const uint32_t cell = uint32_t(r.x);
+      const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
+      if ((cell >> 30) != 0 || unsigned(lx) >= unsigned(T) || unsigned(ly) >= unsigned(T) || unsigned(lz) >= unsigned(T)) {
+        raise_err(PK_DERR_CELLRANGE);
+        continue;
       }
+      const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
+      const float sc = (W ? sw[j] : 1.0f) * weight_scale<P>() * scale;
+      scatter_particle<P, 0>(S.reg[0], lx, ly, lz, fx, fy, fz, sc);
+      if (interlace) scatter_particle<P, 1>(S.reg[1], lx, ly, lz, fx, fy, fz, sc);
+    }
+    __syncthreads();
+    if (cur.c0 + CH >= cur.end) {  // last piece of the tile
+      flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
       __syncthreads();
     }
-    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
-    __syncthreads();
+    if (!has_next) break;
+    cur = nxt;
+    buf ^= 1;
+    has_next = advance(nxt);
   }
 }
 

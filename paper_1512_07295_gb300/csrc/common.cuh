@@ -110,9 +110,11 @@ __device__ __forceinline__ int half_shift(T f, T* f2) {
   return up ? 1 : 0;
 }
 
+// Periodic index for i in [-n, 2n): every caller is a stencil node or a tile region node within a
+// few cells of the grid (N >= 8), so one conditional correction replaces the integer remainder.
 __device__ __forceinline__ int wrap(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
+  i += i < 0 ? n : 0;
+  return i >= n ? i - n : i;
 }
 
 // Signed mode index of FFT slot i (slot N/2 is -N/2).
