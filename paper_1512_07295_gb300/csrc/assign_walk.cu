@@ -140,6 +140,14 @@ __host__ __device__ constexpr float weight_scale() {
   return P == 4 ? 1.0f / 216.0f : 1.0f;
 }
 
+// Integer reduction into shared memory at a 32-bit shared-window address: the regions are plain
+// shared arrays, and naming the state space keeps the address arithmetic 32-bit (constant offsets
+// fold into the instruction) instead of generic 64-bit atomics.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void red_shared(unsigned addr, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
 // Packed pairs of FP32 values in one 64-bit register (PTX .f32x2 arithmetic, sm_100 family).
 typedef unsigned long long f2x;
 __device__ __forceinline__ f2x pack2(float a, float b) {
@@ -334,11 +342,11 @@ __device__ __forceinline__ void flush_plane(const Window<P>& win, int a, int* re
       if (kz >= d) sum += t;
     }
     if (valid) {
-      int* r = reg + (rx * RS + ry0 + b) * RS + kz + s0<P>() + 1;
-      atomicAdd(r, __float2int_rn(sum * scale));
+      const unsigned r = smem_u32(reg + (rx * RS + ry0 + b) * RS + kz + s0<P>() + 1);
+      red_shared(r, __float2int_rn(sum * scale));
 #pragma unroll
       for (int c = 1; c < P; ++c)
-        if (kz + c >= KZ) atomicAdd(r + c, __float2int_rn(v[c] * scale));
+        if (kz + c >= KZ) red_shared(r + 4u * c, __float2int_rn(v[c] * scale));
     }
   }
 }
@@ -539,14 +547,14 @@ __device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int l
   weights<P>(tz, wz);
 #pragma unroll
   for (int a = 0; a < P; ++a) wx[a] *= sc;
-  int* base = reg + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
+  const unsigned base = smem_u32(reg + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1);
 #pragma unroll
   for (int a = 0; a < P; ++a)
 #pragma unroll
     for (int b = 0; b < P; ++b) {
       const float xy = wx[a] * wy[b];
 #pragma unroll
-      for (int c = 0; c < P; ++c) atomicAdd(base + (a * RS + b) * RS + c, __float2int_rn(xy * wz[c]));
+      for (int c = 0; c < P; ++c) red_shared(base + 4u * ((a * RS + b) * RS + c), __float2int_rn(xy * wz[c]));
     }
 }
 
