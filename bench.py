@@ -247,14 +247,25 @@ def measure_rows(dev, host64, big_box):
     cells = torch.cat(parts)
     del parts
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    batch = 128
+    # group size chosen by the library's autotuner, then the call timed eagerly and as a CUDA graph replay
+    batch, tune_ms = api.autotune_batch(cells, offs, cfg, candidates=(32, 64, 128), reps=2)
     wsc = api.batch_workspace(cfg, batch, api.max_group_particles(offs, batch), dev)
     pkb = torch.empty((512, cfg.nb), dtype=torch.float64, device=dev)
     nmb = torch.empty((512, cfg.nb), dtype=torch.int64, device=dev)
     ms = _time_cuda(lambda: api.batch_power(cells, offs, cfg, batch=batch, ws=wsc, out=(pkb, nmb)), 3)
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            api.batch_power(cells, offs, cfg, batch=batch, ws=wsc, out=(pkb, nmb))
+    torch.cuda.current_stream(dev).wait_stream(cap)
+    ms_graph = _time_cuda(graph.replay, 3)
     rows["batch"] = {"workload": f"512 catalogues, {int(sizes.sum())} particles, N_P log-uniform in [1e5, 2e6], L=1000, "
-                                 f"N_G=128, PCS+interlacing, FP32, groups of {batch}",
-                     "ms_per_call": ms, "pk_per_s": 512 / (ms * 1e-3), "particles_per_s": float(sizes.sum()) / (ms * 1e-3)}
+                                 f"N_G=128, PCS+interlacing, FP32, groups of {batch} (autotuned)",
+                     "ms_per_call": ms, "pk_per_s": 512 / (ms * 1e-3), "particles_per_s": float(sizes.sum()) / (ms * 1e-3),
+                     "graph_ms_per_call": ms_graph, "autotune_ms": {str(k): v for k, v in tune_ms.items()}}
+    del graph
     del wsc, cells
     torch.cuda.empty_cache()
     return rows

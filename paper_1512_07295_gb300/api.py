@@ -271,6 +271,34 @@ def batch_power(cells, offsets, cfg, batch=64, ws=None, out=None):
     return pk, nm
 
 
+def autotune_batch(cells, offsets, cfg, candidates=(16, 32, 64, 128), reps=3):
+    """Chooses the group size of batch_power for these catalogues by timing each candidate (CUDA
+    events, after one warm-up call each). Returns (best, {candidate: ms}). The group size sets how
+    many catalogues share each batched launch: larger groups fill the GPU with fewer launches but
+    need a larger workspace."""
+    import numpy as np
+
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    ncat = len(offs) - 1
+    pk = torch.empty((ncat, cfg.nb), dtype=torch.float64, device=cells.device)
+    nm = torch.empty((ncat, cfg.nb), dtype=torch.int64, device=cells.device)
+    times = {}
+    for b in candidates:
+        b = int(min(max(b, 1), 128))
+        ws = batch_workspace(cfg, b, max_group_particles(offs, b), cells.device)
+        batch_power(cells, offs, cfg, batch=b, ws=ws, out=(pk, nm))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            batch_power(cells, offs, cfg, batch=b, ws=ws, out=(pk, nm))
+        e1.record()
+        torch.cuda.synchronize()
+        times[b] = e0.elapsed_time(e1) / reps
+        del ws
+    best = min(times, key=times.get)
+    return best, times
+
+
 def estimate_noalloc(g1_hat, g2_hat, cfg, wsum, w2sum):
     """P(k) from the transforms of the two mass grids without any device allocation by the library
     (pk_estimate_noalloc). g*_hat: (ng, ng, ng/2+1) complex tensors. Returns (pk, kmean, nmodes)."""

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <utility>
 #include <string>
 #include <tuple>
 
@@ -50,6 +51,21 @@ void prof_mark(int k, cudaStream_t s) {
   if (!t_prof || k < 0 || k >= kProfMarks) return;
   if (!t_ev[k] && cudaEventCreate(&t_ev[k]) != cudaSuccess) return;
   if (cudaEventRecord(t_ev[k], s) == cudaSuccess) t_ev_rec[k] = true;
+}
+
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{kernel, dev}];
+  if (have >= smem) return cudaSuccess;
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess) return e;
+  have = smem;
+  return cudaSuccess;
 }
 
 int num_sms() {

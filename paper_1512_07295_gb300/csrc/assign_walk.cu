@@ -16,6 +16,10 @@
 //  - after the tile, the region is added to the grids in global memory.
 // Per particle and grid: p weights per axis, p^2 products w_x w_y and p^3 multiply-adds, issued as
 // packed two-lane FP32 FMAs (fma.rn.f32x2) over pairs of y rows for PCS and CIC.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "internal.cuh"
 
 namespace pk {
@@ -831,6 +835,28 @@ __global__ void __launch_bounds__(walk::SCATTER_THREADS, 4)
   }
 }
 
+// Shared-memory opt-in and resident blocks per SM of a kernel, set up once per (kernel, device): later
+// launches make no attribute or occupancy calls, so a call captured in a CUDA graph holds launches only.
+static cudaError_t kernel_setup(const void* kernel, int threads, size_t smem, int* per_sm) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({kernel, dev});
+  if (it != cache.end()) {
+    *per_sm = it->second;
+    return cudaSuccess;
+  }
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess) return e;
+  int n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+  cache[{kernel, dev}] = n;
+  *per_sm = n;
+  return cudaSuccess;
+}
+
 // Mean particles per tile below which the direct scatter replaces the walk. Measured per tile on one
 // GB300: the walk costs about 73 ns + 0.018 ns per particle of block time, the scatter 19 ns + 0.048 ns,
 // so they cross near 1800 particles per tile (8^3 cells).
@@ -843,13 +869,9 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
   const size_t smem = sizeof(walk::ScatterSmem<W>);
-  cudaError_t e = cudaFuncSetAttribute(k_assign_scatter<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assign_scatter<P, W>, walk::SCATTER_THREADS, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W>), walk::SCATTER_THREADS, smem, &per_sm);
+  if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
   k_assign_scatter<P, W><<<blocks, walk::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
                                                                      cat_stride);
@@ -865,12 +887,9 @@ static cudaError_t launch_walk_pw(const pk_cellpos* p, const float* w, const int
   if (n < kScatterMaxMean * int64_t(ntiles) * ncat)  // sparse tiles: the direct scatter
     return launch_scatter_pw<P, W>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
   const size_t smem = sizeof(walk::Smem<W>);
-  cudaError_t e = cudaFuncSetAttribute(k_assign_walk<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assign_walk<P, W>, walk::threads<P>(), smem) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_walk<P, W>), walk::threads<P>(), smem, &per_sm);
+  if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
   k_assign_walk<P, W><<<blocks, walk::threads<P>(), smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, cat_stride);
   count_launch();

@@ -460,14 +460,14 @@ pk_status pk_bispectrum(const pk_config* cfg, const void* delta_k_dev, int32_t s
     const size_t wsmem = size_t(2 * ntri) * (dbl ? 8 : 4) + size_t((ntri + 3) / 4) * 16 + size_t(nshells) * kRow * (dbl ? 8 : 4);
     int per_sm = 1;
     if (dbl) {
-      if ((e = cudaFuncSetAttribute(k_triple_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wsmem))) != cudaSuccess)
+      if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple_warp<double>), wsmem)) != cudaSuccess)
         return cuda_fail(e, "triple smem");
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_warp<double>, kTriWarps * 32, wsmem) != cudaSuccess)
         per_sm = 1;
       k_triple_warp<double><<<num_sms() * std::max(per_sm, 1), kTriWarps * 32, wsmem, s>>>(
           static_cast<const double*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S);
     } else {
-      if ((e = cudaFuncSetAttribute(k_triple_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wsmem))) != cudaSuccess)
+      if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple_warp<float>), wsmem)) != cudaSuccess)
         return cuda_fail(e, "triple smem");
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_warp<float>, kTriWarps * 32, wsmem) != cudaSuccess)
         per_sm = 1;
@@ -485,8 +485,8 @@ pk_status pk_bispectrum(const pk_config* cfg, const void* delta_k_dev, int32_t s
   }
   const size_t smem = size_t(nshells) * kRow * (dbl ? 8 : 4) + size_t(ntri) * 8;
   if (smem > 48 * 1024) {
-    e = dbl ? cudaFuncSetAttribute(k_triple<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
-            : cudaFuncSetAttribute(k_triple<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = dbl ? ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple<double>), smem)
+            : ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple<float>), smem);
     if (e != cudaSuccess) return cuda_fail(e, "triple smem");
   }
   const int tblocks = num_sms() * 2;

@@ -363,10 +363,7 @@ cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, c
   // private bins while they fit in a quarter of an SM's shared memory (nbins up to ~640 in FP32 mode)
   b.priv = (a.det_pass == 0 && priv_bytes <= 56 * 1024) ? 1 : 0;
   const size_t smem = tab_bytes + (b.priv ? priv_bytes : size_t(a.nbins) * 24);
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_estimate<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-  }
+  if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_estimate<R>), smem)) != cudaSuccess) return e;
   const int64_t rows = int64_t(a.ng) * a.ng;
   const int bx = int(std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, std::max<int64_t>(1, int64_t(num_sms()) * 8 / a.ncat))));
   const dim3 blocks(bx, a.ncat);

@@ -44,3 +44,47 @@ def test_batch_with_empty_catalogue():
     single, _, _ = api.power(a, cfg)
     assert _ref.rel(pk[0].cpu().numpy(), single.cpu().numpy()) <= 1e-6
     assert torch.all(nm[1] == nm[0])
+
+
+def test_batch_call_replays_from_a_cuda_graph():
+    # the whole pk_batch_power call (several groups) captured once and replayed: same results, no
+    # host synchronisation inside
+    box, ng = 200.0, 32
+    sizes = catalogs.batch_sizes(6, 500, 8000, seed=73)
+    cats = [catalogs.poisson(s, box, seed=300 + i) for i, s in enumerate(sizes)]
+    cfg = api.Config(ng=ng, box=box, prec="fp32")
+    cells = torch.cat([api.prepare(_t(c), cfg) for c in cats])
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    ws = api.batch_workspace(cfg, 4, api.max_group_particles(offs, 4), cells.device)
+    pk = torch.empty((len(sizes), cfg.nb), dtype=torch.float64, device=DEV)
+    nm = torch.empty((len(sizes), cfg.nb), dtype=torch.int64, device=DEV)
+    api.batch_power(cells, offs, cfg, batch=4, ws=ws, out=(pk, nm))  # eager call: plans and attributes
+    torch.cuda.synchronize()
+    ref_pk, ref_nm = pk.clone(), nm.clone()
+    pk.zero_()
+    nm.zero_()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            api.batch_power(cells, offs, cfg, batch=4, ws=ws, out=(pk, nm))
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(nm, ref_nm)
+    assert _ref.rel(pk.cpu().numpy(), ref_pk.cpu().numpy()) <= 1e-6
+
+
+def test_autotuned_group_size_gives_the_same_spectra():
+    box, ng = 200.0, 32
+    sizes = catalogs.batch_sizes(9, 500, 8000, seed=74)
+    cats = [catalogs.poisson(s, box, seed=400 + i) for i, s in enumerate(sizes)]
+    cfg = api.Config(ng=ng, box=box, prec="fp32")
+    cells = torch.cat([api.prepare(_t(c), cfg) for c in cats])
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    best, times = api.autotune_batch(cells, offs, cfg, candidates=(2, 4, 8), reps=2)
+    assert best in (2, 4, 8) and set(times) == {2, 4, 8}
+    a, na = api.batch_power(cells, offs, cfg, batch=best)
+    b, nb = api.batch_power(cells, offs, cfg, batch=3)
+    assert torch.equal(na, nb)
+    assert _ref.rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-6
