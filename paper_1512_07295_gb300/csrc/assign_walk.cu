@@ -461,31 +461,36 @@ __device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned pari
 }
 
 // Adds a tile's node regions (origin: node (cx0-1, cy0-1, cz0-1); grid gi at reg + gi RVOL),
-// converted back from fixed point, to the grids; node pairs whose global z index is even are added
-// with one 8-byte vector reduction.
+// converted back from fixed point, to the grids. A thread owns one of 8 slots along z for its whole
+// share of the rows: slot 0 is node 0 of a row, slots 1..5 the node pairs (1,2)..(9,10), whose global
+// z index is even so each pair is one 8-byte vector reduction, slot 6 node 11, slot 7 idle. The
+// slot's z indices are computed once, outside the row loop.
 __device__ __forceinline__ void flush_region(const int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
                                              float inv_scale, float* g1, float* g2, int tid, int nthreads) {
-  for (int i = tid; i < ngrid * RS * RS * 7; i += nthreads) {
-    const int row = i / 7, item = i - row * 7;
+  const int slot = tid & 7;
+  if (slot == 7) return;
+  const bool pair = slot >= 1 && slot <= 5;
+  const int rz = slot == 0 ? 0 : (slot == 6 ? RS - 1 : 2 * slot - 1);
+  const int z = wrap(cz0 - 1 + rz, ng);
+  const bool vec = pair && z + 1 < ng;  // z even, row bases 8-byte aligned (ldz even)
+  const int z1 = pair ? wrap(z + 1, ng) : 0;
+  const int nrows = ngrid * RS * RS;
+  for (int row = tid >> 3; row < nrows; row += nthreads >> 3) {
     const int gi = row / (RS * RS), rr = row - gi * (RS * RS);
     const int rx = rr / RS, ry = rr - rx * RS;
-    const int* src = reg + gi * RVOL + (rx * RS + ry) * RS;
+    const int* src = reg + gi * RVOL + rr * RS + rz;
     float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
-    if (item == 0 || item == 6) {
-      const int rz = item == 0 ? 0 : RS - 1;
-      const float v = float(src[rz]) * inv_scale;
-      if (v != 0.0f) atomicAdd(gg + wrap(cz0 - 1 + rz, ng), v);
+    const float v0 = float(src[0]) * inv_scale;
+    if (!pair) {
+      if (v0 != 0.0f) atomicAdd(gg + z, v0);
     } else {
-      const int rz = 2 * item - 1;  // odd: the global z index cz0 - 1 + rz is even
-      const float v0 = float(src[rz]) * inv_scale, v1 = float(src[rz + 1]) * inv_scale;
+      const float v1 = float(src[1]) * inv_scale;
       if (v0 != 0.0f || v1 != 0.0f) {
-        const int z = wrap(cz0 - 1 + rz, ng);
-        float* dst = gg + z;
-        if (z + 1 < ng && (reinterpret_cast<uintptr_t>(dst) & 7u) == 0) {
-          asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(v0), "f"(v1) : "memory");
+        if (vec) {
+          asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(gg + z), "f"(v0), "f"(v1) : "memory");
         } else {
-          atomicAdd(dst, v0);
-          atomicAdd(gg + wrap(z + 1, ng), v1);
+          atomicAdd(gg + z, v0);
+          atomicAdd(gg + z1, v1);
         }
       }
     }
