@@ -884,12 +884,17 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
   return cudaGetLastError();
 }
 
+bool assign_uses_scatter(int64_t n, int ng, int ncat) {
+  const int64_t nt = tiles_per_axis(ng);
+  return n < kScatterMaxMean * nt * nt * nt * ncat;
+}
+
 template <int P, bool W>
 static cudaError_t launch_walk_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
                                   float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
-  if (n < kScatterMaxMean * int64_t(ntiles) * ncat)  // sparse tiles: the direct scatter
+  if (assign_uses_scatter(n, ng, ncat))  // sparse tiles: the direct scatter
     return launch_scatter_pw<P, W>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
   const size_t smem = sizeof(walk::Smem<W>);
   int per_sm = 1;

@@ -50,6 +50,12 @@ struct CatRanges {  // particle ranges of the catalogues of one batch group (abs
   int nb;
   int ng;
 };
+// Batched binning by tile only (no slab order inside a tile, for the direct scatter), counted and
+// placed through per-block shared-memory histograms: one global atomic per (block, tile) instead of
+// one per particle. Needs ntile^3 <= kSmemBinTiles; counts: nb ntile^3 entries.
+constexpr int kSmemBinTiles = 8192;
+cudaError_t launch_bin_batch_tiles(const pk_cellpos* p, const CatRanges& r, int ntile, pk_cellpos* sorted, int64_t* offsets,
+                                   unsigned long long* counts, long long* scan_scratch, cudaStream_t s);
 cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, int ntile, pk_cellpos* sorted, int64_t* offsets,
                              unsigned long long* counts, int64_t* sub, long long* scan_scratch, cudaStream_t s);
 
@@ -60,6 +66,9 @@ cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* 
                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
 // FP32 column-walk assignment (assign_walk.cu), same layout and binned input as the tiled kernel;
 // ncat > 1: catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids g + c * cat_stride.
+// Whether launch_assign_walk_f32 takes the direct scatter (sparse tiles) for n particles over ncat
+// catalogues of side ng; the scatter needs no slab order inside a tile.
+bool assign_uses_scatter(int64_t n, int ng, int ncat);
 cudaError_t launch_assign_walk_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
                                    int64_t cat_stride = 0);

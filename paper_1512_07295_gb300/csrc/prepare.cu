@@ -187,6 +187,58 @@ __global__ void k_tile_scatter_batch(const pk_cellpos* __restrict__ p, CatRanges
   }
 }
 
+// Batched binning by tile with shared-memory histograms. Block (x, c) takes particles
+// [off[c] + x kBinChunk, ..) of catalogue c: it counts their tiles in shared memory, then adds one
+// count per non-empty tile to the global counters (count pass), or reserves one range per non-empty
+// tile with a global atomic and places its particles there through shared-memory cursors (place
+// pass). Output indices count from the group's first particle, as k_tile_scatter_batch's.
+constexpr int kBinChunk = 32768;
+
+__device__ __forceinline__ int tile_of(const pk_cellpos& r, int ntile) {
+  return ((cell_x(r.cell) / kTileCells) * ntile + cell_y(r.cell) / kTileCells) * ntile + cell_z(r.cell) / kTileCells;
+}
+
+__global__ void k_tile_count_smem(const pk_cellpos* __restrict__ p, CatRanges r, int ntile,
+                                  unsigned long long* __restrict__ counts) {
+  extern __shared__ int s_cnt[];  // [ntiles]
+  const int c = blockIdx.y, ntiles = ntile * ntile * ntile;
+  const int64_t beg = r.off[c] + int64_t(blockIdx.x) * kBinChunk, end = min(r.off[c + 1], beg + kBinChunk);
+  if (beg >= end) return;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_cnt[t] = 0;
+  __syncthreads();
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&s_cnt[tile_of(checked(p[i], r.ng), ntile)], 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+    if (s_cnt[t]) atomicAdd(&counts[int64_t(c) * ntiles + t], (unsigned long long)s_cnt[t]);
+}
+
+__global__ void k_tile_place_smem(const pk_cellpos* __restrict__ p, CatRanges r, int ntile, const int64_t* __restrict__ offsets,
+                                  unsigned long long* __restrict__ cursor, pk_cellpos* __restrict__ out) {
+  extern __shared__ long long s_base[];  // [ntiles] range start, then int cursors [ntiles]
+  const int c = blockIdx.y, ntiles = ntile * ntile * ntile;
+  int* s_cnt = reinterpret_cast<int*>(s_base + ntiles);
+  const int64_t beg = r.off[c] + int64_t(blockIdx.x) * kBinChunk, end = min(r.off[c + 1], beg + kBinChunk);
+  if (beg >= end) return;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_cnt[t] = 0;
+  __syncthreads();
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&s_cnt[tile_of(checked(p[i], r.ng), ntile)], 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const int k = s_cnt[t];
+    if (k) {
+      const int64_t key = int64_t(c) * ntiles + t;
+      s_base[t] = offsets[key] + (long long)atomicAdd(&cursor[key], (unsigned long long)k);
+    }
+    s_cnt[t] = 0;
+  }
+  __syncthreads();
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const pk_cellpos rec = checked(p[i], r.ng);
+    const int t = tile_of(rec, ntile);
+    out[s_base[t] + atomicAdd(&s_cnt[t], 1)] = rec;
+  }
+}
+
 // Exclusive scan of int64 counts, three phases over blocks of kScanBlock elements.
 constexpr int kScanBlock = 1024;
 
@@ -313,6 +365,26 @@ cudaError_t launch_bin_finish(const pk_cellpos* cells, const float* w, int64_t n
     if ((e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     k_tile_scatter<<<int(blocks), threads, 0, s>>>(cells, w, n, ng, ntile, sub, counts, sorted, wsorted); count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_batch_tiles(const pk_cellpos* p, const CatRanges& r, int ntile, pk_cellpos* sorted, int64_t* offsets,
+                                   unsigned long long* counts, long long* scan_scratch, cudaStream_t s) {
+  const int ntiles = ntile * ntile * ntile;
+  const int64_t nkeys = int64_t(ntiles) * r.nb;
+  cudaError_t e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  int64_t maxc = 1;
+  for (int c = 0; c < r.nb; ++c) maxc = std::max<int64_t>(maxc, r.off[c + 1] - r.off[c]);
+  const dim3 blocks(unsigned((maxc + kBinChunk - 1) / kBinChunk), unsigned(r.nb));
+  const size_t smem_count = size_t(ntiles) * sizeof(int), smem_place = size_t(ntiles) * (sizeof(long long) + sizeof(int));
+  if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_tile_count_smem), smem_count)) != cudaSuccess) return e;
+  if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_tile_place_smem), smem_place)) != cudaSuccess) return e;
+  k_tile_count_smem<<<blocks, 512, smem_count, s>>>(p, r, ntile, counts); count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_exclusive_scan(counts, nkeys, offsets, scan_scratch, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counts, 0, size_t(nkeys) * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  k_tile_place_smem<<<blocks, 512, smem_place, s>>>(p, r, ntile, offsets, counts, sorted); count_launch();
   return cudaGetLastError();
 }
 
