@@ -8,9 +8,9 @@
 // phase: on a Nyquist slot (i = N/2, n_i = -N/2) the partner index is again -N/2, so its phase is
 // e^{-i pi/2}, not the conjugate. Both are evaluated from the same loads, so every mode of the full
 // N^3 grid is binned exactly once. P(n) = V |delta(n)|^2 (Sec. 2.2 estimator); bins by the exact
-// integer test e_b^2 <= 4|n|^2 < e_{b+1}^2. Each warp takes one (i_x, i_y) row with lanes along i_z
-// (coalesced loads), reduces runs of equal bins with a shuffle scan and adds the run sums to
-// per-block FP64 shared-memory bins, flushed once per block.
+// integer test e_b^2 <= 4|n|^2 < e_{b+1}^2. Each warp takes 32 consecutive slots of the flattened
+// [i_x][i_y][i_z] array (coalesced loads), reduces runs of equal bins with a shuffle scan and adds the
+// run sums to per-warp shared-memory bins (or per-block FP64 bins), flushed once per block.
 #include "internal.cuh"
 
 namespace pk {
@@ -135,17 +135,17 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
   const int64_t warp_g = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   C2<R>* dout = static_cast<C2<R>*>(a.delta_out);
-  // work items: (row, 32-mode chunk of the row); the next item's loads are issued before the current
-  // item is processed so that two loads per lane are in flight
-  const int nchunk = (lz + 31) / 32;
-  const int items = int(rows) * nchunk;  // <= 1024^2 * 17
+  // work items: 32 consecutive slots of the flattened [row][i_z] half-complex array (an item may span
+  // a row boundary, so no lane idles at the end of a row); the next item's loads are issued before the
+  // current item is processed so that two loads per lane are in flight
+  const int nslots = int(rows) * lz;  // <= 1024^2 * 513 < 2^31
+  const int items = (nslots + 31) / 32;
   C2<R> g1n = {R(0), R(0)}, g2n = {R(0), R(0)};
   if (warp_g < items) {
-    const int row = int(warp_g) / nchunk;
-    const int iz = (int(warp_g) - row * nchunk) * 32 + lane;
-    if (iz < lz) {
-      g1n = G1[int64_t(row) * lz + iz];
-      if (a.interlace) g2n = G2[int64_t(row) * lz + iz];
+    const int sl = int(warp_g) * 32 + lane;
+    if (sl < nslots) {
+      g1n = G1[sl];
+      if (a.interlace) g2n = G2[sl];
     }
   }
   for (int item = int(warp_g); item < items; item += int(nwarps)) {
@@ -153,17 +153,28 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
     {
       const int nxt = item + int(nwarps);
       if (nxt < items) {
-        const int row = nxt / nchunk;
-        const int iz = (nxt - row * nchunk) * 32 + lane;
-        if (iz < lz) {
-          g1n = G1[int64_t(row) * lz + iz];
-          if (a.interlace) g2n = G2[int64_t(row) * lz + iz];
+        const int sl = nxt * 32 + lane;
+        if (sl < nslots) {
+          g1n = G1[sl];
+          if (a.interlace) g2n = G2[sl];
         }
       }
     }
-    const int row = item / nchunk;
-    const int z0 = (item - row * nchunk) * 32;
-    const int ix = row / ng, iy = row - ix * ng;
+    // this lane's slot: row (i_x, i_y) and i_z, from the item's first row by carrying along the rows
+    const int base = item * 32;
+    const int row0 = base / lz;
+    int iz = base - row0 * lz + lane, rseg = 0;
+    while (iz >= lz) {
+      iz -= lz;
+      ++rseg;
+    }
+    int ix = row0 / ng, iy = row0 - ix * ng;
+    iy += rseg;
+    while (iy >= ng) {
+      iy -= ng;
+      ++ix;
+    }
+    const int row = row0 + rseg;
     const int nx = signed_mode(ix, ng), ny = signed_mode(iy, ng);
     const R wxy = winv[ix] * winv[iy];
     const C2<R> phx = {pc[ix], ps[ix]}, phy = {pc[iy], ps[iy]};
@@ -172,8 +183,7 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
     const C2<R> phxy_p = cmul(ix == half ? phx : conj(phx), iy == half ? phy : conj(phy));
     const long long nxy2 = (long long)nx * nx + (long long)ny * ny;
     {
-      const int iz = z0 + lane;
-      const bool live = iz < lz;
+      const bool live = base + lane < nslots;
       int b = -1;
       R val = R(0), ks = R(0);
       int cnt = 0;
@@ -234,16 +244,21 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
             sc += tc;
           }
         }
-        if (end && b >= 0) {
-          if (a.priv) {
-            PrivBin<R>& pb = pbin[(threadIdx.x >> 5) * a.nbins + b];
-            PrivBin<R>::add(pb.sum, sv);
-            PrivBin<R>::add(pb.k, sk);
-            pcnt[(threadIdx.x >> 5) * a.nbins + b] += unsigned(sc);
-          } else {
-            atomicAdd(&s_sum[b], double(sv));
-            atomicAdd(&s_k[b], double(sk));
-            atomicAdd(&s_cnt[b], (unsigned long long)sc);
+        if (!a.priv && end && b >= 0) {
+          atomicAdd(&s_sum[b], double(sv));
+          atomicAdd(&s_k[b], double(sk));
+          atomicAdd(&s_cnt[b], (unsigned long long)sc);
+        }
+        if (a.priv) {  // run ends of one row have distinct bins, of two rows maybe not: rows in turn
+          const int nseg = __reduce_max_sync(0xffffffffu, rseg) + 1;
+          for (int seg = 0; seg < nseg; ++seg) {
+            if (end && b >= 0 && rseg == seg) {
+              PrivBin<R>& pb = pbin[(threadIdx.x >> 5) * a.nbins + b];
+              PrivBin<R>::add(pb.sum, sv);
+              PrivBin<R>::add(pb.k, sk);
+              pcnt[(threadIdx.x >> 5) * a.nbins + b] += unsigned(sc);
+            }
+            __syncwarp();
           }
         }
       } else if (a.det_pass == 1) {  // deterministic mode, pass 1: per-bin maximum and mode count
