@@ -50,3 +50,14 @@ def assign_units(u, ng, p, weights=None, shift=False, chunk=1 << 16):
 def assign(pos, box, ng, p, weights=None, shift=False):
     """Mass grid of eq:delgrid from positions in length units (see ``assign_units``)."""
     return assign_units(grid_units(pos, box, ng), ng, p, weights=weights, shift=shift)
+
+
+def node_value(u, ng, p, node, weights=None, shift=False):
+    """rho_j of eq:delgrid at one node j = (jx, jy, jz): sum_i w_i prod_axis W^(p)(s_axis), with s the
+    minimum-image separation j - u_i (u + 1/2 for shift=True, grid 2 of Sec. 3.1). Particles outside
+    the support contribute W = 0, so u may hold any subset that contains every particle near j."""
+    u = np.asarray(u, dtype=np.float64) + (0.5 if shift else 0.0)
+    w = np.ones(u.shape[0]) if weights is None else np.asarray(weights, dtype=np.float64)
+    s = np.asarray(node, dtype=np.float64)[None, :] - u
+    s -= ng * np.round(s / ng)  # minimum image
+    return float(np.sum(w * weight(p, s[:, 0]) * weight(p, s[:, 1]) * weight(p, s[:, 2])))

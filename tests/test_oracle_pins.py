@@ -340,3 +340,26 @@ def test_mode_counts_with_edges_from_zero_exclude_k0():
     _, _, cnt = power.power_spectrum(np.ones((ng, ng, ng), dtype=complex), 1.0, edges)
     assert cnt[0] == 0
     assert cnt[1] == 6 + 12 + 8  # |n| = 1, sqrt(2), sqrt(3)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("shift", [False, True])
+def test_single_node_value_equals_the_scattered_grid(p, shift):
+    # gather at one node (used for sampled full-size checks) against the scatter over all nodes,
+    # including nodes whose stencils wrap around the periodic box
+    ng = 10
+    u = np.random.default_rng(90 + p).uniform(0.0, ng, size=(400, 3))
+    w = np.random.default_rng(91).uniform(0.5, 1.5, size=400)
+    rho = assign.assign_units(u, ng, p, weights=w, shift=shift)
+    for node in [(0, 0, 0), (9, 0, 5), (3, 9, 9), (5, 5, 5), (9, 9, 9)]:
+        assert assign.node_value(u, ng, p, node, weights=w, shift=shift) == pytest.approx(rho[node], rel=1e-12, abs=1e-14)
+
+
+def test_single_node_value_closed_forms():
+    # a particle on a node: W(0)^3 (PCS 2/3, TSC 3/4, CIC 1); half-way between nodes on x: PCS W(1/2) = 23/48
+    u = np.array([[2.0, 3.0, 4.0]])
+    assert assign.node_value(u, 8, 4, (2, 3, 4)) == pytest.approx((2.0 / 3.0) ** 3, rel=1e-15)
+    assert assign.node_value(u, 8, 3, (2, 3, 4)) == pytest.approx(0.75 ** 3, rel=1e-15)
+    assert assign.node_value(u, 8, 2, (2, 3, 4)) == pytest.approx(1.0, rel=1e-15)
+    v = np.array([[2.5, 3.0, 4.0]])
+    assert assign.node_value(v, 8, 4, (2, 3, 4)) == pytest.approx(23.0 / 48.0 * (2.0 / 3.0) ** 2, rel=1e-15)
