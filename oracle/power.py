@@ -68,3 +68,45 @@ def shot_noise(box, weights=None, n=None):
         return vol / n
     w = np.asarray(weights, dtype=np.float64)
     return vol * np.sum(w * w) / np.sum(w) ** 2
+
+
+def half_complex_weights(ng):
+    """Multiplicity of each stored mode of the half-complex layout [N][N][N/2+1] (i_z <= N/2, i_z = N/2
+    meaning n_z = -N/2): 2 where 0 < i_z < N/2 (the stored mode and its partner -n, whose n_z lies
+    in (-N/2, 0) and is not stored), 1 on the planes i_z = 0 and i_z = N/2, where every mode of the
+    full grid is stored itself."""
+    m = np.full((ng, ng, ng // 2 + 1), 2.0)
+    m[:, :, 0] = 1.0
+    m[:, :, ng // 2] = 1.0
+    return m
+
+
+def cross_power_half(da, db, box, edges=None):
+    """Binned cross power V Re[delta_a(n) conj(delta_b(n))] of two fields given on the half-complex
+    layout, each stored mode counted with the multiplicity of ``half_complex_weights`` (its partner
+    -n contributing the conjugate product, which has the same real part). With da = db this is the
+    auto power over the stored modes and their partners: the N_G^3 vectors of the full grid, except
+    that a partner with a component +N_G/2 stands for the grid's -N_G/2 (the two are the same mode of
+    a periodic grid transform, and different modes of the direct sum of eq:deltaDS).
+
+    Bins as in ``power_spectrum`` (same integer test; counts equal those of the full grid).
+    Returns (P_b, k_eff_b, count_b), NaN for empty bins; no shot noise is subtracted.
+    """
+    ng = da.shape[0]
+    if edges is None:
+        edges = default_edges(ng)
+    nb = len(edges) - 1
+    b = bin_index(ng, edges)[:, :, : ng // 2 + 1].ravel()
+    mult = half_complex_weights(ng).ravel()
+    sel = b >= 0
+    vol = float(box) ** 3
+    prod = vol * np.real(np.asarray(da).ravel() * np.conj(np.asarray(db).ravel()))
+    kf = 2.0 * np.pi / box
+    kmag = kf * np.sqrt(mode_norm2_x4(ng)[:, :, : ng // 2 + 1].ravel() / 4.0)
+    cnt = np.bincount(b[sel], weights=mult[sel], minlength=nb)
+    ssum = np.bincount(b[sel], weights=(mult * prod)[sel], minlength=nb)
+    ksum = np.bincount(b[sel], weights=(mult * kmag)[sel], minlength=nb)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        pk = ssum / cnt
+        keff = ksum / cnt
+    return pk, keff, np.rint(cnt).astype(np.int64)

@@ -255,6 +255,86 @@ def test_accuracy_ordering_against_direct_summation():
     assert e_pcs_i < e_cic_i < e_cic
 
 
+def test_direct_sum_of_lattice_particles_is_the_dft_of_their_counts():
+    # eq:deltaDS with every particle on a grid node (x = j H) is the discrete Fourier transform of the
+    # node counts, computed here by numpy's FFT: pins the sign, the 2 pi / L scale and the signed index.
+    rng = np.random.default_rng(31)
+    ng, box = 8, 40.0
+    nodes = rng.integers(0, ng, size=(300, 3))
+    w = rng.uniform(0.5, 2.0, 300)
+    counts = np.zeros((ng, ng, ng))
+    np.add.at(counts, tuple(nodes.T), w)
+    expect = np.fft.fftn(counts) / w.sum()
+    expect[0, 0, 0] -= 1.0
+    d = direct.direct_modes(nodes * (box / ng), box, ng, weights=w)
+    assert np.max(np.abs(d - expect)) < 1e-13
+
+
+def test_direct_sum_translation_and_hermitian_symmetry():
+    # A rigid shift s of every particle multiplies delta(n != 0) by exp(-i k.s); delta(-n) = conj
+    # delta(n) for any integer n, inside the grid or not (eq:deltaDS is not periodic in n).
+    box = 50.0
+    pos = catalogs.poisson(200, box, seed=33)
+    nv = np.array([[1, 2, 3], [-4, 0, 5], [8, -8, 1], [13, 7, -9], [0, 0, 16]])
+    s = np.array([3.3, -1.25, 7.0])
+    d0 = direct.direct_modes_at(pos, box, nv)
+    d1 = direct.direct_modes_at(np.mod(pos + s, box), box, nv)
+    assert np.max(np.abs(d1 - d0 * np.exp(-2j * np.pi * (nv @ s) / box))) < 1e-13
+    assert np.max(np.abs(direct.direct_modes_at(pos, box, -nv) - np.conj(d0))) < 1e-14
+
+
+def test_direct_sum_poisson_expectation():
+    # eq:ds2pcf with P = 0: for N iid uniform particles E|delta(n)|^2 = 1/N at every n != 0.
+    box, npart = 100.0, 400
+    nv = np.stack(np.meshgrid(np.arange(1, 9), np.arange(-4, 4), np.arange(0, 8), indexing="ij"), -1).reshape(-1, 3)
+    acc = 0.0
+    for seed in range(6):
+        acc += np.mean(np.abs(direct.direct_modes_at(catalogs.poisson(npart, box, seed=40 + seed), box, nv)) ** 2)
+    assert abs(acc / 6 * npart - 1.0) < 0.1  # 3072 exponential variates: std 1.8 %
+
+
+def test_half_complex_cross_power_equals_full_grid_power_for_a_real_grid():
+    # Without interlacing the window-corrected grid density is exactly Hermitian on the signed full
+    # grid (G periodic, W even), so the half-complex sum with multiplicities reproduces the full-grid
+    # bins of the Sec. 2.2 estimator, mode counts included.
+    box, ng = 80.0, 12
+    pos = catalogs.zeldovich(12, box, rms=3.0, seed=34)
+    d = fourier.density_modes(assign.assign(pos, box, ng, 3), 3)
+    pk, ke, cnt = power.power_spectrum(d, box)
+    pk2, ke2, cnt2 = power.cross_power_half(d[:, :, : ng // 2 + 1], d[:, :, : ng // 2 + 1], box)
+    assert np.array_equal(cnt, cnt2)
+    assert np.max(np.abs(pk2 - pk) / pk) < 1e-12
+    assert np.max(np.abs(ke2 - ke) / ke) < 1e-13
+
+
+def test_half_complex_direct_power_by_enumerating_the_mode_set():
+    # The direct-summation power over the stored modes and their partners -n, by brute force: list the
+    # vectors, evaluate eq:deltaDS at each, bin by rounding |n| to the nearest integer in floating point.
+    box, ng = 60.0, 6
+    pos = catalogs.zeldovich(6, box, rms=4.0, seed=35)
+    full = direct.direct_modes(pos, box, ng)
+    half = full[:, :, : ng // 2 + 1]
+    pk, ke, cnt = power.cross_power_half(half, half, box)
+    n = fourier.signed_index(ng)
+    vecs = []
+    for ix, iy, iz in itertools.product(range(ng), range(ng), range(ng // 2 + 1)):
+        v = (n[ix], n[iy], n[iz])
+        if v == (0, 0, 0):
+            continue
+        vecs.append(v)
+        if 0 < iz < ng // 2:
+            vecs.append((-v[0], -v[1], -v[2]))
+    vecs = np.array(vecs)
+    p_modes = box ** 3 * np.abs(direct.direct_modes_at(pos, box, vecs)) ** 2
+    b = np.floor(np.sqrt(np.sum(vecs.astype(np.float64) ** 2, axis=1)) + 0.5).astype(int) - 1
+    for k in range(ng // 2):
+        sel = b == k
+        assert cnt[k] == sel.sum()
+        assert abs(pk[k] - p_modes[sel].mean()) < 1e-12 * pk[k]
+    # the conjugate pair has the same |delta|^2, but a partner outside the signed grid is a new mode
+    assert len(vecs) == ng ** 3 - 1
+
+
 # --- bispectrum (eq:Best, eq:Best2, eq:VBest) ----------------------------------------------------------
 
 def test_bispectrum_fft_form_equals_brute_force():
