@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--box", type=float, default=2000.0)
     ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
+    ap.add_argument("--only-row", choices=["adjoint", "batch", "direct"], default=None,
+                    help="time one secondary row on its own workload and print it (no P(k) step)")
+    ap.add_argument("--ds-nside", type=int, default=128, help="--only-row direct: particles per side")
+    ap.add_argument("--ds-ng", type=int, default=128, help="--only-row direct: grid size")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -181,11 +185,20 @@ def _time_cuda(fn, reps, warm=1):
     return e0.elapsed_time(e1) / reps
 
 
-def measure_rows(dev, host64, big_box):
-    """Times the other hot-path rows on their own workloads (one GB300)."""
+def alu_peak(dev):
+    """Derived FP32 FMA peak (TFLOP/s): SMs x 128 FP32 lanes x 2 flop x the measured maximum SM clock."""
     import torch
 
-    from paper_1512_07295_gb300 import api, catalogs, ffi
+    peaks = measured_peaks() or {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return nsm * 128 * 2 * sm_max * 1e6 / 1e12
+
+
+def row_bispectrum(dev, host64, big_box):
+    import torch
+
+    from paper_1512_07295_gb300 import api, ffi
 
     rows = {}
     # a7: FFT bispectrum, 16 shells of width 4 k_f (up to k_N/2) on N_G = 256, delta of the large catalogue
@@ -213,6 +226,15 @@ def measure_rows(dev, host64, big_box):
                           "counts_once_s": t_counts}
     del ws, delta, counts, out
     torch.cuda.empty_cache()
+    return rows["bispectrum"]
+
+
+def row_adjoint(dev):
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs, ffi
+
+    rows = {}
     # a8: adjoint, 128^3 Zel'dovich particles, L = 500, N_G = 128, PCS + interlacing, FP32
     cfg = api.Config(ng=128, box=500.0, prec="fp32")
     pos = catalogs.zeldovich_torch(128, 500.0, 4.0, seed=6, device=dev)
@@ -229,6 +251,15 @@ def measure_rows(dev, host64, big_box):
                                    "recomputed inside)", "ms_per_call": ms, "particles_per_s": pos.shape[0] / (ms * 1e-3)}
     del wsb, g, pos
     torch.cuda.empty_cache()
+    return rows["adjoint"]
+
+
+def row_batch(dev):
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs
+
+    rows = {}
     # a9: 512 mock catalogues, N_P log-uniform in [1e5, 2e6], L = 1000, N_G = 128, PCS + interlacing, FP32
     cfg = api.Config(ng=128, box=1000.0, prec="fp32")
     sizes = catalogs.batch_sizes(512, 1e5, 2e6, seed=4)
@@ -268,7 +299,53 @@ def measure_rows(dev, host64, big_box):
     del graph
     del wsc, cells
     torch.cuda.empty_cache()
-    return rows
+    return rows["batch"]
+
+
+def row_direct(dev, alu_peak_tflops, nside=128, ng=128):
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs, ffi
+
+    rows = {}
+    # direct summation (eq:deltaDS): 128^3 Zel'dovich particles, L = 50, every stored mode of N_G = 128,
+    # then the Sec. 3.2 comparison of the PCS + interlacing grid estimate with it
+    cfg = api.Config(ng=ng, box=50.0, order=4, interlace=True, prec="fp32")
+    pos = catalogs.zeldovich_torch(nside, 50.0, 1.0, seed=7, device=dev)
+    n = pos.shape[0]
+    wsd = api.workspace(cfg, n, ffi.PK_WS_DIRECT, dev)
+    ds = torch.empty((ng, ng, ng // 2 + 1), dtype=torch.complex64, device=dev)
+
+    def direct():
+        ffi.check(ffi.lib().pk_direct_modes(api.ctypes.byref(cfg.c()), api._p(pos), ffi.PK_POS_F64_XYZ, None, n, api._p(ds),
+                                            api._p(wsd), wsd.numel(), api._stream(dev)))
+
+    ms = _time_cuda(direct, 3)
+    pairs = float(n) * ng * ng * (ng // 2 + 1)
+    tflops = 8.0 * pairs / (ms * 1e-3) / 1e12
+    p_ds, _, _ = api.cross_power(ds, ds, cfg)
+    _, _, _, dg = api.power(pos, cfg, return_delta=True)
+    p_g, _, _ = api.cross_power(dg, dg, cfg)
+    p_x, _, _ = api.cross_power(dg, ds, cfg)
+    shot = 50.0 ** 3 / n  # both spectra corrected by 1/nbar as in Sec. 3.2
+    err_auto = torch.abs((p_g - shot) / (p_ds - shot) - 1.0).max().item()
+    err_cross = torch.abs(p_x / (p_ds - shot) - 1.0).max().item()
+    rows["direct"] = {"workload": f"direct summation of delta(k) (eq:deltaDS): {nside}^3 ZA particles, L=50, all "
+                                  f"{ng * ng * (ng // 2 + 1)} stored modes of N_G={ng}, FP32 terms with compensated sums",
+                      "ms_per_call": ms, "pairs_per_s": pairs / (ms * 1e-3),
+                      "roofline": {"bound": "alu", "achieved": tflops, "peak": alu_peak_tflops, "unit": "TFLOP/s",
+                                   "frac": tflops / alu_peak_tflops, "flop_per_pair": 8,
+                                   "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"},
+                      "pcs_interlace_vs_ds_max_rel": {"auto": err_auto, "cross": err_cross}}
+    del wsd, ds, dg, pos
+    torch.cuda.empty_cache()
+    return rows["direct"]
+
+
+def measure_rows(dev, host64, big_box, alu_peak_tflops):
+    """Times the other hot-path rows on their own workloads (one GB300)."""
+    return {"bispectrum": row_bispectrum(dev, host64, big_box), "adjoint": row_adjoint(dev), "batch": row_batch(dev),
+            "direct": row_direct(dev, alu_peak_tflops)}
 
 
 def run_reference(a):
@@ -330,6 +407,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = ffi.lib()
+    if a.only_row:
+        row = {"adjoint": lambda: row_adjoint(dev), "batch": lambda: row_batch(dev),
+               "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng)}[a.only_row]()
+        if rank == 0:
+            print(json.dumps({"row": a.only_row, **row}), flush=True)
+        return
 
     n = a.nside ** 3
     cfg = api.Config(ng=a.ng, box=a.box, order=4, interlace=True, prec="fp32")
@@ -398,9 +481,7 @@ def main():
 
     peaks = measured_peaks() or {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak_tflops = nsm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max clock
+    alu_peak_tflops = alu_peak(dev)  # FP32 FMA lanes x 2 flop x max clock
     p3 = cfg.order ** 3
     assign_flop = 2.0 * 2 * p3 * n  # two grids, p^3 multiply-adds per particle each
     assign_bytes = 16.0 * n + 2 * 4.0 * a.ng ** 3  # particle records read once, two grids written once
@@ -427,7 +508,7 @@ def main():
                      "traffic": traffic, "traffic_source": WALK_TRAFFIC_SOURCE if traffic else None,
                      "algorithmic_bytes": assign_bytes, "hbm_achieved_gbs": achieved_gbs,
                      "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                     "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:g} MHz",
+                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x the maximum SM clock",
                      "timing": "CUDA events on the library's stream around the assignment launch, mean over "
                                f"{nprof} steps"},
         "clocks": clk,
@@ -487,7 +568,7 @@ def main():
         sample = host64[torch.from_numpy(idx)].numpy()
         rate, det = oracle_sample_rate(sample, n, a.box, a.ng, with_fft=True)
         cores = len(os.sched_getaffinity(0))
-        result["rows"] = measure_rows(dev, host64, a.box)
+        result["rows"] = measure_rows(dev, host64, a.box, alu_peak_tflops)
         result["cpu_baseline"] = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
                                   "sample": f"2^16 random particles of the catalogue assigned to both grids (single-threaded "
                                             f"NumPy) + one full N_G={a.ng} FFT (scipy, {cores} workers), deconvolution and "

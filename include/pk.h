@@ -102,7 +102,9 @@ typedef enum {
   PK_WS_BACKWARD = 5,
   PK_WS_BISPECTRUM = 6,
   PK_WS_BISPECTRUM_COUNTS = 7,
-  PK_WS_POWER_HOST = 8
+  PK_WS_POWER_HOST = 8,
+  PK_WS_DIRECT = 9,
+  PK_WS_CROSS = 10
 } pk_ws_kind;
 
 /* Fills cfg with the paper's default binning for an N grid: bins centred on b k_f, b = 1..N/2
@@ -227,6 +229,37 @@ pk_status pk_power_backward(const pk_config* cfg, const void* pos_dev, int32_t p
 pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* offsets_host,
                          const pk_cellpos* pos_dev, double* pk_dev, int64_t* nmodes_dev, int32_t batch,
                          void* ws, size_t ws_bytes, void* stream);
+
+/* Direct summation (eq:deltaDS, Sec. 2.2; the alias-free benchmark of Sec. 3.2): for every stored
+ * mode of the half-complex layout of pk_fft_estimate (index (i_x, i_y, i_z) <-> signed n, i_z = N/2
+ * meaning n_z = -N/2),
+ *   delta(n) = (1/sum_i w_i) sum_i w_i exp(-2 pi i n.x_i/L),  delta(0) = 0,
+ * with no grid, no window and no aliasing; cfg->order and cfg->interlace are ignored. Unlike a grid
+ * transform the sum is not periodic in n: the stored n_i = -N/2 is that vector, not +N/2. Cost
+ * N_P x N^2 (N/2+1) complex multiply-adds. Positions in either format (FP64 wrapped into [0, L), or
+ * pk_cellpos of the grid cfg->ng), w_dev float[n] or NULL for unit weights; n >= 1.
+ * Output delta_k_dev: complex float (PK_FP32) or complex double (PK_FP64, PK_FIXED64), overwritten.
+ * Arithmetic: each phase is the exact integer product of n with a fixed-point fraction x/L mod 1
+ * (32 bits in PK_FP32, 64 bits otherwise) before its sine and cosine are taken; PK_FP32 sums the
+ * products in FP32 over chunks of 64 particles with compensated chunk totals (relative error of a
+ * few 1e-7 of sum |w|), PK_FP64 / PK_FIXED64 compute in FP64. Partial sums of particle slices are
+ * added in FP64 with atomics, so the last bits may differ between runs.
+ * Invalid positions set PK_DERR_NONFINITE / PK_DERR_CELLRANGE and count at x = 0 with their weight.
+ * Workspace: pk_workspace_size(cfg, n, PK_WS_DIRECT). */
+pk_status pk_direct_modes(const pk_config* cfg, const void* pos_dev, int32_t pos_format, const float* w_dev,
+                          int64_t n, void* delta_k_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Binned cross power of two fields on the half-complex layout (Sec. 3.2 compares the grid estimate
+ * delta^G with the direct sum through P_{G-DS} ~ <delta^G(k) delta(-k)> and the auto spectra): for
+ * each bin of cfg, pk_dev[b] = mean over the modes of V Re[a(n) conj(b(n))], where a stored mode with
+ * 0 < i_z < N/2 counts twice (its partner -n, not stored, contributes the conjugate product) and the
+ * planes i_z = 0 and i_z = N/2 count once; nmodes_dev[b] the number of modes so counted (equal to
+ * the full-grid count of pk_power), kmean_dev[b] their mean |k| (may be NULL). With a = b this is
+ * the auto power of a field that is Hermitian in n, such as the direct sum. No shot noise is
+ * subtracted; empty bins give NaN. delta_a_dev / delta_b_dev: complex float (PK_FP32) or complex
+ * double. Workspace: pk_workspace_size(cfg, 0, PK_WS_CROSS). */
+pk_status pk_cross_power(const pk_config* cfg, const void* delta_a_dev, const void* delta_b_dev, double* pk_dev,
+                         double* kmean_dev, int64_t* nmodes_dev, void* ws, size_t ws_bytes, void* stream);
 
 /* No-allocation variant of the fused estimate (a5+a6), for callers that cannot allocate device
  * memory or pass a workspace: code running inside a framework that owns all device memory and

@@ -196,6 +196,35 @@ def power_binned(binned, cfg, return_delta=False, ws=None, out=None):
     return (pk, km, nm, delta) if return_delta else (pk, km, nm)
 
 
+def direct_modes(pos, cfg, weights=None, ws=None):
+    """delta(n) by direct summation (eq:deltaDS) on the half-complex layout (ng, ng, ng/2+1), no window
+    and no aliasing; cfg.order and cfg.interlace are ignored."""
+    fmt = _pos_format(pos)
+    n = pos.shape[0]
+    w = _weights(weights, n, pos.device)
+    ctype = torch.complex64 if cfg.prec == "fp32" else torch.complex128
+    delta = torch.empty(half_shape(cfg.ng), dtype=ctype, device=pos.device)
+    if ws is None:
+        ws = workspace(cfg, n, ffi.PK_WS_DIRECT, pos.device)
+    check(ffi.lib().pk_direct_modes(ctypes.byref(cfg.c()), _p(pos), fmt, _p(w), n, _p(delta), _p(ws), ws.numel(),
+                                    _stream(pos.device)))
+    return delta
+
+
+def cross_power(delta_a, delta_b, cfg, ws=None):
+    """Binned V Re[delta_a conj(delta_b)] of two half-complex fields (pk_cross_power): (pk, kmean, nmodes)."""
+    ctype = torch.complex64 if cfg.prec == "fp32" else torch.complex128
+    for d in (delta_a, delta_b):
+        if d.dtype != ctype or tuple(d.shape) != half_shape(cfg.ng) or not d.is_contiguous() or not d.is_cuda:
+            raise ValueError(f"fields: contiguous {ctype} CUDA tensors of shape {half_shape(cfg.ng)}")
+    pk, km, nm = _outputs(cfg, delta_a.device)
+    if ws is None:
+        ws = workspace(cfg, 0, ffi.PK_WS_CROSS, delta_a.device)
+    check(ffi.lib().pk_cross_power(ctypes.byref(cfg.c()), _p(delta_a), _p(delta_b), _p(pk), _p(km), _p(nm), _p(ws),
+                                   ws.numel(), _stream(delta_a.device)))
+    return pk, km, nm
+
+
 def bispectrum_ntri(nshells):
     return int(ffi.lib().pk_bispectrum_ntri(int(nshells)))
 

@@ -15,7 +15,10 @@ SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", SRC]
-SOURCES = ["prepare.cu", "assign.cu", "assign_walk.cu", "estimate.cu", "api.cu", "bispec.cu", "adjoint.cu", "batch.cu", "noalloc.cu"]
+SOURCES = [
+    "prepare.cu", "assign.cu", "assign_walk.cu", "estimate.cu", "api.cu", "bispec.cu", "adjoint.cu", "batch.cu",
+    "noalloc.cu", "direct.cu",
+]
 
 
 def _nvcc():

@@ -26,18 +26,6 @@ __device__ __forceinline__ CC<R> cj(CC<R> a) {
   return {a.x, -a.y};
 }
 
-__device__ __forceinline__ int bin_of_adj(long long v4, int lo2, int w2, int nbins) {
-  if (v4 == 0) return -1;
-  int b = int(floorf((sqrtf(float(v4)) - float(lo2)) / float(w2)));
-  if (b < 0) b = 0;
-  long long e = (long long)lo2 + (long long)b * w2;
-  while (b > 0 && e * e > v4) { --b; e -= w2; }
-  if (e * e > v4) return -1;
-  long long e1 = e + w2;
-  while (e1 * e1 <= v4) { ++b; e1 += w2; if (b >= nbins) return -1; }
-  return b < nbins ? b : -1;
-}
-
 // In place: (G_1, G_2) at every stored slot -> (X_1, X_2); window and phases evaluated in FP64.
 template <typename R>
 __global__ void k_adjoint_modes(CC<R>* __restrict__ G1, CC<R>* __restrict__ G2, int ng, int order, int interlace,
@@ -54,7 +42,7 @@ __global__ void k_adjoint_modes(CC<R>* __restrict__ G1, CC<R>* __restrict__ G2, 
     const int iy = int(row % ng), ix = int(row / ng);
     const int n[3] = {signed_mode(ix, ng), signed_mode(iy, ng), iz == half ? -half : iz};
     const long long n2 = (long long)n[0] * n[0] + (long long)n[1] * n[1] + (long long)n[2] * n[2];
-    const int b = bin_of_adj(4 * n2, lo2, w2, nbins);
+    const int b = bin_of(4 * n2, lo2, w2, nbins);
     CC<R> x1 = {R(0), R(0)}, x2 = {R(0), R(0)};
     if (b >= 0 && counts[b] > 0) {
       // window, phases (signed index of the mode and of its partner on each axis)

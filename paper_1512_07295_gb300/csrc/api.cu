@@ -399,7 +399,8 @@ int32_t pk_device_error(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned v = 0;
   if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
-  if (take_err_prepare(&v) != 0 || take_err_assign(&v) != 0 || take_err_walk(&v) != 0) return -1;
+  if (take_err_prepare(&v) != 0 || take_err_assign(&v) != 0 || take_err_walk(&v) != 0 || take_err_direct(&v) != 0)
+    return -1;
   return int32_t(v);
 }
 
@@ -452,6 +453,9 @@ size_t pk_workspace_size(const pk_config* cfg, int64_t n, int32_t kind) {
     }
     case PK_WS_BACKWARD:
       return backward_ws(cfg, n, &out) == PK_OK ? out : 0;
+    case PK_WS_DIRECT:
+    case PK_WS_CROSS:
+      return direct_ws(cfg, n, kind == PK_WS_CROSS, &out) == PK_OK ? out : 0;
     case PK_WS_BISPECTRUM:
     case PK_WS_BISPECTRUM_COUNTS:
       if (n < 1 || n > 64) {

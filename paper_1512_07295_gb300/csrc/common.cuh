@@ -120,6 +120,21 @@ __device__ __forceinline__ int wrap(int i, int n) {
 // Signed mode index of FFT slot i (slot N/2 is -N/2).
 __device__ __forceinline__ int signed_mode(int i, int n) { return i < n / 2 ? i : i - n; }
 
+// Bin of a mode with 4|n|^2 = v4 for the edges e_b = lo2 + b w2 (units of k_f/2): e_b^2 <= v4 <
+// e_{b+1}^2, decided exactly in integers after a floating-point guess; -1 outside the bins and for n = 0.
+__device__ __forceinline__ int bin_of(long long v4, int lo2, int w2, int nbins) {
+  if (v4 == 0) return -1;
+  const float r = sqrtf(float(v4));
+  int b = int(floorf((r - float(lo2)) / float(w2)));
+  if (b < 0) b = 0;
+  long long e = (long long)lo2 + (long long)b * w2;
+  while (b > 0 && e * e > v4) { --b; e -= w2; }
+  if (e * e > v4) return -1;
+  long long e1 = e + w2;
+  while (e1 * e1 <= v4) { ++b; e1 += w2; if (b >= nbins) return -1; }
+  return b < nbins ? b : -1;
+}
+
 // Fixed-point scale 2^F of the deterministic grids, F = 62 - ceil(log2(sum |w|)): no node can hold
 // more than the total mass, so the int64 sums cannot overflow.
 __device__ __forceinline__ float fixed_scale(double total) {

@@ -46,20 +46,6 @@ __global__ void k_tables(R* tab, int ng, int order) {
 
 size_t estimate_table_bytes(int ng, bool dbl) { return size_t(3) * ng * (dbl ? 8 : 4); }
 
-__device__ __forceinline__ int bin_of(long long v4, int lo2, int w2, int nbins) {
-  if (v4 == 0) return -1;
-  const float r = sqrtf(float(v4));
-  int b = int(floorf((r - float(lo2)) / float(w2)));
-  // exact correction with integers
-  if (b < 0) b = 0;
-  long long e = (long long)lo2 + (long long)b * w2;
-  while (b > 0 && e * e > v4) { --b; e -= w2; }
-  if (e * e > v4) return -1;
-  long long e1 = e + w2;
-  while (e1 * e1 <= v4) { ++b; e1 += w2; if (b >= nbins) return -1; }
-  return b < nbins ? b : -1;
-}
-
 // Per-warp private bin accumulators (single pass, non-deterministic mode). Within one warp item the
 // bins of the run ends are distinct (|n| grows with i_z), so a warp updates its own copy without
 // atomics: FP32 mode keeps each sum as an FP32 pair (value, compensation; Neumaier's summation,

@@ -110,5 +110,6 @@ void prof_mark(int k, cudaStream_t s);
 pk_status bispectrum_ws(const pk_config* c, int nshells, bool counts, size_t* out);
 pk_status backward_ws(const pk_config* c, int64_t n, size_t* out);
 pk_status batch_ws(const pk_config* c, int64_t nmax, size_t* out);
+pk_status direct_ws(const pk_config* c, int64_t n, bool cross, size_t* out);
 
 }  // namespace pk

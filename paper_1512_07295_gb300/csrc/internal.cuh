@@ -17,6 +17,7 @@ void count_launch(int k = 1);  // number of kernels this library launched (pk_pr
 int take_err_prepare(unsigned* acc);
 int take_err_assign(unsigned* acc);
 int take_err_walk(unsigned* acc);
+int take_err_direct(unsigned* acc);
 // Raises a kernel's dynamic shared-memory limit to at least smem bytes, once per (kernel, device) and
 // size: calls captured in a CUDA graph after the first eager call then issue launches only.
 cudaError_t ensure_dynamic_smem(const void* kernel, size_t smem);

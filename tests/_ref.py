@@ -47,3 +47,19 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+def pack_cellpos(u, ng):
+    """pk_cellpos records (int32 (n,4)) of grid-unit positions u (FP64), made on the host: cell index
+    floor(u) mod N on each axis, FP32 offset u - floor(u) (an offset that rounds up to 1 moves to the
+    next cell with offset 0). cellpos_to_units gives back the exact positions of the records."""
+    u = np.mod(np.asarray(u, dtype=np.float64), ng)
+    c = np.floor(u).astype(np.int64)
+    f = (u - c).astype(np.float32)
+    up = f >= np.float32(1.0)
+    c = np.where(up, c + 1, c) % ng
+    f = np.where(up, np.float32(0.0), f).astype(np.float32)
+    out = np.empty((len(u), 4), dtype=np.int32)
+    out[:, 0] = ((c[:, 0] << 20) | (c[:, 1] << 10) | c[:, 2]).astype(np.uint32).view(np.int32)
+    out[:, 1:] = f.view(np.int32)
+    return out
