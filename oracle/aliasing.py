@@ -8,12 +8,16 @@ Test infrastructure (see ``oracle/__init__``); never imported by the product pat
   [1 + (-1)^(m_x+m_y+m_z)]/2 (interlacing). With x = n/N_G, |W(k - m k_s)| = |sinc(pi (x - m))|^p.
 - ``fres_1d`` / ``fres_1d_hurwitz``: the one-dimensional residual factor of eq:res1Di and
   eq:res1Dnoi as a truncated image sum and in its Hurwitz-zeta closed form.
+- ``fres_3d``: the residual factor F_res(k) = sum_{m != 0} theta_m |w_m(k)|^2 of eq:res (reading:
+  |w_m|, not |w_2m|) on three-dimensional modes, from the one-dimensional forms.
 """
 
 import numpy as np
 import scipy.special
 
 from .bspline import sinc
+from .fourier import signed_index
+from .power import bin_index, default_edges
 
 
 def _image_sums(x, p, mmax):
@@ -57,3 +61,47 @@ def fres_1d_hurwitz(x, p, interlace):
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
     y = x / 2.0 if interlace else x
     return y ** (2 * p) * (scipy.special.zeta(2 * p, 1.0 - y) + scipy.special.zeta(2 * p, 1.0 + y))
+
+
+def fres_3d(n, ng, p, interlace):
+    """F_res(n) = sum_{m != 0} theta_m prod_i (x_i / (x_i - m_i))^{2p}, x = n / N_G (eq:res with
+    |w_m(k)|^2 = |W(k - m k_s)|^2 / |W(k)|^2 and |W| = sinc^p).
+
+    The sum over all m factorises per axis: with f(x) = sum_{m != 0} (x/(x-m))^{2p} (eq:res1Dnoi) and
+    the alternating f'(x) = sum_{m != 0} (-1)^m (x/(x-m))^{2p} = 2 F_int(x) - f(x) (F_int of eq:res1Di
+    keeps the even images), theta_m = 1 gives prod(1 + f_i) - 1 and theta_m = [1 + (-1)^{sum m}]/2
+    gives [prod(1 + f_i) + prod(1 + f'_i)]/2 - 1. The products are expanded so that no 1 is
+    subtracted from a sum close to 1 (F_res is tiny at small k)."""
+    n = np.asarray(n, dtype=np.float64)
+    x = n / ng
+    f = [fres_1d_hurwitz(x[..., a].ravel(), p, False).reshape(x.shape[:-1]) for a in range(3)]
+
+    def excess(g):  # prod(1 + g_i) - 1
+        return g[0] + g[1] + g[2] + g[0] * g[1] + g[0] * g[2] + g[1] * g[2] + g[0] * g[1] * g[2]
+
+    if not interlace:
+        return excess(f)
+    fi = [fres_1d_hurwitz(x[..., a].ravel(), p, True).reshape(x.shape[:-1]) for a in range(3)]
+    fa = [2.0 * fi[a] - f[a] for a in range(3)]
+    return 0.5 * (excess(f) + excess(fa))
+
+
+def fres_binned(ng, p, interlace, edges=None):
+    """Mean and maximum of F_res(n) over the modes of each bin of the full N_G^3 grid (bins as in
+    ``power.power_spectrum``), with the integer mode counts; NaN for empty bins."""
+    if edges is None:
+        edges = default_edges(ng)
+    nb = len(edges) - 1
+    s = signed_index(ng)
+    n = np.stack(np.meshgrid(s, s, s, indexing="ij"), -1).reshape(-1, 3)
+    b = bin_index(ng, edges).ravel()
+    sel = b >= 0
+    f = fres_3d(n[sel], ng, p, interlace)
+    cnt = np.bincount(b[sel], minlength=nb).astype(np.int64)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mean = np.bincount(b[sel], weights=f, minlength=nb) / cnt
+    mx = np.full(nb, np.nan)
+    for k in range(nb):
+        if cnt[k]:
+            mx[k] = f[b[sel] == k].max()
+    return mean, mx, cnt

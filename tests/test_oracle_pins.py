@@ -335,6 +335,51 @@ def test_half_complex_direct_power_by_enumerating_the_mode_set():
     assert len(vecs) == ng ** 3 - 1
 
 
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("interlace", [False, True])
+def test_fres_3d_is_the_poisson_shot_noise_excess(p, interlace):
+    # eq:Pknoint with P = 0: E[P(n)] n_bar = sum_m theta_m |W(k - m k_s)|^2 / |W(k)|^2 = 1 + F_res(n); the
+    # expectation is summed as truncated sinc^{2p} image sums, F_res through the Hurwitz-zeta forms
+    rng = np.random.default_rng(61)
+    ng = 32
+    n = rng.integers(-16, 16, (60, 3))
+    n = n[np.abs(n).max(axis=1) >= 6]  # away from k = 0, where 1 + F_res - 1 loses its digits
+    e = aliasing.shot_noise_expectation(n, ng, p, interlace, 1.0, mmax=4000)
+    f = aliasing.fres_3d(n, ng, p, interlace)
+    assert np.max(np.abs(e - 1.0 - f) / (1.0 + f)) < 2e-10
+
+
+def test_fres_3d_brute_force_image_sum():
+    # the definition summed directly over a cube of images |m_i| <= 12 (PCS terms fall as |m|^-8: the
+    # truncated tail is below 1e-6 of F_res even where the interlacing leaves only |m| >= 2 images)
+    ng, p, mmax = 16, 4, 12
+    m = np.arange(-mmax, mmax + 1)
+    M = np.stack(np.meshgrid(m, m, m, indexing="ij"), -1).reshape(-1, 3)
+    M = M[np.any(M != 0, axis=1)]
+    for n in ([1, 0, 0], [3, 2, 1], [8, -8, 5], [-8, -8, -8], [5, 0, -7]):
+        x = np.array(n, dtype=np.float64) / ng
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = np.where(M == 0, 1.0, (x[None, :] / (x[None, :] - M)) ** (2 * p))
+        terms = np.prod(g, axis=1)
+        theta = (M.sum(axis=1) % 2 == 0).astype(float)
+        for inter, th in ((False, 1.0), (True, theta)):
+            ref = np.sum(th * terms)
+            got = aliasing.fres_3d(np.array([n]), ng, p, inter)[0]
+            assert abs(got - ref) <= 1e-6 * ref
+
+
+def test_fres_3d_on_an_axis_is_the_one_dimensional_form():
+    # eq:res1Dnoi / eq:res1Di are F_res along a grid axis
+    ng = 64
+    k = np.arange(1, 33)
+    n = np.stack([k, 0 * k, 0 * k], 1)
+    for p in (1, 2, 4):
+        for inter in (False, True):
+            got = aliasing.fres_3d(n, ng, p, inter)
+            ref = aliasing.fres_1d(k / ng, p, inter, mmax=200000)
+            assert np.max(np.abs(got - ref) / ref) < (2e-5 if p == 1 else 1e-10)
+
+
 # --- bispectrum (eq:Best, eq:Best2, eq:VBest) ----------------------------------------------------------
 
 def test_bispectrum_fft_form_equals_brute_force():
