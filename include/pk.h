@@ -104,7 +104,8 @@ typedef enum {
   PK_WS_BISPECTRUM_COUNTS = 7,
   PK_WS_POWER_HOST = 8,
   PK_WS_DIRECT = 9,
-  PK_WS_CROSS = 10
+  PK_WS_CROSS = 10,
+  PK_WS_ALIASING = 11
 } pk_ws_kind;
 
 /* Fills cfg with the paper's default binning for an N grid: bins centred on b k_f, b = 1..N/2
@@ -260,6 +261,18 @@ pk_status pk_direct_modes(const pk_config* cfg, const void* pos_dev, int32_t pos
  * double. Workspace: pk_workspace_size(cfg, 0, PK_WS_CROSS). */
 pk_status pk_cross_power(const pk_config* cfg, const void* delta_a_dev, const void* delta_b_dev, double* pk_dev,
                          double* kmean_dev, int64_t* nmodes_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Residual aliasing factor (eq:res, Sec. 3.2): for every mode n of the full N^3 grid,
+ *   F_res(n) = sum_{m != 0} theta_m |W(k - m k_s)|^2 / |W(k)|^2,  |W| = sinc^p (p = cfg->order),
+ * with theta_m = 1, or [1 + (-1)^{m_x+m_y+m_z}]/2 when cfg->interlace (the images the interlacing
+ * cancels). It factorises per axis into the one-dimensional forms of eq:res1Dnoi / eq:res1Di
+ * (Hurwitz zeta functions, evaluated in FP64). Per bin of cfg: fres_mean_dev[b] the mean of F_res
+ * over the bin's modes, fres_max_dev[b] its largest value (may be NULL), kmean_dev[b] the mean |k|
+ * (may be NULL), nmodes_dev[b] the mode count (as pk_power); NaN for empty bins. The window-corrected
+ * power of a Poisson catalogue has expectation (1 + F_res(n)) / nbar at every mode (eq:Pknoint with
+ * P = 0). Workspace: pk_workspace_size(cfg, 0, PK_WS_ALIASING). */
+pk_status pk_aliasing_residual(const pk_config* cfg, double* fres_mean_dev, double* fres_max_dev, double* kmean_dev,
+                               int64_t* nmodes_dev, void* ws, size_t ws_bytes, void* stream);
 
 /* No-allocation variant of the fused estimate (a5+a6), for callers that cannot allocate device
  * memory or pass a workspace: code running inside a framework that owns all device memory and

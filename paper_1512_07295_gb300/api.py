@@ -225,6 +225,18 @@ def cross_power(delta_a, delta_b, cfg, ws=None):
     return pk, km, nm
 
 
+def aliasing_residual(cfg, device="cuda"):
+    """Per-bin mean and maximum of the residual aliasing factor F_res (eq:res) for cfg's order and
+    interlacing, with the mean |k| and mode counts (pk_aliasing_residual): (mean, max, kmean, nmodes)."""
+    nb = cfg.nb
+    mean, mx, km = (torch.empty(nb, dtype=torch.float64, device=device) for _ in range(3))
+    nm = torch.empty(nb, dtype=torch.int64, device=device)
+    ws = workspace(cfg, 0, ffi.PK_WS_ALIASING, device)
+    check(ffi.lib().pk_aliasing_residual(ctypes.byref(cfg.c()), _p(mean), _p(mx), _p(km), _p(nm), _p(ws), ws.numel(),
+                                         _stream(torch.device(device))))
+    return mean, mx, km, nm
+
+
 def bispectrum_ntri(nshells):
     return int(ffi.lib().pk_bispectrum_ntri(int(nshells)))
 

@@ -456,6 +456,8 @@ size_t pk_workspace_size(const pk_config* cfg, int64_t n, int32_t kind) {
     case PK_WS_DIRECT:
     case PK_WS_CROSS:
       return direct_ws(cfg, n, kind == PK_WS_CROSS, &out) == PK_OK ? out : 0;
+    case PK_WS_ALIASING:
+      return aliasing_ws(cfg, &out) == PK_OK ? out : 0;
     case PK_WS_BISPECTRUM:
     case PK_WS_BISPECTRUM_COUNTS:
       if (n < 1 || n > 64) {

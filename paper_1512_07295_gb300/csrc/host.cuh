@@ -111,5 +111,6 @@ pk_status bispectrum_ws(const pk_config* c, int nshells, bool counts, size_t* ou
 pk_status backward_ws(const pk_config* c, int64_t n, size_t* out);
 pk_status batch_ws(const pk_config* c, int64_t nmax, size_t* out);
 pk_status direct_ws(const pk_config* c, int64_t n, bool cross, size_t* out);
+pk_status aliasing_ws(const pk_config* c, size_t* out);
 
 }  // namespace pk

@@ -15,7 +15,7 @@ PK_OK, PK_EINVAL, PK_ESIZE, PK_ECUDA, PK_ECUFFT, PK_ETIMEOUT, PK_EDEVICE = range
 PK_FP64, PK_FP32, PK_FIXED64 = 0, 1, 2
 PK_POS_F64_XYZ, PK_POS_CELL_F32OFF = 0, 1
 (PK_WS_ASSIGN, PK_WS_FFT_ESTIMATE, PK_WS_POWER, PK_WS_POWER_BINNED, PK_WS_BIN, PK_WS_BACKWARD, PK_WS_BISPECTRUM,
- PK_WS_BISPECTRUM_COUNTS, PK_WS_POWER_HOST, PK_WS_DIRECT, PK_WS_CROSS) = range(11)
+ PK_WS_BISPECTRUM_COUNTS, PK_WS_POWER_HOST, PK_WS_DIRECT, PK_WS_CROSS, PK_WS_ALIASING) = range(12)
 PK_DERR_NONFINITE, PK_DERR_CELLRANGE, PK_DERR_TIMEOUT, PK_DERR_ORDER = 1, 2, 4, 8
 
 
@@ -61,6 +61,7 @@ SIGNATURES = {
                                  c_void_p]),
     "pk_direct_modes": (c_int32, [_CFG, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pk_cross_power": (c_int32, [_CFG, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pk_aliasing_residual": (c_int32, [_CFG, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pk_estimate_noalloc": (c_int32, [_CFG, c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pk_profile_enable": (c_int32, [c_int32]),
     "pk_profile_read": (c_int32, [c_void_p, c_int32]),
