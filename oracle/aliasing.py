@@ -29,20 +29,35 @@ def _image_sums(x, p, mmax):
     return t.sum(axis=1), (t * sgn[None, :]).sum(axis=1)
 
 
-def shot_noise_expectation(n, ng, p, interlace, shot, mmax=2000):
-    """E[P(n)] for a uniform random catalogue (n: (..., 3) integer modes, n != 0)."""
+def _parities(interlace, shifts):
+    """Per grid and axis, whether the shift is an odd number of half cells (None: 1 or 2 grids)."""
+    if shifts is None:
+        shifts = [(0.0, 0.0, 0.0), (0.5, 0.5, 0.5)] if interlace else [(0.0, 0.0, 0.0)]
+    return [[int(round(2 * d)) % 2 == 1 for d in sh] for sh in shifts]
+
+
+def shot_noise_expectation(n, ng, p, interlace, shot, mmax=2000, shifts=None):
+    """E[P(n)] for a uniform random catalogue (n: (..., 3) integer modes, n != 0). With ``shifts`` (grid
+    units, multiples of 1/2) the grids of multi-grid interlacing: image m is kept with weight
+    (1/J) sum_j (-1)^{m.(2 d_j)}, so per grid each axis contributes its plain image sum (even shift)
+    or its alternating one (odd number of half cells)."""
     n = np.asarray(n, dtype=np.float64)
     x = n / ng
-    even = np.ones(x.shape[:-1])
-    alt = np.ones(x.shape[:-1])
+    sums, alts = [], []
     win = np.ones(x.shape[:-1])
     for a in range(3):
         s, sa = _image_sums(x[..., a].ravel(), p, mmax)
-        even = even * s.reshape(x.shape[:-1])
-        alt = alt * sa.reshape(x.shape[:-1])
+        sums.append(s.reshape(x.shape[:-1]))
+        alts.append(sa.reshape(x.shape[:-1]))
         win = win * (sinc(np.pi * x[..., a]) ** (2 * p))
-    num = 0.5 * (even + alt) if interlace else even
-    return shot * num / win
+    par = _parities(interlace, shifts)
+    num = np.zeros(x.shape[:-1])
+    for odd in par:
+        term = np.ones(x.shape[:-1])
+        for a in range(3):
+            term = term * (alts[a] if odd[a] else sums[a])
+        num += term
+    return shot * num / len(par) / win
 
 
 def fres_1d(x, p, interlace, mmax=100000):
@@ -63,7 +78,7 @@ def fres_1d_hurwitz(x, p, interlace):
     return y ** (2 * p) * (scipy.special.zeta(2 * p, 1.0 - y) + scipy.special.zeta(2 * p, 1.0 + y))
 
 
-def fres_3d(n, ng, p, interlace):
+def fres_3d(n, ng, p, interlace, shifts=None):
     """F_res(n) = sum_{m != 0} theta_m prod_i (x_i / (x_i - m_i))^{2p}, x = n / N_G (eq:res with
     |w_m(k)|^2 = |W(k - m k_s)|^2 / |W(k)|^2 and |W| = sinc^p).
 
@@ -71,19 +86,25 @@ def fres_3d(n, ng, p, interlace):
     the alternating f'(x) = sum_{m != 0} (-1)^m (x/(x-m))^{2p} = 2 F_int(x) - f(x) (F_int of eq:res1Di
     keeps the even images), theta_m = 1 gives prod(1 + f_i) - 1 and theta_m = [1 + (-1)^{sum m}]/2
     gives [prod(1 + f_i) + prod(1 + f'_i)]/2 - 1. The products are expanded so that no 1 is
-    subtracted from a sum close to 1 (F_res is tiny at small k)."""
+    subtracted from a sum close to 1 (F_res is tiny at small k).
+
+    With ``shifts`` (multi-grid interlacing, grid units) theta_m = (1/J) sum_j (-1)^{m.(2 d_j)} and
+    F_res = (1/J) sum_j [prod_i (1 + g_ji) - 1], g_ji = f'(x_i) where d_ji is an odd number of half
+    cells, else f(x_i)."""
     n = np.asarray(n, dtype=np.float64)
     x = n / ng
     f = [fres_1d_hurwitz(x[..., a].ravel(), p, False).reshape(x.shape[:-1]) for a in range(3)]
+    fi = [fres_1d_hurwitz(x[..., a].ravel(), p, True).reshape(x.shape[:-1]) for a in range(3)]
+    fa = [2.0 * fi[a] - f[a] for a in range(3)]
 
     def excess(g):  # prod(1 + g_i) - 1
         return g[0] + g[1] + g[2] + g[0] * g[1] + g[0] * g[2] + g[1] * g[2] + g[0] * g[1] * g[2]
 
-    if not interlace:
-        return excess(f)
-    fi = [fres_1d_hurwitz(x[..., a].ravel(), p, True).reshape(x.shape[:-1]) for a in range(3)]
-    fa = [2.0 * fi[a] - f[a] for a in range(3)]
-    return 0.5 * (excess(f) + excess(fa))
+    par = _parities(interlace, shifts)
+    total = np.zeros(x.shape[:-1])
+    for odd in par:
+        total += excess([fa[a] if odd[a] else f[a] for a in range(3)])
+    return total / len(par)
 
 
 def fres_binned(ng, p, interlace, edges=None):

@@ -28,15 +28,19 @@ def assign_units(u, ng, p, weights=None, shift=False, chunk=1 << 16):
 
     Every node j whose distance to the particle lies inside the kernel support (|s| < p/2) is
     visited: the candidates on one axis are j = ceil(u - p/2) + a, a = 0..p, and the distance
-    s = j - u is the minimum-image separation. shift=True adds 1/2 to u (grid 2 of Sec. 3.1).
+    s = j - u is the minimum-image separation. shift=True adds 1/2 to u (grid 2 of Sec. 3.1); a
+    3-vector adds that shift (grid units) per axis, for the grids of multi-grid interlacing.
     """
     u = np.asarray(u, dtype=np.float64)
+    if isinstance(shift, (bool, np.bool_)):
+        shift = 0.5 if shift else 0.0
+    shift = np.broadcast_to(np.asarray(shift, dtype=np.float64), (3,))
     n = u.shape[0]
     w_all = np.ones(n) if weights is None else np.asarray(weights, dtype=np.float64)
     rho = np.zeros(ng * ng * ng)
     offs = np.arange(p + 1)
     for lo in range(0, n, chunk):
-        uu = u[lo:lo + chunk] + (0.5 if shift else 0.0)
+        uu = u[lo:lo + chunk] + shift[None, :]
         ww = w_all[lo:lo + chunk]
         j = np.ceil(uu - 0.5 * p).astype(np.int64)[:, :, None] + offs[None, None, :]  # (m,3,p+1)
         wt = weight(p, j - uu[:, :, None])                                              # (m,3,p+1)

@@ -67,3 +67,32 @@ def density_modes(rho1, p, rho2=None):
         d2 = fourier_coefficients(overdensity(rho2))
         dt = 0.5 * (d1 + interlace_phase(ng) * d2)
     return dt / window_3d(p, ng)
+
+
+def density_modes_multi(rhos, shifts, p):
+    """Window-corrected density from J grids, grid j holding the particles shifted by d_j (grid
+    units): delta^G = (1/J) sum_j e^{+2 pi i n.d_j/N_G} delta~_j^G / W, the phase that undoes each
+    shift (Sec. 3.1 for J = 2, d = {0, (1,1,1)/2}). Image m of grid j then carries e^{+2 pi i m.d_j},
+    so the average keeps images with weight (1/J) sum_j e^{2 pi i m.d_j}."""
+    ng = rhos[0].shape[0]
+    n = signed_index(ng)
+    acc = np.zeros((ng, ng, ng), dtype=np.complex128)
+    for rho, d in zip(rhos, shifts):
+        d = np.asarray(d, dtype=np.float64)
+        ph = np.exp(2j * np.pi * (n[:, None, None] * d[0] + n[None, :, None] * d[1] + n[None, None, :] * d[2]) / ng)
+        acc += ph * fourier_coefficients(overdensity(rho))
+    return acc / len(rhos) / window_3d(p, ng)
+
+
+def multigrid_shifts(ngrids):
+    """Shift sets of multi-grid interlacing (grid units): 1 grid {0}; 2 grids {0, (1,1,1)/2} (Sec. 3.1);
+    4 grids {0, (1,1,0)/2, (1,0,1)/2, (0,1,1)/2}; 8 grids {0, 1/2}^3."""
+    if ngrids == 1:
+        return [(0.0, 0.0, 0.0)]
+    if ngrids == 2:
+        return [(0.0, 0.0, 0.0), (0.5, 0.5, 0.5)]
+    if ngrids == 4:
+        return [(0.0, 0.0, 0.0), (0.5, 0.5, 0.0), (0.5, 0.0, 0.5), (0.0, 0.5, 0.5)]
+    if ngrids == 8:
+        return [(a, b, c) for a in (0.0, 0.5) for b in (0.0, 0.5) for c in (0.0, 0.5)]
+    raise ValueError("ngrids must be 1, 2, 4 or 8")

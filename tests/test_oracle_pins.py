@@ -216,6 +216,64 @@ def test_poisson_power_matches_alias_expectation(p, interlace):
     assert np.max(np.abs(z)) < 4.5, z
 
 
+@pytest.mark.parametrize("ngrids", [4, 8])
+def test_multigrid_poisson_power_matches_alias_expectation(ngrids):
+    # Multi-grid interlacing (the extension of Sec. 3.1): each grid's shift phase must cancel exactly
+    # the images whose weight (1/J) sum_j e^{2 pi i m.d_j} vanishes; the realised power of uniform random
+    # catalogues averages to the aliasing sum with those weights. A wrong phase sign or shift direction
+    # on any grid leaves odd images in and fails by many sigma near the Nyquist frequency.
+    p, ng, box, npart, nseeds = 2, 8, 100.0, 400, 150
+    shifts = fourier.multigrid_shifts(ngrids)
+    shot = box ** 3 / npart
+    edges = power.default_edges(ng)
+    b = power.bin_index(ng, edges)
+    half = ng // 2
+    sn = fourier.signed_index(ng)
+    nvec = np.stack(np.meshgrid(sn, sn, sn, indexing="ij"), axis=-1)
+    sel = b >= 0
+    e_mode = aliasing.shot_noise_expectation(nvec[sel], ng, p, False, shot, mmax=3000, shifts=shifts)
+    cnt = np.bincount(b[sel], minlength=half)
+    expect = np.bincount(b[sel], weights=e_mode, minlength=half) / cnt
+    var_mode = np.bincount(b[sel], weights=e_mode ** 2, minlength=half) / cnt
+    acc = np.zeros(half)
+    for s in range(nseeds):
+        pos = catalogs.poisson(npart, box, seed=3000 + s)
+        u = assign.grid_units(pos, box, ng)
+        rhos = [assign.assign_units(u, ng, p, shift=d) for d in shifts]
+        pk, _, _ = power.power_spectrum(fourier.density_modes_multi(rhos, shifts, p), box, edges)
+        acc += pk
+    mean = acc / nseeds
+    sigma = np.sqrt(var_mode / (cnt / 2.0) / nseeds)
+    z = (mean - expect) / sigma
+    assert np.max(np.abs(z)) < 4.5, z
+    # more grids leave less aliasing: the expectation approaches 1/nbar bin by bin near Nyquist
+    e2 = aliasing.shot_noise_expectation(nvec[sel], ng, p, True, shot, mmax=3000)
+    exp2 = np.bincount(b[sel], weights=e2, minlength=half) / cnt
+    assert abs(expect[-1] / shot - 1.0) < abs(exp2[-1] / shot - 1.0)
+
+
+@pytest.mark.parametrize("ngrids", [1, 2, 4, 8])
+def test_multigrid_fres_is_the_shot_noise_excess(ngrids):
+    # the Hurwitz-zeta F_res with the multi-grid weights against the sinc^{2p} image sums
+    shifts = fourier.multigrid_shifts(ngrids)
+    rng = np.random.default_rng(62)
+    n = rng.integers(-16, 16, (50, 3))
+    n = n[np.abs(n).max(axis=1) >= 6]
+    for p in (2, 4):
+        e = aliasing.shot_noise_expectation(n, 32, p, False, 1.0, mmax=4000, shifts=shifts)
+        f = aliasing.fres_3d(n, 32, p, False, shifts=shifts)
+        assert np.max(np.abs(e - 1.0 - f) / (1.0 + f)) < 2e-10
+
+
+def test_two_grid_combine_is_the_interlaced_estimate():
+    pos = catalogs.zeldovich(8, 50.0, rms=2.0, seed=63)
+    u = assign.grid_units(pos, 50.0, 12)
+    r1, r2 = assign.assign_units(u, 12, 3), assign.assign_units(u, 12, 3, shift=True)
+    a = fourier.density_modes(r1, 3, r2)
+    b = fourier.density_modes_multi([r1, r2], fourier.multigrid_shifts(2), 3)
+    assert np.max(np.abs(a - b)) < 1e-14
+
+
 def test_interlacing_removes_odd_images_in_expectation():
     # With interlacing the expected PCS shot noise is much closer to 1/nbar near Nyquist.
     shot = 1.0
