@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--box", type=float, default=2000.0)
     ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
-    ap.add_argument("--only-row", choices=["adjoint", "batch", "direct"], default=None,
+    ap.add_argument("--only-row", choices=["adjoint", "batch", "direct", "multigrid"], default=None,
                     help="time one secondary row on its own workload and print it (no P(k) step)")
     ap.add_argument("--ds-nside", type=int, default=128, help="--only-row direct: particles per side")
     ap.add_argument("--ds-ng", type=int, default=128, help="--only-row direct: grid size")
@@ -345,10 +345,42 @@ def row_direct(dev, alu_peak_tflops, nside=128, ng=128):
     return rows["direct"]
 
 
+def row_multigrid(dev):
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs
+
+    # multi-grid interlacing: P(k) of 256^3 ZA particles (L = 500, N_G = 256, PCS, FP32) from J = 2, 4, 8
+    # shifted grids; accuracy against the direct sum on 64^3 particles / N_G = 64 (L = 50, Sec. 3.2 style,
+    # shot noise subtracted from both), in FP64 so that the aliasing left, not FP32 rounding, is measured
+    out = {"workload": "P(k) from J half-cell-shifted grids, 256^3 ZA particles, L=500, N_G=256, PCS, FP32; accuracy "
+                       "(FP64) vs direct summation on 64^3 ZA particles, L=50, N_G=64", "ms_per_call": {},
+           "max_rel_vs_ds": {}, "rel_vs_ds_at_kN": {}}
+    cfg = api.Config(ng=256, box=500.0, order=4, prec="fp32")
+    pos = catalogs.zeldovich_torch(256, 500.0, 4.0, seed=8, device=dev)
+    for J in (2, 4, 8):
+        out["ms_per_call"][str(J)] = _time_cuda(lambda: api.power_multigrid(pos, cfg, J), 3)
+    del pos
+    torch.cuda.empty_cache()
+    small = api.Config(ng=64, box=50.0, order=4, prec="fp64")
+    pos = catalogs.zeldovich_torch(64, 50.0, 1.0, seed=7, device=dev)
+    ds = api.direct_modes(pos, small)
+    p_ds, _, _ = api.cross_power(ds, ds, small)
+    shot = 50.0 ** 3 / pos.shape[0]
+    for J in (1, 2, 4, 8):
+        pk, _, _ = api.power_multigrid(pos, small, J)
+        rel = torch.abs((pk - shot) / (p_ds - shot) - 1.0)
+        out["max_rel_vs_ds"][str(J)] = rel.max().item()
+        out["rel_vs_ds_at_kN"][str(J)] = rel[-1].item()
+    del pos, ds
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_rows(dev, host64, big_box, alu_peak_tflops):
     """Times the other hot-path rows on their own workloads (one GB300)."""
     return {"bispectrum": row_bispectrum(dev, host64, big_box), "adjoint": row_adjoint(dev), "batch": row_batch(dev),
-            "direct": row_direct(dev, alu_peak_tflops)}
+            "direct": row_direct(dev, alu_peak_tflops), "multigrid": row_multigrid(dev)}
 
 
 def run_reference(a):
@@ -412,7 +444,8 @@ def main():
     lib = ffi.lib()
     if a.only_row:
         row = {"adjoint": lambda: row_adjoint(dev), "batch": lambda: row_batch(dev),
-               "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng)}[a.only_row]()
+               "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng),
+               "multigrid": lambda: row_multigrid(dev)}[a.only_row]()
         if rank == 0:
             print(json.dumps({"row": a.only_row, **row}), flush=True)
         return

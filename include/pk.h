@@ -262,6 +262,21 @@ pk_status pk_direct_modes(const pk_config* cfg, const void* pos_dev, int32_t pos
 pk_status pk_cross_power(const pk_config* cfg, const void* delta_a_dev, const void* delta_b_dev, double* pk_dev,
                          double* kmean_dev, int64_t* nmodes_dev, void* ws, size_t ws_bytes, void* stream);
 
+/* Multi-grid interlacing (the extension of Sec. 3.1 to more than two grids): P(k) from J = ngrids
+ * mass grids, grid j holding the particles shifted by d_j H, each transformed, multiplied by
+ * e^{+2 pi i n.d_j/N} and averaged, delta(n) = sum_j e^{+2 pi i n.d_j/N} G_j(n) / (J sum(w) W(n)).
+ * Shift sets: J = 1 {0}; J = 2 {0, (1,1,1)/2} (the pk_power interlacing); J = 4 {0, (1,1,0)/2,
+ * (1,0,1)/2, (0,1,1)/2}, which keeps only the alias images m whose components share one parity
+ * (first left: |m|^2 = 3, against 2 for J = 2); J = 8 {0, 1/2}^3, which keeps only images with every
+ * m_i even (first left: |m|^2 = 4). cfg->interlace is ignored; positions, weights, precision modes
+ * and outputs as pk_power (delta_k_dev optional, the half-complex layout). Cost: J assignments (J/2
+ * interlaced pairs for J = 2, 8) and one batched transform of J grids.
+ * Workspace: pk_multigrid_workspace_size(cfg, ngrids, n) bytes (0 for invalid arguments). */
+size_t pk_multigrid_workspace_size(const pk_config* cfg, int32_t ngrids, int64_t n);
+pk_status pk_power_multigrid(const pk_config* cfg, int32_t ngrids, const void* pos_dev, int32_t pos_format,
+                             const float* w_dev, int64_t n, double* pk_dev, double* kmean_dev, int64_t* nmodes_dev,
+                             void* delta_k_dev, void* ws, size_t ws_bytes, void* stream);
+
 /* Residual aliasing factor (eq:res, Sec. 3.2): for every mode n of the full N^3 grid,
  *   F_res(n) = sum_{m != 0} theta_m |W(k - m k_s)|^2 / |W(k)|^2,  |W| = sinc^p (p = cfg->order),
  * with theta_m = 1, or [1 + (-1)^{m_x+m_y+m_z}]/2 when cfg->interlace (the images the interlacing

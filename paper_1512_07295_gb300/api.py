@@ -225,6 +225,27 @@ def cross_power(delta_a, delta_b, cfg, ws=None):
     return pk, km, nm
 
 
+def power_multigrid(pos, cfg, ngrids, weights=None, return_delta=False, ws=None):
+    """P(k) with multi-grid interlacing over ngrids = 1, 2, 4 or 8 half-cell-shifted grids
+    (pk_power_multigrid): (pk, kmean, nmodes[, delta])."""
+    fmt = _pos_format(pos)
+    n = pos.shape[0]
+    w = _weights(weights, n, pos.device)
+    pk, km, nm = _outputs(cfg, pos.device)
+    delta = None
+    if return_delta:
+        ctype = torch.complex64 if cfg.prec == "fp32" else torch.complex128
+        delta = torch.empty(half_shape(cfg.ng), dtype=ctype, device=pos.device)
+    if ws is None:
+        size = ffi.lib().pk_multigrid_workspace_size(ctypes.byref(cfg.c()), int(ngrids), int(n))
+        if size == 0:
+            raise ffi.PkError(ffi.PK_EINVAL, ffi.last_error())
+        ws = torch.empty(size, dtype=torch.uint8, device=pos.device)
+    check(ffi.lib().pk_power_multigrid(ctypes.byref(cfg.c()), int(ngrids), _p(pos), fmt, _p(w), n, _p(pk), _p(km), _p(nm),
+                                       _p(delta), _p(ws), ws.numel(), _stream(pos.device)))
+    return (pk, km, nm, delta) if return_delta else (pk, km, nm)
+
+
 def aliasing_residual(cfg, device="cuda"):
     """Per-bin mean and maximum of the residual aliasing factor F_res (eq:res) for cfg's order and
     interlacing, with the mean |k| and mode counts (pk_aliasing_residual): (mean, max, kmean, nmodes)."""

@@ -112,5 +112,6 @@ pk_status backward_ws(const pk_config* c, int64_t n, size_t* out);
 pk_status batch_ws(const pk_config* c, int64_t nmax, size_t* out);
 pk_status direct_ws(const pk_config* c, int64_t n, bool cross, size_t* out);
 pk_status aliasing_ws(const pk_config* c, size_t* out);
+pk_status multigrid_ws(const pk_config* c, int ngrids, int64_t n, size_t* out);
 
 }  // namespace pk

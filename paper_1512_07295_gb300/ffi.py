@@ -61,6 +61,9 @@ SIGNATURES = {
                                  c_void_p]),
     "pk_direct_modes": (c_int32, [_CFG, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pk_cross_power": (c_int32, [_CFG, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pk_multigrid_workspace_size": (c_size_t, [_CFG, c_int32, c_int64]),
+    "pk_power_multigrid": (c_int32, [_CFG, c_int32, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_size_t, c_void_p]),
     "pk_aliasing_residual": (c_int32, [_CFG, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pk_estimate_noalloc": (c_int32, [_CFG, c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pk_profile_enable": (c_int32, [c_int32]),
