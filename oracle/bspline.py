@@ -11,7 +11,13 @@ between two nodes still gives its whole mass to one of them (the paper's |s| < 1
 
 Reading taken for CIC: the paper prints the support of 1-|s| as |s| < 1/2, which contradicts the
 two grid points per axis of a p = 2 scheme and the sinc^2 window; the support used is |s| < 1.
+
+Orders p = 5, 6 (beyond the paper's PCS; Sec. 2.3 defines W^(p) as the top hat convolved with itself
+p - 1 times): the centred B-spline in its truncated-power form,
+W^(p)(s) = (1/(p-1)!) sum_{k=0}^{p} (-1)^k C(p, k) (s + p/2 - k)_+^{p-1}.
 """
+
+from math import comb, factorial
 
 import numpy as np
 
@@ -36,8 +42,14 @@ def weight(p, s):
         m1 = (a >= 1.0) & (a < 2.0)
         w[m0] = (4.0 - 6.0 * a[m0] ** 2 + 3.0 * a[m0] ** 3) / 6.0
         w[m1] = (2.0 - a[m1]) ** 3 / 6.0
+    elif p in (5, 6):
+        for k in range(p + 1):
+            t = s + 0.5 * p - k
+            w += (-1) ** k * comb(p, k) * np.where(t > 0.0, t, 0.0) ** (p - 1)
+        w /= factorial(p - 1)
+        w[a >= 0.5 * p] = 0.0
     else:
-        raise ValueError("order p must be 1..4")
+        raise ValueError("order p must be 1..6")
     return w
 
 
@@ -62,8 +74,14 @@ def dweight(p, s):
         m1 = (a >= 1.0) & (a < 2.0)
         d[m0] = (-12.0 * a[m0] + 9.0 * a[m0] ** 2) / 6.0 * sg[m0]
         d[m1] = -0.5 * (2.0 - a[m1]) ** 2 * sg[m1]
+    elif p in (5, 6):
+        for k in range(p + 1):
+            t = s + 0.5 * p - k
+            d += (-1) ** k * comb(p, k) * np.where(t > 0.0, t, 0.0) ** (p - 2)
+        d /= factorial(p - 2)
+        d[a >= 0.5 * p] = 0.0
     else:
-        raise ValueError("order p must be 1..4")
+        raise ValueError("order p must be 1..6")
     return d
 
 

@@ -27,7 +27,7 @@ def _ft_numeric(p, nu):
     return total
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 def test_kernel_fourier_transform_is_sinc_power(p):
     # eq:intkerFT: the FT of the order-p B-spline of unit spacing is sinc^p(pi nu); this pins the
     # piece-wise coefficients of Sec. 2.3 (and the CIC support reading |s| < 1).
@@ -36,9 +36,9 @@ def test_kernel_fourier_transform_is_sinc_power(p):
         assert abs(_ft_numeric(p, nu) - expect) < 1e-12
 
 
-@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6])
 def test_kernel_derivative_matches_finite_difference(p):
-    s = np.linspace(-2.3, 2.3, 461) + 1e-3
+    s = np.linspace(-3.3, 3.3, 661) + 1e-3
     h = 1e-6
     fd = (bspline.weight(p, s + h) - bspline.weight(p, s - h)) / (2 * h)
     assert np.max(np.abs(fd - bspline.dweight(p, s))) < 1e-6
@@ -46,7 +46,7 @@ def test_kernel_derivative_matches_finite_difference(p):
 
 # --- eq:delgrid: partition of unity, single particle, lattices -------------------------------------
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("shift", [False, True])
 def test_mass_conservation(p, shift):
     pos = catalogs.poisson(500, 100.0, seed=11)
@@ -65,7 +65,7 @@ def _poisson_sum_1d(u, ng, p, mmax):
     return np.sum(np.exp(-2j * np.pi * f * u) * bspline.sinc(np.pi * f) ** p, axis=1)
 
 
-@pytest.mark.parametrize("p,tol", [(2, 2e-6), (3, 1e-9), (4, 1e-11)])
+@pytest.mark.parametrize("p,tol", [(2, 2e-6), (3, 1e-9), (4, 1e-11), (5, 1e-11), (6, 1e-11)])
 @pytest.mark.parametrize("shift", [False, True])
 def test_single_particle_grid_transform(p, tol, shift):
     # One particle: the DFT of its mass grid is the product over axes of the aliased window sums.
@@ -79,7 +79,7 @@ def test_single_particle_grid_transform(p, tol, shift):
     assert np.max(np.abs(g - expect)) < tol
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 def test_full_lattice_has_no_power(p):
     # Particles on every node: the partition of unity makes the grid uniform, so delta = 0 (both
     # the plain and the shifted grid), and P vanishes in every bin.
