@@ -82,7 +82,8 @@ typedef struct {
 
 typedef struct {
   int32_t ng;            /* N: even, 8 <= N <= 1024 */
-  int32_t order;         /* p: 1 NGP, 2 CIC, 3 TSC, 4 PCS (Sec. 2.3) */
+  int32_t order;         /* p: 1 NGP, 2 CIC, 3 TSC, 4 PCS (Sec. 2.3); 5, 6 the next B-splines
+                            (PK_FP64 and PK_FP32; not pk_batch_power) */
   int32_t interlace;     /* 1: add the H/2-shifted grid (Sec. 3.1); 0: single grid */
   int32_t prec;          /* pk_precision */
   double box;            /* L > 0 */

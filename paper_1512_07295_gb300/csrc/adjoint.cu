@@ -166,7 +166,9 @@ static cudaError_t launch_gather(int order, const void* pos, int fmt, const floa
   switch (order) {
     case 2: k_gather<2, R><<<blocks, 256, 0, s>>>(pos, fmt, w, n, ng, box, interlace, f32pos, g1, g2, out); count_launch(); break;
     case 3: k_gather<3, R><<<blocks, 256, 0, s>>>(pos, fmt, w, n, ng, box, interlace, f32pos, g1, g2, out); count_launch(); break;
-    default: k_gather<4, R><<<blocks, 256, 0, s>>>(pos, fmt, w, n, ng, box, interlace, f32pos, g1, g2, out); count_launch(); break;
+    case 4: k_gather<4, R><<<blocks, 256, 0, s>>>(pos, fmt, w, n, ng, box, interlace, f32pos, g1, g2, out); count_launch(); break;
+    case 5: k_gather<5, R><<<blocks, 256, 0, s>>>(pos, fmt, w, n, ng, box, interlace, f32pos, g1, g2, out); count_launch(); break;
+    default: k_gather<6, R><<<blocks, 256, 0, s>>>(pos, fmt, w, n, ng, box, interlace, f32pos, g1, g2, out); count_launch(); break;
   }
   return cudaGetLastError();
 }
@@ -205,7 +207,7 @@ extern "C" pk_status pk_power_backward(const pk_config* cfg, const void* pos_dev
   clear_err();
   pk_status st = validate(cfg);
   if (st != PK_OK) return st;
-  if (cfg->order < 2) return fail(PK_EINVAL, "the adjoint needs order 2..4 (NGP has no derivative)");
+  if (cfg->order < 2) return fail(PK_EINVAL, "the adjoint needs order 2..6 (NGP has no derivative)");
   if (pos_format != PK_POS_F64_XYZ && pos_format != PK_POS_CELL_F32OFF) return fail(PK_EINVAL, "bad pos_format");
   if (n < 1 || !pos_dev || !dl_dpk_dev || !dl_dx_dev) return fail(PK_EINVAL, "bad pointers");
   size_t need = 0;

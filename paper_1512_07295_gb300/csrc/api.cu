@@ -87,7 +87,8 @@ int num_sms() {
 pk_status validate(const pk_config* c) {
   if (!c) return fail(PK_EINVAL, "cfg is NULL");
   if (c->ng < 8 || c->ng > 1024 || (c->ng & 1)) return fail(PK_EINVAL, "ng must be even and in [8, 1024] (got %d)", c->ng);
-  if (c->order < 1 || c->order > 4) return fail(PK_EINVAL, "order must be 1..4 (got %d)", c->order);
+  if (c->order < 1 || c->order > 6) return fail(PK_EINVAL, "order must be 1..6 (got %d)", c->order);
+  if (c->order > 4 && c->prec == PK_FIXED64) return fail(PK_EINVAL, "orders 5 and 6 need PK_FP64 or PK_FP32");
   if (c->interlace != 0 && c->interlace != 1) return fail(PK_EINVAL, "interlace must be 0 or 1");
   if (c->prec < PK_FP64 || c->prec > PK_FIXED64) return fail(PK_EINVAL, "prec must be PK_FP64, PK_FP32 or PK_FIXED64");
   if (!(c->box > 0.0) || !std::isfinite(c->box)) return fail(PK_EINVAL, "box must be finite and > 0");

@@ -16,8 +16,8 @@ PK_ERR_ACCESSOR(take_err_assign)
 
 // ---- plain FP64 path ------------------------------------------------------------------------------
 
-template <int P>
-__device__ __forceinline__ void scatter_direct(double* __restrict__ g, const int* c, const double* f, double wgt, int ng,
+template <int P, typename G>
+__device__ __forceinline__ void scatter_direct(G* __restrict__ g, const int* c, const double* f, double wgt, int ng,
                                                int ldz) {
   double wx[P], wy[P], wz[P];
   const int sx = bspline<P>(f[0], wx), sy = bspline<P>(f[1], wy), sz = bspline<P>(f[2], wz);
@@ -28,16 +28,16 @@ __device__ __forceinline__ void scatter_direct(double* __restrict__ g, const int
     for (int b = 0; b < P; ++b) {
       const int gy = wrap(c[1] + sy + b, ng);
       const double wxy = wgt * wx[a] * wy[b];
-      double* row = g + (int64_t(gx) * ng + gy) * ldz;
+      G* row = g + (int64_t(gx) * ng + gy) * ldz;
 #pragma unroll
-      for (int d = 0; d < P; ++d) atomicAdd(row + wrap(c[2] + sz + d, ng), wxy * wz[d]);
+      for (int d = 0; d < P; ++d) atomicAdd(row + wrap(c[2] + sz + d, ng), G(wxy * wz[d]));
     }
   }
 }
 
-template <int P>
+template <int P, typename G>
 __global__ void k_assign_direct(const void* __restrict__ pos, int fmt, const float* __restrict__ w, int64_t n, int ng,
-                                double box, int interlace, double* __restrict__ g1, double* __restrict__ g2, int ldz) {
+                                double box, int interlace, G* __restrict__ g1, G* __restrict__ g2, int ldz) {
   const double scale = double(ng) / box;
   for (int64_t i = gtid(); i < n; i += gstride()) {
     int c[3];
@@ -81,18 +81,35 @@ __global__ void k_assign_direct(const void* __restrict__ pos, int fmt, const flo
   }
 }
 
-cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
-                                     bool interlace, double* g1, double* g2, int ldz, cudaStream_t s) {
+template <typename G>
+static cudaError_t launch_direct(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
+                                 bool interlace, G* g1, G* g2, int ldz, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int threads = 256;
   const int blocks = int(std::min<int64_t>((n + threads - 1) / threads, int64_t(num_sms()) * 16));
   switch (order) {
-    case 1: k_assign_direct<1><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); count_launch(); break;
-    case 2: k_assign_direct<2><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); count_launch(); break;
-    case 3: k_assign_direct<3><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); count_launch(); break;
-    default: k_assign_direct<4><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); count_launch(); break;
+    case 1: k_assign_direct<1, G><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); break;
+    case 2: k_assign_direct<2, G><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); break;
+    case 3: k_assign_direct<3, G><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); break;
+    case 4: k_assign_direct<4, G><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); break;
+    case 5: k_assign_direct<5, G><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); break;
+    case 6: k_assign_direct<6, G><<<blocks, threads, 0, s>>>(pos, fmt, w, n, ng, box, interlace, g1, g2, ldz); break;
+    default: return cudaErrorInvalidValue;
   }
+  count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
+                                     bool interlace, double* g1, double* g2, int ldz, cudaStream_t s) {
+  return launch_direct<double>(order, pos, fmt, w, n, ng, box, interlace, g1, g2, ldz, s);
+}
+
+// FP32 grids by the direct scatter (global FP32 atomics): the FP32 path of orders 5 and 6, whose
+// stencils the tiled kernels' shared-memory regions do not hold.
+cudaError_t launch_assign_direct_f32(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
+                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s) {
+  return launch_direct<float>(order, pos, fmt, w, n, ng, box, interlace, g1, g2, ldz, s);
 }
 
 // ---- tiled shared-memory path ---------------------------------------------------------------------
@@ -202,7 +219,8 @@ static cudaError_t launch_tile(int order, const pk_cellpos* p, const float* w, c
     case 1: k_assign_tile<1, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
     case 2: k_assign_tile<2, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
     case 3: k_assign_tile<3, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
-    default: k_assign_tile<4, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
+    case 4: k_assign_tile<4, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
+    default: return cudaErrorInvalidValue;  // the tile region holds stencils up to PCS
   }
   return cudaGetLastError();
 }

@@ -920,7 +920,12 @@ cudaError_t launch_assign_walk_f32(int order, const pk_cellpos* p, const float* 
     case 1: return launch_walk_p<1>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
     case 2: return launch_walk_p<2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
     case 3: return launch_walk_p<3>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    default: return launch_walk_p<4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 4: return launch_walk_p<4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 5:
+    case 6:  // orders beyond PCS: the direct scatter of the records (box unused for packed records)
+      if (ncat != 1) return cudaErrorInvalidValue;
+      return launch_assign_direct_f32(order, p, PK_POS_CELL_F32OFF, w, n, ng, 1.0, interlace, g1, g2, ldz, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -9,7 +9,7 @@
 
 namespace pk {
 
-constexpr int kMaxOrder = 4;
+constexpr int kMaxOrder = 6;
 
 // Device error word (PK_DERR_* bits). Without relocatable device code a __device__ variable is local to
 // its translation unit, so each unit that raises errors has its own word and a host accessor defined
@@ -34,6 +34,44 @@ __host__ __device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
 __host__ __device__ __forceinline__ int cell_x(uint32_t c) { return int(c >> 20) & 1023; }
 __host__ __device__ __forceinline__ int cell_y(uint32_t c) { return int(c >> 10) & 1023; }
 __host__ __device__ __forceinline__ int cell_z(uint32_t c) { return int(c) & 1023; }
+
+// Values N_P(f + k), k = 0..P-1, of the cardinal B-spline of order P on integer knots (support [0, P])
+// at an offset f in [0, 1), by the recurrence N_q(x) = [x N_{q-1}(x) + (q - x) N_{q-1}(x - 1)] / (q - 1)
+// (every term non-negative, so no cancellation), updated in place from the top index down.
+template <int P, typename T>
+__device__ __forceinline__ void cardinal_bspline(T f, T* b) {
+  b[0] = T(1);
+#pragma unroll
+  for (int q = 2; q <= P; ++q) {
+    const T inv = T(1) / T(q - 1);
+    b[q - 1] = (T(1) - f) * b[q - 2] * inv;
+#pragma unroll
+    for (int k = q - 2; k >= 1; --k) b[k] = ((f + T(k)) * b[k] + (T(q) - f - T(k)) * b[k - 1]) * inv;
+    b[0] = f * b[0] * inv;
+  }
+}
+
+// The centred B-spline of order P >= 5 (beyond PCS): the weight of the k-th stencil node is
+// N_P(m - g) = N_P(g + P - m) with m = k + 1, i.e. b[P - 1 - k]; g is the offset from floor(u) (even P)
+// or floor(u + 1/2) (odd P). Returns the first node relative to c = floor(u).
+template <int P, typename T>
+__device__ __forceinline__ int bspline_high(T f, T* w, T* g_out) {
+  T g = f;
+  int start;
+  if constexpr (P % 2 == 0) {
+    start = 1 - P / 2;
+  } else {
+    const bool up = f >= T(0.5);
+    g = up ? f - T(0.5) : f + T(0.5);
+    start = (up ? 1 : 0) - (P - 1) / 2;
+  }
+  T b[P];
+  cardinal_bspline<P>(g, b);
+#pragma unroll
+  for (int k = 0; k < P; ++k) w[k] = b[P - 1 - k];
+  *g_out = g;
+  return start;
+}
 
 // Order-P B-spline weights of Sec. 2.3 for a particle at u = c + f (c integer, 0 <= f < 1) on one
 // axis. Returns the first node of the stencil relative to c and writes the P weights of nodes
@@ -60,7 +98,7 @@ __device__ __forceinline__ int bspline(T f, T* w) {
     w[1] = T(0.75) - t * t;
     w[2] = T(0.5) * b * b;
     return up ? 0 : -1;
-  } else {
+  } else if constexpr (P == 4) {
     const T g = T(1) - f;
     const T f2 = f * f, g2 = g * g;
     const T sixth = T(1) / T(6);
@@ -69,6 +107,9 @@ __device__ __forceinline__ int bspline(T f, T* w) {
     w[2] = (T(4) - T(6) * g2 + T(3) * g2 * g) * sixth;
     w[3] = f2 * f * sixth;
     return -1;
+  } else {
+    T g;
+    return bspline_high<P>(f, w, &g);
   }
 }
 
@@ -86,7 +127,7 @@ __device__ __forceinline__ int bspline_deriv(T f, T* w, T* dw) {
     w[0] = T(0.5) * a * a; w[1] = T(0.75) - t * t; w[2] = T(0.5) * b * b;
     dw[0] = -a; dw[1] = T(-2) * t; dw[2] = b;
     return up ? 0 : -1;
-  } else {
+  } else if constexpr (P == 4) {
     const T g = T(1) - f;
     const T f2 = f * f, g2 = g * g;
     const T sixth = T(1) / T(6);
@@ -99,6 +140,16 @@ __device__ __forceinline__ int bspline_deriv(T f, T* w, T* dw) {
     dw[2] = T(2) * g - T(1.5) * g2;
     dw[3] = T(0.5) * f2;
     return -1;
+  } else {
+    // d/du N_P(m - g) = N_{P-1}(m - 1 - g) - N_{P-1}(m - g), and N_{P-1}(m - g) = c[P - 1 - m] for
+    // 1 <= m <= P - 1 (zero outside), c the order P - 1 values at g
+    T g;
+    const int start = bspline_high<P>(f, w, &g);
+    T c[P - 1];
+    cardinal_bspline<P - 1>(g, c);
+#pragma unroll
+    for (int k = 0; k < P; ++k) dw[k] = (k >= 1 ? c[P - 1 - k] : T(0)) - (k <= P - 2 ? c[P - 2 - k] : T(0));
+    return start;
   }
 }
 
