@@ -242,10 +242,11 @@ pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* off
  * pk_cellpos of the grid cfg->ng), w_dev float[n] or NULL for unit weights; n >= 1.
  * Output delta_k_dev: complex float (PK_FP32) or complex double (PK_FP64, PK_FIXED64), overwritten.
  * Arithmetic: each phase is the exact integer product of n with a fixed-point fraction x/L mod 1
- * (32 bits in PK_FP32, 64 bits otherwise) before its sine and cosine are taken; PK_FP32 sums the
- * products in FP32 over chunks of 64 particles with compensated chunk totals (relative error of a
- * few 1e-7 of sum |w|), PK_FP64 / PK_FIXED64 compute in FP64. Partial sums of particle slices are
- * added in FP64 with atomics, so the last bits may differ between runs.
+ * (32 bits in PK_FP32, 64 bits otherwise) before its sine and cosine are taken. PK_FP32 runs the sum
+ * as a matrix product on the tensor cores (TF32 operands split in two, three products per term,
+ * hardware sine/cosine, FP32 sums over runs of 64 particles with compensated totals): error below
+ * about 6e-6 of sum |w| / sum w. PK_FP64 / PK_FIXED64 compute in FP64 on the CUDA cores. Partial sums
+ * of particle slices are added in FP64 with atomics, so the last bits may differ between runs.
  * Invalid positions set PK_DERR_NONFINITE / PK_DERR_CELLRANGE and count at x = 0 with their weight.
  * Workspace: pk_workspace_size(cfg, n, PK_WS_DIRECT). */
 pk_status pk_direct_modes(const pk_config* cfg, const void* pos_dev, int32_t pos_format, const float* w_dev,

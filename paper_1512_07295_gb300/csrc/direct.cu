@@ -406,6 +406,286 @@ __global__ void __launch_bounds__(256) k_cross_bins(const V* __restrict__ da, co
   }
 }
 
+// ---- FP32 on the tensor cores (tcgen05, kind::tf32) -----------------------------------------------------
+//
+// The same product as a real matrix product D = A B per block: M = 128 rows (i_x, i_z), N = 64 real
+// columns (the real parts of 32 complex columns i_y, then their imaginary parts), K = 2 per particle:
+//   A[r][2k] = Re a_k(r), A[r][2k+1] = Im a_k(r),
+//   B[c][2k] = Re b_k(c), B[c][2k+1] = -Im b_k(c)   (c < 32: real part of column c),
+//   B[32+c][2k] = Im b_k(c), B[32+c][2k+1] = Re b_k(c) (imaginary part).
+// TF32 keeps 10 mantissa bits, so each operand x is split into big = x rounded to TF32 and small =
+// x - big (exact in FP32), and D accumulates big.big + big.small + small.big (three MMAs per k-step):
+// each product then errs by about 2^-21 of its size.
+//
+// Pipeline, per chunk c of 32 particles: the operands go to stage c % 2 of shared memory and the
+// chunk's MMAs (one issuing thread) to accumulator (c / 2) % 2 in TMEM (128 lanes x 64 FP32 columns,
+// restarted every second chunk, so each total covers 64 particles), completion signalled on mbarrier
+// c % 2 by tcgen05.commit. While they run, the block (16 warps) reads the accumulator of the previous
+// pair (warp w: lanes 32 (w % 4).., columns 16 (w / 4)..) into TwoSum pairs in registers, then builds
+// the next chunk's operands. Operands are K-major without
+// swizzle: 8-row x 16-byte core matrices, K-adjacent cores 128 B apart (LBO), 8-row groups 2048 B
+// apart (SBO). Every mbarrier wait is bounded in time.
+constexpr int kTcRows = 128, kTcCols = 32, kTcK = 32, kTcThreads = 512;
+constexpr int kTcTx = 8, kTcTz = 16;  // main row tiles: 8 i_x x 16 i_z
+constexpr int kTcKr = 2 * kTcK;       // real K per chunk
+constexpr uint32_t kTcTmemCols = 128; // two accumulators of 64 columns
+constexpr uint64_t kTcWaitNs = 1000000000ull;  // bound of every mbarrier wait
+
+__host__ __device__ inline int tc_main_x_tiles(int ng) { return (ng + kTcTx - 1) / kTcTx; }
+__host__ __device__ inline int tc_main_z_tiles(int ng) { return (ng / 2 + kTcTz - 1) / kTcTz; }
+__host__ __device__ inline int tc_row_tiles(int ng) { return tc_main_x_tiles(ng) * tc_main_z_tiles(ng) + (ng + kTcRows - 1) / kTcRows; }
+
+struct TcSmem {  // byte offsets in the dynamic shared memory (base aligned to 128)
+  static constexpr uint32_t a_part = kTcRows * kTcKr * 4, b_part = 2 * kTcCols * kTcKr * 4;
+  static constexpr uint32_t stage = 2 * a_part + 2 * b_part;  // A big, A small, B big, B small
+  static constexpr uint32_t rec = 2 * stage, bar = rec + kTcK * 16, tmem = bar + 16, total = tmem + 16;
+};
+
+// Byte offset of element (row, k) of a K-major operand with kTcKr columns of K (core matrices of 8 rows
+// x 4 elements, K-adjacent cores 128 B apart, 8-row groups (kTcKr / 4) x 128 B apart).
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+  return uint32_t(((row >> 3) * (kTcKr / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ void tc_split(float x, float& big, float& small) {
+  big = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);  // nearest TF32 (ties away from 0)
+  small = x - big;
+}
+
+// w e^{-2 pi i T / 2^32}: the phase T (a fraction of a turn, exact in integers) becomes an angle in
+// [-pi, pi) and the hardware sine and cosine (__sincosf, absolute error about 2^-21.4 there) take it.
+__device__ __forceinline__ void tc_expi(uint32_t t, float w, float& re, float& im) {
+  float s, c;
+  __sincosf(float(int32_t(t)) * 1.46291807926715968e-9f, &s, &c);  // pi / 2^31
+  re = w * c;
+  im = -(w * s);
+}
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  constexpr uint64_t lbo = 128, sbo = (kTcKr / 4) * 128;
+  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) | (uint64_t((sbo >> 4) & 0x3FFF) << 32) |
+         (uint64_t(1) << 46);  // version 1 (sm_100 family); base offset 0; no swizzle
+}
+
+// kind::tf32, FP32 accumulator, A and B K-major, N = 64, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(64 >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+
+__device__ __forceinline__ uint64_t tc_now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the phase of the given parity, for at most about one second.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = tc_now_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (tc_now_ns() - t0 > kTcWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tc_read_acc(uint32_t taddr, float (&hi)[16], float (&lo)[16]) {
+  uint32_t v[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {  // TwoSum of the chunk total into (hi, lo)
+    const float x = __uint_as_float(v[j]);
+    const float sum = __fadd_rn(hi[j], x);
+    const float bb = __fsub_rn(sum, hi[j]);
+    lo[j] = __fadd_rn(lo[j], __fadd_rn(__fsub_rn(hi[j], __fsub_rn(sum, bb)), __fsub_rn(x, bb)));
+    hi[j] = sum;
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>::Rec* __restrict__ recs, int64_t n, int ng,
+                                                               int64_t slice_len, double2* __restrict__ acc_out) {
+  using Rec = DsT<float>::Rec;
+  extern __shared__ __align__(128) unsigned char smem_tc[];
+  unsigned char* sm = smem_tc;
+  const uint32_t sbase = uint32_t(__cvta_generic_to_shared(sm));
+  Rec* sRec = reinterpret_cast<Rec*>(sm + TcSmem::rec);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + TcSmem::tmem);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int H = ng / 2 + 1;
+  const int col0 = blockIdx.y * kTcCols;
+  const int64_t k_beg = int64_t(blockIdx.z) * slice_len;
+  const int64_t k_end = min(n, k_beg + slice_len);
+  const int nchunks = k_end > k_beg ? int((k_end - k_beg + kTcK - 1) / kTcK) : 0;
+  const int tmain = tc_main_x_tiles(ng) * tc_main_z_tiles(ng);
+  const bool nyq = int(blockIdx.x) >= tmain;
+  int ix0, iz0;
+  if (!nyq) {
+    ix0 = (int(blockIdx.x) / tc_main_z_tiles(ng)) * kTcTx;
+    iz0 = (int(blockIdx.x) % tc_main_z_tiles(ng)) * kTcTz;
+  } else {
+    ix0 = (int(blockIdx.x) - tmain) * kTcRows;
+    iz0 = ng / 2;
+  }
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + TcSmem::tmem),
+                 "r"(kTcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + TcSmem::bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + TcSmem::bar + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // operand roles, chosen so that a warp's 8-byte stores cover 8 rows x 4 consecutive particles (two
+  // core matrices, 256 contiguous bytes): A row 8 warp + lane % 8, particles lane / 8 + 4 j (j < 8);
+  // B row 8 (warp % 8) + lane % 8, particles lane / 8 + 4 j + 16 (warp / 8) (j < 4)
+  const int ar = 8 * warp + (lane & 7), ak0 = lane >> 3;
+  const int a_ix = nyq ? ix0 + ar : ix0 + (ar >> 4), a_iz = nyq ? iz0 : iz0 + (ar & 15);
+  const bool a_ok = a_ix < ng && (nyq || a_iz < ng / 2);
+  const uint32_t nx_row = uint32_t(int64_t(signed_mode(min(a_ix, ng - 1), ng)));
+  const uint32_t nz_row = uint32_t(int64_t(nyq ? -(ng / 2) : a_iz));
+  const int br = 8 * (warp & 7) + (lane & 7), bk0 = (lane >> 3) + 16 * (warp >> 3), bc = br & 31;
+  const bool b_ok = col0 + bc < ng;
+  const uint32_t ny = uint32_t(int64_t(signed_mode(min(col0 + bc, ng - 1), ng)));
+  // epilogue: TMEM lanes 32 (warp % 4) + lane, columns 16 (warp / 4) .. + 15 of the accumulator
+  const int er = 32 * (warp & 3) + lane, ecol = 16 * (warp >> 2);
+  const uint32_t tlane = uint32_t(32 * (warp & 3)) << 16;
+  float hi[16], lo[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0.0f;
+  bool timed_out = false;
+  uint32_t phase0 = 0u, phase1 = 0u;  // parity to wait for on mbarrier 0 / 1
+  Rec next_rec;  // threads < kTcK: the record of the next chunk (zero weight past the slice)
+  next_rec.px = next_rec.py = next_rec.pz = 0u;
+  next_rec.w = 0.0f;
+  if (tid < kTcK && k_beg + tid < k_end) next_rec = recs[k_beg + tid];
+  int outstanding = -1;  // chunk whose MMAs may still be in flight
+
+  for (int c = 0; c <= nchunks && !timed_out; ++c) {
+    if (c < nchunks) {
+      const int64_t k0 = k_beg + int64_t(c) * kTcK;
+      const int st = c & 1;
+      if (tid < kTcK) {  // this chunk's record (loaded one chunk ahead), then the next one's load
+        sRec[tid] = next_rec;
+        const int64_t kn = k0 + kTcK + tid;
+        if (kn < k_end) {
+          next_rec = recs[kn];
+        } else {
+          next_rec.px = next_rec.py = next_rec.pz = 0u;
+          next_rec.w = 0.0f;
+        }
+      }
+      __syncthreads();
+      unsigned char* stg = sm + st * TcSmem::stage;
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 4; ++kk) {  // A: row ar, particles ak0 + 4 kk: w e^{-2 pi i (n_x x + n_z z)/L}
+        const int k = ak0 + 4 * kk;
+        const Rec r = sRec[k];
+        float re = 0.0f, im = 0.0f;
+        if (a_ok) tc_expi(nx_row * r.px + nz_row * r.pz, r.w, re, im);
+        float2 big, small;
+        tc_split(re, big.x, small.x);
+        tc_split(im, big.y, small.y);
+        const uint32_t off = tc_off(ar, 2 * k);
+        *reinterpret_cast<float2*>(stg + off) = big;
+        *reinterpret_cast<float2*>(stg + TcSmem::a_part + off) = small;
+      }
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 8; ++kk) {  // B: row br, particles bk0 + 4 kk: e^{-2 pi i n_y y/L}
+        const int k = bk0 + 4 * kk;
+        float yr = 0.0f, yi = 0.0f;
+        if (b_ok) tc_expi(ny * sRec[k].py, 1.0f, yr, yi);
+        const float v0 = br < 32 ? yr : yi, v1 = br < 32 ? -yi : yr;
+        float2 big, small;
+        tc_split(v0, big.x, small.x);
+        tc_split(v1, big.y, small.y);
+        const uint32_t off = tc_off(br, 2 * k);
+        *reinterpret_cast<float2*>(stg + 2 * TcSmem::a_part + off) = big;
+        *reinterpret_cast<float2*>(stg + 2 * TcSmem::a_part + TcSmem::b_part + off) = small;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = sbase + st * TcSmem::stage, sb = sa + 2 * TcSmem::a_part;
+        const uint32_t d = tmem + uint32_t(64 * ((c >> 1) & 1));  // chunks 2p, 2p + 1 share accumulator p % 2
+        // a k-step advances each operand by two core matrices (256 B): 16 in the address field
+        const uint64_t ab0 = tc_desc(sa), as0 = tc_desc(sa + TcSmem::a_part);
+        const uint64_t bb0 = tc_desc(sb), bs0 = tc_desc(sb + TcSmem::b_part);
+#pragma unroll
+        for (int ks = 0; ks < kTcKr / 8; ++ks) {
+          const uint64_t ab = ab0 + 16u * ks, as = as0 + 16u * ks, bb = bb0 + 16u * ks, bs = bs0 + 16u * ks;
+          const uint32_t acc0 = (ks > 0 || (c & 1)) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+              "l"(ab), "l"(bb), "r"(kTcIdesc), "r"(acc0)
+              : "memory");
+          asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(ab), "l"(bs), "r"(kTcIdesc)
+                       : "memory");
+          asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(as), "l"(bb), "r"(kTcIdesc)
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         sbase + TcSmem::bar + 8 * st)
+                     : "memory");
+      }
+      outstanding = c;
+    }
+    if (c >= 1) {  // the previous chunk's MMAs; after the second chunk of a pair (or the last), its accumulator
+      const int pb = (c - 1) & 1;
+      const bool ok = tc_wait(sbase + TcSmem::bar + 8 * pb, pb ? phase1 : phase0);
+      timed_out = __syncthreads_or(!ok) != 0;  // one decision for the whole block
+      if (!timed_out) {
+        if (pb) phase1 ^= 1u; else phase0 ^= 1u;
+        if (outstanding == c - 1) outstanding = -1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (((c - 1) & 1) || c == nchunks) tc_read_acc(tmem + tlane + uint32_t(64 * (((c - 1) >> 1) & 1) + ecol), hi, lo);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      } else if (tid == 0) {
+        raise_err(PK_DERR_TIMEOUT);
+      }
+    }
+  }
+
+  if (!timed_out) {  // this thread's accumulator lane is row (i_x, i_z); its 16 columns are real or imaginary parts
+    const int ix = nyq ? ix0 + er : ix0 + (er >> 4), iz = nyq ? iz0 : iz0 + (er & 15);
+    if (ix < ng && (nyq || iz < ng / 2)) {
+#pragma unroll 4
+      for (int j = 0; j < 16; ++j) {
+        const int col = col0 + (ecol & 31) + j;
+        if (col >= ng) break;
+        double2* dst = acc_out + (int64_t(ix) * ng + col) * H + iz;
+        atomicAdd(ecol < 32 ? &dst->x : &dst->y, double(hi[j]) + double(lo[j]));
+      }
+    }
+  } else {  // give the MMAs still in flight a bounded wait before the TMEM is freed
+    if (outstanding >= 0) tc_wait(sbase + TcSmem::bar + 8 * (outstanding & 1), (outstanding & 1) ? phase1 : phase0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+  }
+}
+
 // ---- host side --------------------------------------------------------------------------------------------
 
 namespace {
@@ -475,6 +755,26 @@ pk_status run_direct(const pk_config* c, const void* pos, int fmt, const float* 
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "direct wsum");
   const int64_t hc = half_count(ng);
   if ((e = cudaMemsetAsync(L.sums, 0, sizeof(double2) * size_t(hc), s)) != cudaSuccess) return cuda_fail(e, "memset");
+  if constexpr (DsT<R>::kCompensated) {  // FP32: the tensor-core kernel
+    const int64_t row_tiles = tc_row_tiles(ng);
+    const int col_tiles = (ng + kTcCols - 1) / kTcCols;
+    const int slices = ds_slices(row_tiles * col_tiles, n, kTcK);
+    const int64_t chunks = (n + kTcK - 1) / kTcK;
+    const int64_t slice_len = ((chunks + slices - 1) / slices) * kTcK;
+    const size_t smem = TcSmem::total;
+    if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_ds_modes_tc), smem)) != cudaSuccess)
+      return cuda_fail(e, "direct smem");
+    if (row_tiles > 2147483647) return fail(PK_EINVAL, "too many rows");
+    k_ds_modes_tc<<<dim3(unsigned(row_tiles), col_tiles, slices), kTcThreads, smem, s>>>(
+        reinterpret_cast<const DsT<float>::Rec*>(L.recs), n, ng, slice_len, L.sums);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "direct modes");
+    const int fblocks = int(std::min<int64_t>(int64_t(num_sms()) * 8, (hc + 255) / 256));
+    k_ds_finish<float2><<<fblocks, 256, 0, s>>>(L.sums, L.wsum, hc, static_cast<float2*>(delta_out));
+    count_launch();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PK_OK : cuda_fail(e, "direct finish");
+  }
   const int64_t row_tiles = ds_row_tiles(ng);
   const int col_tiles = (ng + kDsCols - 1) / kDsCols;
   const int slices = ds_slices(row_tiles * col_tiles, n, K);

@@ -2,11 +2,12 @@
 power (pk_cross_power) against the FP64 oracle, through the C ABI.
 
 Tolerances. FP64 mode: 1e-12 absolute on delta (|delta| <= sum|w|/sum w = 1 for positive weights).
-FP32 mode: every product w e^{-i k.x} carries a few FP32 roundings (phase, sine/cosine, the weight
-and the complex product) and each chunk of 64 products is summed in FP32 before the compensated
-total, so the error is bounded by about 64 eps_32 sum|w| / sum w = 3.8e-6 (a sum of m terms in FP32
-errs by at most (m-1) eps of the sum of their magnitudes); the tests use 4e-6. Binned cross powers of
-given fields: 1e-12 relative per bin (FP64 sums), counts bit-exact."""
+FP32 mode (tensor cores, three TF32 products per term): each product w e^{-i k.x} = a b carries the
+hardware sine/cosine of its two factors (absolute error 2^-21.4 each), about 3 x 2^-21 from the TF32
+split and a few FP32 roundings, and each run of 64 products is summed in FP32 before the compensated
+total (at most 63 eps_32 of the sum of the magnitudes), so the error is bounded by about
+(2 x 2^-21.4 + 3 x 2^-21 + 4 eps_32 + 63 eps_32) sum|w| / sum w = 6.2e-6; the tests use 7e-6.
+Binned cross powers of given fields: 1e-12 relative per bin (FP64 sums), counts bit-exact."""
 
 import numpy as np
 import pytest
@@ -18,7 +19,7 @@ from paper_1512_07295_gb300 import api, catalogs, ffi
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-TOL32 = 4e-6
+TOL32 = 7e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
