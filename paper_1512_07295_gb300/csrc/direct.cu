@@ -6,13 +6,13 @@
 //   delta(n) = (1/sum w) sum_i w_i exp(-2 pi i n.x_i/L),   delta(0) = 0.
 // The sum is separable: with rows r = (i_x, i_z) and columns c = i_y,
 //   delta[r][c] = sum_i a_i(r) b_i(c),  a_i(r) = w_i e^{-2 pi i (n_x x + n_z z)/L},  b_i(c) = e^{-2 pi i n_y y/L},
-// a complex matrix product over the particles, computed on the FP32 (or FP64) pipes in 256 x 32 mode
-// tiles: each thread holds a 4 x 8 register tile, the operands of a chunk of particles are generated
-// in shared memory from per-particle, per-axis phase tables. Phases are exact integer products n * Phi of a fixed-point position fraction
-// Phi = x/L mod 1 (32 bits in FP32, 64 in FP64) before the sine and cosine are taken, so no large
-// argument is ever reduced in floating point. FP32 sums each chunk of 56 particles in registers and
-// adds the chunk sums to a compensated pair (hi, lo); the particle slices of different blocks meet in
-// FP64 sums.
+// a complex matrix product over the particles. Phases are exact integer products n * Phi of a
+// fixed-point position fraction Phi = x/L mod 1 (32 bits in FP32, 64 in FP64) before the sine and
+// cosine are taken, so no large argument is ever reduced in floating point.
+//   FP32: k_ds_modes_tc, the product on the tensor cores (tcgen05, TF32 operands split in two).
+//   FP64: k_ds_modes, FP64 FMAs on the CUDA cores in 256 x 32 mode tiles, each thread a 4 x 8
+//         register tile, operands built in shared memory from per-particle, per-axis phase tables.
+// Partial sums of particle slices meet in FP64 atomics.
 #include "host.cuh"
 
 namespace pk {
@@ -774,7 +774,7 @@ pk_status run_direct(const pk_config* c, const void* pos, int fmt, const float* 
     count_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? PK_OK : cuda_fail(e, "direct finish");
-  }
+  } else {  // FP64: the CUDA-core kernel
   const int64_t row_tiles = ds_row_tiles(ng);
   const int col_tiles = (ng + kDsCols - 1) / kDsCols;
   const int slices = ds_slices(row_tiles * col_tiles, n, K);
@@ -789,13 +789,11 @@ pk_status run_direct(const pk_config* c, const void* pos, int fmt, const float* 
                                                                                     slice_len, L.sums); count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "direct modes");
   const int fblocks = int(std::min<int64_t>(int64_t(num_sms()) * 8, (hc + 255) / 256));
-  if (c->prec == PK_FP32)
-    k_ds_finish<float2><<<fblocks, 256, 0, s>>>(L.sums, L.wsum, hc, static_cast<float2*>(delta_out));
-  else
-    k_ds_finish<double2><<<fblocks, 256, 0, s>>>(L.sums, L.wsum, hc, static_cast<double2*>(delta_out));
+  k_ds_finish<double2><<<fblocks, 256, 0, s>>>(L.sums, L.wsum, hc, static_cast<double2*>(delta_out));
   count_launch();
   e = cudaGetLastError();
   return e == cudaSuccess ? PK_OK : cuda_fail(e, "direct finish");
+  }
 }
 
 }  // namespace
