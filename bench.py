@@ -602,8 +602,9 @@ def main():
         ms_e2e = e0.elapsed_time(e1) / ke
         result["e2e"] = {"value": n / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": 24 * n,
                          "d2h_bytes_per_step": 24 * cfg.nb, "ms_per_step": ms_e2e,
-                         "path": "pk_power_host: pinned host FP64 xyz read over the CPU-GPU link by the prepare+count "
-                                 "kernel -> bin -> assign -> FFT -> estimate -> D2H of P(k), kmean, counts"}
+                         "path": "pk_power_host: pinned host FP64 xyz copied over the CPU-GPU link in 16 pieces by the "
+                                 "copy engine, each prepared, binned and assigned while the next is in flight -> FFT -> "
+                                 "estimate -> D2H of P(k), kmean, counts"}
         del wsp
         torch.cuda.empty_cache()
 

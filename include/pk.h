@@ -174,10 +174,12 @@ pk_status pk_power(const pk_config* cfg, const void* pos_dev, int32_t pos_format
 
 /* a1..a6 end to end from host memory: pk_power for positions pos_host (and optional weights w_host,
  * float[n]) in HOST memory, with P(k), kmean and the mode counts written to host memory (length
- * nbins each). Pinned positions (cudaHostAlloc, cudaHostRegister) are read by the GPU directly over
- * the CPU-GPU link while they are prepared and counted (the FP32 and FIXED64 modes); pageable ones
- * are copied through the workspace in pieces; weights, and positions in the FP64 mode or the packed
- * format, are copied to the workspace first. Asynchronous on `stream` like every call: the host
+ * nbins each). PK_FP32 with FP64 positions: the positions cross the CPU-GPU link in about sixteen
+ * pieces, copied by the copy engine on a stream the call creates (and releases) for itself, each
+ * piece prepared, binned and added to the grids while the next one is in flight. PK_FIXED64: pinned
+ * positions are read by the GPU directly while being prepared and counted, pageable ones copied
+ * through the workspace in pieces. Weights, and positions in the FP64 mode or the packed format, are
+ * copied to the workspace first. Asynchronous on `stream` like every call: the host
  * outputs are valid once the stream has synchronised. Device or managed pos_host: PK_EINVAL.
  * Workspace: pk_workspace_size(cfg, n, PK_WS_POWER_HOST). */
 pk_status pk_power_host(const pk_config* cfg, const void* pos_host, int32_t pos_format, const float* w_host,

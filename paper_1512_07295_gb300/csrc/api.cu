@@ -269,20 +269,21 @@ pk_status run_weight_sums(const float* w, int64_t n, double* sums, cudaStream_t 
 // PK_FP64 from positions in any order (direct FP64 atomics); PK_FP32 / PK_FIXED64 from the binned
 // layout (sorted, offsets). wsums (device) holds the weight sums (fixed-point scale).
 pk_status run_assign_into(const pk_config* c, const void* pos, int fmt, const pk_cellpos* sorted, const float* w,
-                          const int64_t* offsets, int64_t n, const double* wsums, void* grids, int ldz, cudaStream_t s) {
+                          const int64_t* offsets, int64_t n, const double* wsums, void* grids, int ldz, cudaStream_t s,
+                          bool clear) {
   const bool two = c->interlace != 0;
   const int64_t per = int64_t(c->ng) * c->ng * ldz;
   const size_t all = size_t(per) * (two ? 2 : 1);
   cudaError_t e;
   if (c->prec == PK_FP64) {
     double* g1 = static_cast<double*>(grids);
-    if ((e = cudaMemsetAsync(g1, 0, all * 8, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    if (clear && (e = cudaMemsetAsync(g1, 0, all * 8, s)) != cudaSuccess) return cuda_fail(e, "memset");
     prof_mark(2, s);
     e = launch_assign_direct_f64(c->order, pos, fmt, w, n, c->ng, c->box, two, g1, two ? g1 + per : nullptr, ldz, s);
     if (e != cudaSuccess) return cuda_fail(e, "assign (fp64)");
   } else if (c->prec == PK_FP32) {
     float* g1 = static_cast<float*>(grids);
-    if ((e = cudaMemsetAsync(g1, 0, all * 4, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    if (clear && (e = cudaMemsetAsync(g1, 0, all * 4, s)) != cudaSuccess) return cuda_fail(e, "memset");
     prof_mark(2, s);
     e = launch_assign_walk_f32(c->order, sorted, w, offsets, n, c->ng, two, g1, two ? g1 + per : nullptr, ldz, s);
     if (e != cudaSuccess) return cuda_fail(e, "assign (fp32)");
@@ -313,12 +314,22 @@ pk_status carve_forward(const pk_config* c, int64_t n, Carver& cv, ForwardStage*
 // Workspace of pk_power_host: the forward stage, device copies of the weights (and, in FP64 mode, of
 // the positions), the staging buffer for pageable positions and the device outputs.
 constexpr int64_t kHostStageParticles = int64_t(1) << 22;
+// FP32 from FP64 host positions: the catalogue crosses the CPU-GPU link in about sixteen pieces of
+// 2^20 .. 2^26 particles (up to 1.6 GB), each prepared, binned and assigned while the next one is
+// being copied; only the last piece's processing is not hidden behind the link.
+constexpr int64_t kHostPieceMin = int64_t(1) << 20, kHostPieceMax = int64_t(1) << 26;
 pk_status carve_host(const pk_config* c, int64_t n, Carver& cv, HostLayout* h) {
   pk_status st = carve_forward(c, n, cv, &h->f);
   if (st != PK_OK) return st;
   h->w = cv.take<float>(size_t(std::max<int64_t>(n, 1)));
   h->stage_cap = std::max<int64_t>(1, std::min<int64_t>(n, kHostStageParticles));
   h->stage = cv.take<double>(size_t(3 * h->stage_cap));
+  if (c->prec == PK_FP32) {
+    h->piece_cap = std::min<int64_t>(std::max<int64_t>(n, 1),
+                                     std::min(kHostPieceMax, std::max(kHostPieceMin, (n + 15) / 16)));
+    h->piece[0] = cv.take<double>(size_t(3 * h->piece_cap));
+    h->piece[1] = cv.take<double>(size_t(3 * h->piece_cap));
+  }
   h->pos = c->prec == PK_FP64 ? cv.take<double>(size_t(3 * std::max<int64_t>(n, 1))) : nullptr;
   h->pk = cv.take<double>(size_t(c->nbins));
   h->kmean = cv.take<double>(size_t(c->nbins));
@@ -600,6 +611,65 @@ pk_status pk_power(const pk_config* cfg, const void* pos_dev, int32_t pos_format
   return run_fft_estimate(cfg, f.g, delta_k_dev, pk_dev, kmean_dev, nmodes_dev, s);
 }
 
+// FP32 grids from FP64 host positions, piece by piece: on a copy stream of its own the copy engine
+// moves piece j into device buffer j % 2 (after the processing of piece j - 2 has read it); the caller's
+// stream prepares and counts it, bins it and adds its assignment to the grids, so the transfer of
+// piece j + 1 overlaps the processing of piece j. The grids are cleared once.
+static pk_status run_host_pieces(const pk_config* c, const double* pos_host, const float* w, int64_t n, HostLayout& h,
+                                 cudaStream_t s) {
+  cudaError_t e;
+  pk_status st = run_weight_sums(w, n, h.f.g.wsums, s);
+  if (st != PK_OK) return st;
+  const int nt = tiles_per_axis(c->ng);
+  const size_t nkeys = size_t(nt) * nt * nt * kSlabs;
+  const size_t gbytes = size_t(c->interlace ? 2 : 1) * size_t(padded_count(c->ng)) * sizeof(float);
+  if ((e = cudaMemsetAsync(h.f.g.grids, 0, gbytes, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[5] = {};  // start, ready[2], free[2]
+  auto release = [&]() {
+    for (cudaEvent_t& x : ev)
+      if (x) cudaEventDestroy(x);
+    if (cs) cudaStreamDestroy(cs);
+  };
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "copy stream");
+  for (cudaEvent_t& x : ev)
+    if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess) {
+      release();
+      return cuda_fail(e, "events");
+    }
+  cudaEvent_t ev_start = ev[0], *ev_ready = ev + 1, *ev_free = ev + 3;
+  st = PK_OK;
+  if ((e = cudaEventRecord(ev_start, s)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_start, 0)) != cudaSuccess)
+    st = cuda_fail(e, "order copy stream");
+  for (int64_t i0 = 0, j = 0; st == PK_OK && i0 < n; i0 += h.piece_cap, ++j) {
+    const int b = int(j & 1);
+    const int64_t cnt = std::min<int64_t>(h.piece_cap, n - i0);
+    if (j >= 2 && (e = cudaStreamWaitEvent(cs, ev_free[b], 0)) != cudaSuccess) { st = cuda_fail(e, "wait"); break; }
+    if ((e = cudaMemcpyAsync(h.piece[b], pos_host + 3 * i0, size_t(cnt) * 3 * sizeof(double), cudaMemcpyHostToDevice, cs)) !=
+            cudaSuccess ||
+        (e = cudaEventRecord(ev_ready[b], cs)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev_ready[b], 0)) != cudaSuccess) {
+      st = cuda_fail(e, "copy positions");
+      break;
+    }
+    if ((e = cudaMemsetAsync(h.f.b.counts, 0, nkeys * sizeof(unsigned long long), s)) != cudaSuccess ||
+        (e = launch_prepare_hist(h.piece[b], 0, cnt, c->ng, c->box, nt, h.f.b.cells, h.f.b.counts, s)) != cudaSuccess ||
+        (e = cudaEventRecord(ev_free[b], s)) != cudaSuccess) {
+      st = cuda_fail(e, "prepare");
+      break;
+    }
+    const float* wp = w ? w + i0 : nullptr;
+    if ((e = launch_bin_finish(h.f.b.cells, wp, cnt, c->ng, nt, h.f.sorted, w ? h.f.wsorted : nullptr, h.f.offsets,
+                               h.f.b.counts, h.f.b.sub, h.f.b.scan, s)) != cudaSuccess) {
+      st = cuda_fail(e, "bin");
+      break;
+    }
+    st = run_assign_into(c, nullptr, PK_POS_CELL_F32OFF, h.f.sorted, w ? h.f.wsorted : nullptr, h.f.offsets, cnt, h.f.g.wsums,
+                         h.f.g.grids, c->ng + 2, s, false);
+  }
+  release();  // destruction is deferred by the runtime until the queued work is done
+  return st;
+}
+
 pk_status pk_power_host(const pk_config* cfg, const void* pos_host, int32_t pos_format, const float* w_host, int64_t n,
                         double* pk_host, double* kmean_host, int64_t* nmodes_host, void* ws, size_t ws_bytes, void* stream) {
   clear_err();
@@ -638,6 +708,9 @@ pk_status pk_power_host(const pk_config* cfg, const void* pos_host, int32_t pos_
     if ((e = cudaMemcpyAsync(dst, pos_host, size_t(n) * rec, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "copy positions");
     st = run_forward_grids(cfg, dst, pos_format, w, n, h.f, s);
+  } else if (cfg->prec == PK_FP32) {  // pieces copied by the copy engine while the previous one is processed
+    (void)mapped;
+    st = run_host_pieces(cfg, static_cast<const double*>(pos_host), w, n, h, s);
   } else if (mapped) {  // read over the CPU-GPU link while being prepared and counted
     st = run_forward_grids(cfg, mapped, pos_format, w, n, h.f, s);
   } else {

@@ -73,8 +73,10 @@ struct HostStage {
 pk_status run_bin(const pk_config* c, const void* pos, int fmt, const float* w, int64_t n, BinStage& b, pk_cellpos* sorted,
                   float* wsorted, int64_t* offsets, cudaStream_t s, const HostStage* stage = nullptr);
 pk_status run_weight_sums(const float* w, int64_t n, double* sums, cudaStream_t s);
+// clear = false adds to the grids instead of overwriting them (FP64 and FP32; the pieces of a catalogue).
 pk_status run_assign_into(const pk_config* c, const void* pos, int fmt, const pk_cellpos* sorted, const float* w,
-                          const int64_t* offsets, int64_t n, const double* wsums, void* grids, int ldz, cudaStream_t s);
+                          const int64_t* offsets, int64_t n, const double* wsums, void* grids, int ldz, cudaStream_t s,
+                          bool clear = true);
 
 // Workspace of the forward "positions -> padded transformed grids" stage (used by pk_power and
 // recomputed by pk_power_backward).
@@ -94,6 +96,8 @@ struct HostLayout {
   float* w = nullptr;
   double* stage = nullptr;
   int64_t stage_cap = 0;
+  double* piece[2] = {nullptr, nullptr};  // FP32 from FP64 positions: device copies of two pieces
+  int64_t piece_cap = 0;
   double* pos = nullptr;
   double* pk = nullptr;
   double* kmean = nullptr;

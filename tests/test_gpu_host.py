@@ -64,7 +64,8 @@ def test_host_weights_and_packed_records(pinned):
 
 
 def test_pageable_positions_in_several_pieces():
-    # more particles than one staging piece (2^22) holds
+    # FP32 from FP64 positions crosses the link in pieces of at least 2^20 particles: five pieces here,
+    # each binned and added to the grids while the next one is copied
     box, ng, n = 1000.0, 64, 5_000_000
     pos = catalogs.poisson(n, box, seed=74)
     cfg = api.Config(ng=ng, box=box, prec="fp32")
@@ -75,6 +76,21 @@ def test_pageable_positions_in_several_pieces():
     # 19 particles per cell: the lowest bins' power is a small difference of large FP32 grid sums, so
     # two FP32 runs differ there by more than in the sparser cases above (summation order only)
     assert _ref.rel(pk_h.numpy(), pk_d.cpu().numpy()) <= 1e-5
+
+
+def test_pinned_weighted_positions_in_several_pieces():
+    # pinned positions and weights in four pieces (the last one short): the weights of each piece
+    # follow its positions
+    box, ng, n = 800.0, 48, 3_500_000
+    pos = catalogs.poisson(n, box, seed=76)
+    w = catalogs.random_weights(n, seed=77).astype(np.float32)
+    cfg = api.Config(ng=ng, box=box, prec="fp32")  # a Poisson catalogue: P is the shot noise, kept in
+    pk_h, km_h, cnt_h = api.power_host(_host(pos, True), cfg, weights=_host(w, True))
+    torch.cuda.synchronize()
+    pk_d, km_d, cnt_d = api.power(torch.from_numpy(pos).to(DEV), cfg, weights=torch.from_numpy(w).to(DEV))
+    assert torch.equal(cnt_h, cnt_d.cpu())
+    assert _ref.rel(pk_h.numpy(), pk_d.cpu().numpy()) <= 1e-5
+    assert _ref.rel(km_h.numpy(), km_d.cpu().numpy()) <= 1e-6
 
 
 def test_device_pointer_is_rejected():
