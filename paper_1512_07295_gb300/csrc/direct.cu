@@ -518,6 +518,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
   const uint32_t sbase = uint32_t(__cvta_generic_to_shared(sm));
   Rec* sRec = reinterpret_cast<Rec*>(sm + TcSmem::rec);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + TcSmem::tmem);
+  volatile int* s_bad = reinterpret_cast<volatile int*>(sm + TcSmem::tmem + 4);  // a wait ran out
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int H = ng / 2 + 1;
@@ -543,6 +544,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
+    *s_bad = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + TcSmem::bar) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + TcSmem::bar + 8) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
   if (tid < kTcK && k_beg + tid < k_end) next_rec = recs[k_beg + tid];
   int outstanding = -1;  // chunk whose MMAs may still be in flight
 
-  for (int c = 0; c <= nchunks && !timed_out; ++c) {
+  for (int c = 0; c <= nchunks; ++c) {
     if (c < nchunks) {
       const int64_t k0 = k_beg + int64_t(c) * kTcK;
       const int st = c & 1;
@@ -592,6 +594,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
         }
       }
       __syncthreads();
+      if (*s_bad) break;  // a wait of the previous chunk ran out (one value for the whole block here)
       unsigned char* stg = sm + st * TcSmem::stage;
 #pragma unroll
       for (int kk = 0; kk < kTcK / 4; ++kk) {  // A: row ar, particles ak0 + 4 kk: w e^{-2 pi i (n_x x + n_z z)/L}
@@ -650,19 +653,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
     }
     if (c >= 1) {  // the previous chunk's MMAs; after the second chunk of a pair (or the last), its accumulator
       const int pb = (c - 1) & 1;
-      const bool ok = tc_wait(sbase + TcSmem::bar + 8 * pb, pb ? phase1 : phase0);
-      timed_out = __syncthreads_or(!ok) != 0;  // one decision for the whole block
-      if (!timed_out) {
+      // no block barrier here (the MMA-issuing thread would hold every warp): each warp decides alone,
+      // and a timeout reaches the whole block through s_bad at the next chunk's first barrier
+      const bool ok = __all_sync(0xffffffffu, tc_wait(sbase + TcSmem::bar + 8 * pb, pb ? phase1 : phase0));
+      if (ok) {
         if (pb) phase1 ^= 1u; else phase0 ^= 1u;
         if (outstanding == c - 1) outstanding = -1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (((c - 1) & 1) || c == nchunks) tc_read_acc(tmem + tlane + uint32_t(64 * (((c - 1) >> 1) & 1) + ecol), hi, lo);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      } else if (tid == 0) {
-        raise_err(PK_DERR_TIMEOUT);
+      } else if (lane == 0) {
+        *s_bad = 1;
       }
     }
   }
+  __syncthreads();
+  timed_out = *s_bad != 0;
+  if (timed_out && tid == 0) raise_err(PK_DERR_TIMEOUT);
 
   if (!timed_out) {  // this thread's accumulator lane is row (i_x, i_z); its 16 columns are real or imaginary parts
     const int ix = nyq ? ix0 + er : ix0 + (er >> 4), iz = nyq ? iz0 : iz0 + (er & 15);
