@@ -13,7 +13,7 @@ region); ``roofline`` for the assignment kernel;
 ``cpu_baseline`` = the FP64 CPU oracle on a bounded sample; ``fp64_plain`` = the plain FP64 GPU path
 (global FP64 atomics, FP64 FFT) on the same catalogue.
 
-``--impl reference`` times the FP64 CPU oracle (the reference arm of this build) on a bounded
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on a bounded
 sample of the same workload and prints the same metric.
 """
 

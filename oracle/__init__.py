@@ -22,7 +22,7 @@ Modules (each function cites the section / equation of the paper it follows):
 - ``aliasing``  : aliasing sums of the Poisson shot noise (eq:Pknoint and its interlaced form) and
                   the residual factor F_res (eq:Fres, eq:res1Di, eq:res1Dnoi).
 
-Conventions (the readings taken where the paper is silent or inconsistent are listed in the design doc):
+Conventions (where the paper is silent or inconsistent, each module states the reading it takes):
 delta_n = (1/N_c) sum_j delta_j exp(-2 pi i n.j/N_G); P = V |delta_n|^2; mode vector n in signed
 convention n_i in [-N_G/2, N_G/2); grid 2 samples the particles shifted by +H/2 on every axis and is
 combined with phase exp(+i pi (n_x+n_y+n_z)/N_G).
