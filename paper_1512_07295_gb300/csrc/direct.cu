@@ -14,6 +14,7 @@
 //         register tile, operands built in shared memory from per-particle, per-axis phase tables.
 // Partial sums of particle slices meet in FP64 atomics.
 #include "host.cuh"
+#include "tc.cuh"
 
 namespace pk {
 
@@ -430,6 +431,8 @@ constexpr int kTcTx = 8, kTcTz = 16;  // main row tiles: 8 i_x x 16 i_z
 constexpr int kTcKr = 2 * kTcK;       // real K per chunk
 constexpr uint32_t kTcTmemCols = 128; // two accumulators of 64 columns
 constexpr uint64_t kTcWaitNs = 1000000000ull;  // bound of every mbarrier wait
+constexpr uint32_t kTcSbo = (kTcKr / 4) * 128;   // 8-row groups of an operand
+constexpr uint32_t kTcIdesc = tc::idesc_tf32(64, 128);
 
 __host__ __device__ inline int tc_main_x_tiles(int ng) { return (ng + kTcTx - 1) / kTcTx; }
 __host__ __device__ inline int tc_main_z_tiles(int ng) { return (ng / 2 + kTcTz - 1) / kTcTz; }
@@ -441,17 +444,6 @@ struct TcSmem {  // byte offsets in the dynamic shared memory (base aligned to 1
   static constexpr uint32_t rec = 2 * stage, bar = rec + kTcK * 16, tmem = bar + 16, total = tmem + 16;
 };
 
-// Byte offset of element (row, k) of a K-major operand with kTcKr columns of K (core matrices of 8 rows
-// x 4 elements, K-adjacent cores 128 B apart, 8-row groups (kTcKr / 4) x 128 B apart).
-__device__ __forceinline__ uint32_t tc_off(int row, int k) {
-  return uint32_t(((row >> 3) * (kTcKr / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
-
-__device__ __forceinline__ void tc_split(float x, float& big, float& small) {
-  big = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);  // nearest TF32 (ties away from 0)
-  small = x - big;
-}
-
 // w e^{-2 pi i T / 2^32}: the phase T (a fraction of a turn, exact in integers) becomes an angle in
 // [-pi, pi) and the hardware sine and cosine (__sincosf, absolute error about 2^-21.4 there) take it.
 __device__ __forceinline__ void tc_expi(uint32_t t, float w, float& re, float& im) {
@@ -459,55 +451,6 @@ __device__ __forceinline__ void tc_expi(uint32_t t, float w, float& re, float& i
   __sincosf(float(int32_t(t)) * 1.46291807926715968e-9f, &s, &c);  // pi / 2^31
   re = w * c;
   im = -(w * s);
-}
-
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  constexpr uint64_t lbo = 128, sbo = (kTcKr / 4) * 128;
-  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) | (uint64_t((sbo >> 4) & 0x3FFF) << 32) |
-         (uint64_t(1) << 46);  // version 1 (sm_100 family); base offset 0; no swizzle
-}
-
-// kind::tf32, FP32 accumulator, A and B K-major, N = 64, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(64 >> 3) << 17) | (uint32_t(128 >> 4) << 24);
-
-__device__ __forceinline__ uint64_t tc_now_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits for the phase of the given parity, for at most about one second.
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = tc_now_ns();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (tc_now_ns() - t0 > kTcWaitNs) return false;
-  }
-}
-
-__device__ __forceinline__ void tc_read_acc(uint32_t taddr, float (&hi)[16], float (&lo)[16]) {
-  uint32_t v[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {  // TwoSum of the chunk total into (hi, lo)
-    const float x = __uint_as_float(v[j]);
-    const float sum = __fadd_rn(hi[j], x);
-    const float bb = __fsub_rn(sum, hi[j]);
-    lo[j] = __fadd_rn(lo[j], __fadd_rn(__fsub_rn(hi[j], __fsub_rn(sum, bb)), __fsub_rn(x, bb)));
-    hi[j] = sum;
-  }
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>::Rec* __restrict__ recs, int64_t n, int ng,
@@ -603,9 +546,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
         float re = 0.0f, im = 0.0f;
         if (a_ok) tc_expi(nx_row * r.px + nz_row * r.pz, r.w, re, im);
         float2 big, small;
-        tc_split(re, big.x, small.x);
-        tc_split(im, big.y, small.y);
-        const uint32_t off = tc_off(ar, 2 * k);
+        tc::split(re, big.x, small.x);
+        tc::split(im, big.y, small.y);
+        const uint32_t off = tc::off(ar, 2 * k, kTcKr);
         *reinterpret_cast<float2*>(stg + off) = big;
         *reinterpret_cast<float2*>(stg + TcSmem::a_part + off) = small;
       }
@@ -616,9 +559,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
         if (b_ok) tc_expi(ny * sRec[k].py, 1.0f, yr, yi);
         const float v0 = br < 32 ? yr : yi, v1 = br < 32 ? -yi : yr;
         float2 big, small;
-        tc_split(v0, big.x, small.x);
-        tc_split(v1, big.y, small.y);
-        const uint32_t off = tc_off(br, 2 * k);
+        tc::split(v0, big.x, small.x);
+        tc::split(v1, big.y, small.y);
+        const uint32_t off = tc::off(br, 2 * k, kTcKr);
         *reinterpret_cast<float2*>(stg + 2 * TcSmem::a_part + off) = big;
         *reinterpret_cast<float2*>(stg + 2 * TcSmem::a_part + TcSmem::b_part + off) = small;
       }
@@ -630,8 +573,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
         const uint32_t sa = sbase + st * TcSmem::stage, sb = sa + 2 * TcSmem::a_part;
         const uint32_t d = tmem + uint32_t(64 * ((c >> 1) & 1));  // chunks 2p, 2p + 1 share accumulator p % 2
         // a k-step advances each operand by two core matrices (256 B): 16 in the address field
-        const uint64_t ab0 = tc_desc(sa), as0 = tc_desc(sa + TcSmem::a_part);
-        const uint64_t bb0 = tc_desc(sb), bs0 = tc_desc(sb + TcSmem::b_part);
+        const uint64_t ab0 = tc::desc(sa, kTcSbo), as0 = tc::desc(sa + TcSmem::a_part, kTcSbo);
+        const uint64_t bb0 = tc::desc(sb, kTcSbo), bs0 = tc::desc(sb + TcSmem::b_part, kTcSbo);
 #pragma unroll
         for (int ks = 0; ks < kTcKr / 8; ++ks) {
           const uint64_t ab = ab0 + 16u * ks, as = as0 + 16u * ks, bb = bb0 + 16u * ks, bs = bs0 + 16u * ks;
@@ -655,12 +598,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
       const int pb = (c - 1) & 1;
       // no block barrier here (the MMA-issuing thread would hold every warp): each warp decides alone,
       // and a timeout reaches the whole block through s_bad at the next chunk's first barrier
-      const bool ok = __all_sync(0xffffffffu, tc_wait(sbase + TcSmem::bar + 8 * pb, pb ? phase1 : phase0));
+      const bool ok = __all_sync(0xffffffffu, tc::wait(sbase + TcSmem::bar + 8 * pb, pb ? phase1 : phase0, kTcWaitNs));
       if (ok) {
         if (pb) phase1 ^= 1u; else phase0 ^= 1u;
         if (outstanding == c - 1) outstanding = -1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (((c - 1) & 1) || c == nchunks) tc_read_acc(tmem + tlane + uint32_t(64 * (((c - 1) >> 1) & 1) + ecol), hi, lo);
+        if (((c - 1) & 1) || c == nchunks) tc::read_acc16(tmem + tlane + uint32_t(64 * (((c - 1) >> 1) & 1) + ecol), hi, lo);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       } else if (lane == 0) {
         *s_bad = 1;
@@ -683,7 +626,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ds_modes_tc(const DsT<float>:
       }
     }
   } else {  // give the MMAs still in flight a bounded wait before the TMEM is freed
-    if (outstanding >= 0) tc_wait(sbase + TcSmem::bar + 8 * (outstanding & 1), (outstanding & 1) ? phase1 : phase0);
+    if (outstanding >= 0) tc::wait(sbase + TcSmem::bar + 8 * (outstanding & 1), (outstanding & 1) ? phase1 : phase0, kTcWaitNs);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
