@@ -70,8 +70,6 @@ typedef enum {
 #define PK_DERR_NONFINITE 1u  /* a position was NaN or infinite; the particle was skipped */
 #define PK_DERR_CELLRANGE 2u  /* a packed cell coordinate was >= N or an offset outside [0,1) */
 #define PK_DERR_TIMEOUT 4u    /* a bounded device-side wait ran out */
-#define PK_DERR_ORDER 8u      /* a binned layout out of slab order inside a tile (see pk_bin); the
-                                 particles behind the FP32 assignment's walk were skipped */
 
 /* A particle on the grid of side N: cell = cx << 20 | cy << 10 | cz (each coordinate < N <= 1024),
  * and the offset of the particle inside that cell in units of H, each in [0, 1). 16 bytes. */
@@ -139,8 +137,8 @@ pk_status pk_prepare(const pk_config* cfg, const double* pos_dev, int64_t n, pk_
  * w_sorted_dev (float[n], or NULL when w_dev is NULL) and tile_offsets_dev (int64[ntiles + 1],
  * ntiles = tiles_per_axis^3, the start of each tile's particles; the last entry is n).
  * Inside a tile, particles are ordered by half-cell slab along x, 2 (c_x mod T) + [f_x >= 1/2]
- * (no defined order within a slab): the FP32 assignment of pk_power_binned walks a tile's slabs in
- * this order, and a binned layout made elsewhere must keep it (PK_DERR_ORDER otherwise). Invalid
+ * (no defined order within a slab); the assignment of pk_power_binned accepts any order inside a
+ * tile, so a binned layout made elsewhere only has to keep each tile's particles together. Invalid
  * packed records (a coordinate >= N or an offset outside [0, 1)) set PK_DERR_CELLRANGE and are
  * written as cell 0, offset 0. */
 pk_status pk_bin(const pk_config* cfg, const void* pos_dev, int32_t pos_format, const float* w_dev,

@@ -16,7 +16,7 @@ OUT = os.path.join(PKG, "_lib")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", SRC]
 SOURCES = [
-    "prepare.cu", "assign.cu", "assign_walk.cu", "estimate.cu", "api.cu", "bispec.cu", "adjoint.cu", "batch.cu",
+    "prepare.cu", "assign.cu", "assign_tiles.cu", "estimate.cu", "api.cu", "bispec.cu", "adjoint.cu", "batch.cu",
     "noalloc.cu", "direct.cu", "aliasing.cu", "multigrid.cu",
 ]
 

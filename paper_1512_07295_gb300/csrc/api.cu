@@ -285,7 +285,7 @@ pk_status run_assign_into(const pk_config* c, const void* pos, int fmt, const pk
     float* g1 = static_cast<float*>(grids);
     if (clear && (e = cudaMemsetAsync(g1, 0, all * 4, s)) != cudaSuccess) return cuda_fail(e, "memset");
     prof_mark(2, s);
-    e = launch_assign_walk_f32(c->order, sorted, w, offsets, n, c->ng, two, g1, two ? g1 + per : nullptr, ldz, s);
+    e = launch_assign_tiles_f32(c->order, sorted, w, offsets, n, c->ng, two, g1, two ? g1 + per : nullptr, ldz, s);
     if (e != cudaSuccess) return cuda_fail(e, "assign (fp32)");
   } else {
     unsigned long long* g1 = static_cast<unsigned long long*>(grids);
@@ -411,7 +411,7 @@ int32_t pk_device_error(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned v = 0;
   if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
-  if (take_err_prepare(&v) != 0 || take_err_assign(&v) != 0 || take_err_walk(&v) != 0 || take_err_direct(&v) != 0)
+  if (take_err_prepare(&v) != 0 || take_err_assign(&v) != 0 || take_err_tiles(&v) != 0 || take_err_direct(&v) != 0)
     return -1;
   return int32_t(v);
 }
@@ -545,7 +545,7 @@ pk_status pk_assign(const pk_config* cfg, const void* pos_dev, int32_t pos_forma
   if ((st = run_bin(&c, pos_dev, pos_format, w_dev, n, b, sorted, w_dev ? wsorted : nullptr, offsets, s)) != PK_OK) return st;
   const float* ws_w = w_dev ? wsorted : nullptr;
   if (c.prec == PK_FP32) {
-    e = launch_assign_walk_f32(c.order, sorted, ws_w, offsets, n, c.ng, c.interlace != 0, static_cast<float*>(grid1_dev),
+    e = launch_assign_tiles_f32(c.order, sorted, ws_w, offsets, n, c.ng, c.interlace != 0, static_cast<float*>(grid1_dev),
                                static_cast<float*>(c.interlace ? grid2_dev : nullptr), c.ng, s);
     return e == cudaSuccess ? PK_OK : cuda_fail(e, "assign (fp32)");
   }

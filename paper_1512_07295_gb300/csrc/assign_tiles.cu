@@ -1,19 +1,15 @@
-// a3 mass assignment, FP32, column walk with register windows (eq:delgrid on both grids of Sec. 3.1).
+// a3 mass assignment, FP32, on tiles of binned particles (eq:delgrid on both grids of Sec. 3.1).
 //
-// A particle adds p^3 products to each grid. Accumulating them one by one in shared memory
-// (k_assign_tile) serialises on shared atomics; here the products are summed in registers and only
-// completed planes leave the thread:
-//  - one block per tile of T^3 cells at a time; the tile's particles (binned by tile and, inside
-//    the tile, by half-cell slab along x: pk_bin) are staged in shared memory in pieces and sorted
-//    there by "key cell" with a counting sort; the key cell is the cell whose fixed stencil (nodes
-//    key + S0 .. key + S0 + p - 1 per axis) covers the particle on that grid, key = cell + delta,
-//    delta in {0, 1};
-//  - each lane owns one key column (k_y, k_z) of one grid and walks it in x with a window of
-//    p x p x p register accumulators (planes key+S0 .. key+S0+p-1); after each x step the oldest
-//    plane is complete, is summed along z across the lanes of the key row with shuffles and is
-//    added to a shared-memory region of (T+4)^3 nodes per grid (32-bit fixed point); the walk of a
-//    tile resumes across its pieces, which the slab order makes possible;
-//  - after the tile, the region is added to the grids in global memory.
+// A particle adds p^3 products to each grid. The particles arrive binned by tile of T^3 cells (pk_bin);
+// a block takes one tile at a time, stages its particles in shared memory in pieces (bulk copies) and
+// accumulates the tile's nodes in a shared region of (T+4)^3 nodes per grid held in 32-bit fixed
+// point, which is added to the grids in global memory after the tile. Two kernels fill the region:
+//  - k_assign_scatter (sparse tiles): each thread adds its particles' p^3 weights per grid with
+//    integer shared atomics;
+//  - k_assign_cells (dense tiles): a piece is counting-sorted by "key cell" (the cell whose fixed
+//    stencil, nodes key + S0 .. key + S0 + p - 1 per axis, covers the particle on that grid); each
+//    lane sums one key cell's particles into a p x p x p register window and adds the window to the
+//    region once, so a node receives one addition per key cell instead of one per particle.
 // Per particle and grid: p weights per axis, p^2 products w_x w_y and p^3 multiply-adds, issued as
 // packed two-lane FP32 FMAs (fma.rn.f32x2) over pairs of y rows for PCS and CIC.
 #include <map>
@@ -24,60 +20,15 @@
 
 namespace pk {
 
-PK_ERR_ACCESSOR(take_err_walk)
+PK_ERR_ACCESSOR(take_err_tiles)
 
-namespace walk {
+namespace tiles {
 
 constexpr int T = kTileCells;  // tile edge (cells)
 constexpr int K = T + 1;       // key cells per axis and grid
 constexpr int NKEY = K * K * K;
 constexpr int RS = T + 4;  // region edge (nodes -1 .. T+2)
 constexpr int RVOL = RS * RS * RS;
-constexpr int MAXWARP = 6;
-
-// Key columns per row (and key cells per axis) that grid G uses: the unshifted grid of an even
-// order keys on floor(u), so its keys stay inside the tile's T cells; the shifted grid, and odd
-// orders (nearest-node keys), reach one cell further.
-template <int P, int G>
-__host__ __device__ constexpr int kspan() {
-  return (G == 0 && P % 2 == 0) ? T : K;
-}
-// Walker lanes: lane = KZ r + kz for key row r of the warp and key column kz (KZ = kspan); 8-column
-// rows give four rows per warp (all 32 lanes hold a column), 9-column rows three (lanes 27..31 hold
-// none). Neighbouring key columns of a row are neighbouring lanes, so a completed plane is summed
-// along z with shuffles before it is added to shared memory.
-template <int P, int G>
-__host__ __device__ constexpr int rows_per_warp() {
-  return 32 / kspan<P, G>();
-}
-template <int P, int G>
-__host__ __device__ constexpr int warps_of_grid() {
-  return kspan<P, G>() / rows_per_warp<P, G>();
-}
-template <int P>
-__host__ __device__ constexpr int threads() {
-  return 32 * (warps_of_grid<P, 0>() + warps_of_grid<P, 1>());
-}
-static_assert(T == 8 && K == 9, "the lane layout assumes 8-cell tiles");
-
-template <bool W>
-__host__ __device__ constexpr int chunk() {
-  return W ? 1024 : 2048;
-}
-
-template <bool W>
-struct Smem {
-  int4 sp[chunk<W>()];
-  unsigned short perm[2][chunk<W>()];
-  int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
-  int reg[2][RVOL];  // the tile's node region, fixed point at the tile's scale
-  float red[MAXWARP];
-  int kmin[2], kmax[2];  // range of key x per grid over the staged chunk
-  int scan[2][MAXWARP];
-  unsigned long long mbar;  // completion barrier of the bulk copy that stages a chunk
-  float sw[W ? chunk<W>() : 1];
-};
-
 // Stencil start relative to the key cell: PCS and TSC start one node below it.
 template <int P>
 __host__ __device__ constexpr int s0() {
@@ -198,7 +149,7 @@ __device__ __forceinline__ float half2x(f2x v, bool high) {
   return high ? q.y : q.x;
 }
 
-// Register window of one walker: plane a (x node key+S0+a) x row b (y) x column c (z).
+// Register window of one key cell: plane a (x node key+S0+a) x row b (y) x column c (z).
 // Even p: y pairs packed in 64-bit registers; odd p: scalars.
 template <int P, bool PACK = (P % 2 == 0)>
 struct Window;
@@ -230,18 +181,6 @@ struct Window<P, true> {
 #pragma unroll
     for (int c = 0; c < P; ++c) out[c] = half2x(v[a][ypair<P>(b)][c], yhigh<P>(b));
   }
-  __device__ __forceinline__ void shift() {
-#pragma unroll
-    for (int a = 0; a + 1 < P; ++a)
-#pragma unroll
-      for (int bp = 0; bp < P / 2; ++bp)
-#pragma unroll
-        for (int c = 0; c < P; ++c) v[a][bp][c] = v[a + 1][bp][c];
-#pragma unroll
-    for (int bp = 0; bp < P / 2; ++bp)
-#pragma unroll
-      for (int c = 0; c < P; ++c) v[P - 1][bp][c] = 0ull;
-  }
 };
 
 template <int P>
@@ -268,18 +207,6 @@ struct Window<P, false> {
   __device__ __forceinline__ void row(int a, int b, float* out) const {
 #pragma unroll
     for (int c = 0; c < P; ++c) out[c] = v[a][b][c];
-  }
-  __device__ __forceinline__ void shift() {
-#pragma unroll
-    for (int a = 0; a + 1 < P; ++a)
-#pragma unroll
-      for (int b = 0; b < P; ++b)
-#pragma unroll
-        for (int c = 0; c < P; ++c) v[a][b][c] = v[a + 1][b][c];
-#pragma unroll
-    for (int b = 0; b < P; ++b)
-#pragma unroll
-      for (int c = 0; c < P; ++c) v[P - 1][b][c] = 0.0f;
   }
 };
 
@@ -325,114 +252,6 @@ __device__ __forceinline__ Operands<P> particle_operands(const int4 r, float wgt
     for (int a = 0; a < P; ++a) o.wx[a] *= wgt;
   }
   return o;
-}
-
-// Plane a of every lane's window, summed over the key columns of each row with shuffles: node z of
-// the row receives column kz's offset c = z - kz - S0 for kz = z - S0 - c; the lane of column kz
-// collects the sum for node kz + S0 and adds it to the region; nodes past the row's last column are
-// added by the columns that reach them. The region holds fixed-point integers (value x scale, rounded
-// to nearest): integer shared-memory atomics run about three times faster than FP32 ones.
-template <int P, int KZ>
-__device__ __forceinline__ void flush_plane(const Window<P>& win, int a, int* reg, int rx, int ry0, int kz, bool valid,
-                                            float scale) {
-#pragma unroll
-  for (int b = 0; b < P; ++b) {
-    float v[P];
-    win.row(a, b, v);
-    float sum = v[0];
-#pragma unroll
-    for (int d = 1; d < P; ++d) {
-      const float t = __shfl_up_sync(0xffffffffu, v[d], d);
-      if (kz >= d) sum += t;
-    }
-    if (valid) {
-      const unsigned r = smem_u32(reg + (rx * RS + ry0 + b) * RS + kz + s0<P>() + 1);
-      red_shared(r, __float2int_rn(sum * scale));
-#pragma unroll
-      for (int c = 1; c < P; ++c)
-        if (kz + c >= KZ) red_shared(r + 4u * c, __float2int_rn(v[c] * scale));
-    }
-  }
-}
-
-// State of one warp of walkers across the chunks of a tile: the register window, the next x step to
-// process (xo) and the number of window shifts since a particle was last added (zs; the window is all
-// zero once zs >= P).
-template <int P>
-struct Walker {
-  Window<P> win;
-  int xo, zs;
-  __device__ __forceinline__ void reset() {
-    win.zero();
-    xo = 0;
-    zs = P;
-  }
-};
-
-// One warp of walkers of grid G (warp-in-grid q) over the staged chunk: lane -> key column (ky, kz);
-// each walks its column in x with its register window; bucket (col, x) holds perm[hist[key-1] ..
-// hist[key]) after the scatter (hist = bucket ends). All 32 lanes run the x loop together (the
-// flush shuffles). A tile's particles arrive ordered by half-cell slab along x, and every grid's key
-// x is a non-decreasing function of that slab, so the chunk's keys lie in [xo, kmax]: steps below
-// kmax are complete after this chunk and are flushed; step kmax stays open for the next chunk (its
-// partial sums stay in the window), unless this is the tile's last chunk, which walks to the end of
-// the span and flushes the remaining planes. Buckets past the grid's key span are empty by
-// construction.
-template <int P, int G, bool W>
-__device__ __forceinline__ void walk_range(Smem<W>& S, Walker<P>& wk, bool last, int q, int lane, float scale) {
-  constexpr int KZ = kspan<P, G>(), R = rows_per_warp<P, G>();
-  const int* ends = S.hist[G];
-  const int r = lane / KZ, kz = lane - r * KZ;
-  const bool valid = r < R;
-  const int ky = R * q + (valid ? r : 0);
-  const int kbase = (ky * K + kz) * K;
-  if (S.kmin[G] < wk.xo && lane == 0) raise_err(PK_DERR_ORDER);  // keys behind the walk: not in slab order
-  const int xe = last ? KZ - 1 : max(wk.xo, S.kmax[G]);
-  int jb = valid ? (kbase + wk.xo == 0 ? 0 : ends[kbase + wk.xo - 1]) : 0;
-  const int ry0 = ky + s0<P>() + 1;  // region row of stencil offset 0
-  int* reg = S.reg[G];
-  const unsigned short* perm = S.perm[G];
-  Window<P>& win = wk.win;
-#pragma unroll 1
-  for (int x = wk.xo; x <= xe; ++x) {
-    const int je = valid ? ends[kbase + x] : 0;
-    if (__any_sync(0xffffffffu, jb < je)) {
-      wk.zs = 0;
-      // one particle per iteration; the next record is loaded before the current one is accumulated
-      int j = jb;
-      int4 r0 = make_int4(0, 0, 0, 0);
-      float s0w = 1.0f;
-      if (j < je) {
-        const int i0 = perm[j];
-        r0 = S.sp[i0];
-        if (W) s0w = S.sw[i0];
-      }
-      for (; j < je; ++j) {
-        const int4 c0 = r0;
-        const float c0w = s0w;
-        if (j + 1 < je) {
-          const int i0 = perm[j + 1];
-          r0 = S.sp[i0];
-          if (W) s0w = S.sw[i0];
-        }
-        win.add(particle_operands<P, G>(c0, c0w * weight_scale<P>()));
-      }
-    }
-    if (valid) jb = je;
-    if (x < xe || last) {  // node plane x + s0 is complete: add it to the region and shift the window
-      if (wk.zs < P) flush_plane<P, KZ>(win, 0, reg, x + s0<P>() + 1, ry0, kz, valid, scale);
-      win.shift();
-      ++wk.zs;
-    }
-  }
-  if (last) {  // the remaining planes KZ + s0 .. KZ + s0 + P - 2 (plane a is non-zero while a < P - zs)
-#pragma unroll
-    for (int a = 0; a + 1 < P; ++a)
-      if (a < P - wk.zs) flush_plane<P, KZ>(win, a, reg, KZ + a + s0<P>() + 1, ry0, kz, valid, scale);
-    wk.reset();
-  } else {
-    wk.xo = xe;
-  }
 }
 
 // Bulk copy (TMA) of `bytes` from global to shared memory, completing on the mbarrier at bar.
@@ -497,10 +316,18 @@ __device__ __forceinline__ void flush_region(const int* reg, int ngrid, int cx0,
   }
 }
 
-// Fixed-point scale 2^e of a tile's region: no node (nor any partial sum of one) exceeds the tile's
-// total |weight| B, and B 2^e < 2^30 leaves room for the rounding of every addition. With weights,
-// B is summed by the block (red: one float per warp); the caller synchronises before the first use.
-template <bool W>
+// Largest share of a particle's weight that one node receives: the peak of the one-dimensional
+// window cubed (CIC and NGP 1, TSC 3/4 per axis, PCS 2/3 per axis).
+template <int P>
+__host__ __device__ constexpr float node_share() {
+  return P == 4 ? 8.0f / 27.0f : (P == 3 ? 27.0f / 64.0f : 1.0f);
+}
+
+// Fixed-point scale 2^e of a tile's region: no node (nor any partial sum of one) exceeds
+// node_share x the tile's total |weight| B, and that bound x 2^e < 2^30 leaves room for the rounding
+// of every addition. With weights, B is summed by the block (red: one float per warp); the caller
+// synchronises before the first use.
+template <int P, bool W>
 __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t end, float* red, int nwarp, int tid,
                                            int nthreads, float* scale, float* inv_scale) {
   float bound = float(end - beg);
@@ -516,15 +343,15 @@ __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t 
     bound *= 1.0001f;  // the FP32 sum's rounding
   }
   int ex;
-  frexpf(fmaxf(bound, 1.0f), &ex);  // bound < 2^ex
+  frexpf(fmaxf(bound * node_share<P>(), 1.0f), &ex);  // node bound < 2^ex
   *scale = ldexpf(1.0f, 30 - ex);
   *inv_scale = ldexpf(1.0f, ex - 30);
 }
 
 // ---- direct scatter (sparse tiles) ------------------------------------------------------------------
-// A walk pays for every x step of every key column of a tile whether or not its buckets hold
-// particles; on sparse tiles that fixed cost dominates. There, each thread adds its particles' p^3
-// weights per grid straight into the fixed-point region with integer shared atomics instead.
+// Sorting a piece by key cell costs a fixed amount per piece (histograms, scans, the count order);
+// on sparse tiles that fixed cost dominates. There, each thread adds its particles' p^3 weights per
+// grid straight into the fixed-point region with integer shared atomics instead.
 constexpr int SCATTER_THREADS = 256;
 
 // Pieces of the scatter are staged in two buffers: the next piece is copied while this one is used.
@@ -567,179 +394,18 @@ __device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int l
     }
 }
 
-}  // namespace walk
-
-template <int P, bool W>
-__global__ void __launch_bounds__(walk::threads<P>(), 3)
-    k_assign_walk(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
-                  int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                  int64_t cat_stride) {
-  using namespace walk;
-  constexpr int CH = chunk<W>();
-  constexpr int THREADS = threads<P>(), NWARP = THREADS / 32, NW0 = warps_of_grid<P, 0>();
-  constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
-  {  // blockIdx.y selects a catalogue of a batch: its grids and its tile offsets
-    const int cat = blockIdx.y;
-    g1 += cat * cat_stride;
-    if (g2) g2 += cat * cat_stride;
-    toff += int64_t(cat) * ntile * ntile * ntile;
-  }
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<W>& S = *reinterpret_cast<Smem<W>*>(smem_raw);
-  const int ngrid = interlace ? 2 : 1;
-  const int ntiles = ntile * ntile * ntile;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-  }
-  __syncthreads();
-  unsigned parity = 0;
-  Walker<P> wk;
-  wk.reset();
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
-    if (beg >= end) continue;
-    const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
-    const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
-    for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
-    float scale, inv_scale;
-    tile_scale<W>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
-    for (int64_t c0 = beg; c0 < end; c0 += CH) {
-      const int m = int(min(int64_t(CH), end - c0));
-      // stage the chunk with one bulk copy (16-byte records, 16-byte aligned)
-      if (tid == 0) bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
-      if (W)
-        for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
-      for (int i = tid; i < 2 * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
-      if (tid < 2) {
-        S.kmin[tid] = K;
-        S.kmax[tid] = -1;
-      }
-      const bool arrived = bulk_wait(&S.mbar, parity);
-      parity ^= 1u;
-      if (__syncthreads_or(!arrived)) {  // the copy did not complete: report, drain, stop
-        if (tid == 0) {
-          raise_err(PK_DERR_TIMEOUT);
-          bulk_wait(&S.mbar, parity ^ 1u);
-        }
-        return;
-      }
-      // count the key cells of both grids; the record's cell word is replaced by the two keys
-      // (grid 1 in the low half, grid 2 in the high half), or by -1 for a particle that is skipped;
-      // the range of key x per grid is gathered for the walk
-      int lo0 = K, hi0 = -1, lo1 = K, hi1 = -1;
-      for (int i = tid; i < m; i += THREADS) {
-        const int4 r = S.sp[i];
-        const uint32_t cell = uint32_t(r.x);
-        const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        if ((cell >> 30) == 0 && unsigned(lx) < unsigned(T) && unsigned(ly) < unsigned(T) && unsigned(lz) < unsigned(T)) {
-          float t;
-          const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
-          const int kx1 = lx + grid_key<P, 0>(fx, &t);
-          const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + kx1;
-          atomicAdd(&S.hist[0][k1], 1);
-          lo0 = min(lo0, kx1);
-          hi0 = max(hi0, kx1);
-          int k2 = 0;
-          if (interlace) {
-            const int kx2 = lx + grid_key<P, 1>(fx, &t);
-            k2 = ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + kx2;
-            atomicAdd(&S.hist[1][k2], 1);
-            lo1 = min(lo1, kx2);
-            hi1 = max(hi1, kx2);
-          }
-          S.sp[i].x = k1 | (k2 << 16);
-        } else {
-          raise_err(PK_DERR_CELLRANGE);
-          S.sp[i].x = -1;
-        }
-      }
-      lo0 = __reduce_min_sync(0xffffffffu, lo0);
-      hi0 = __reduce_max_sync(0xffffffffu, hi0);
-      lo1 = __reduce_min_sync(0xffffffffu, lo1);
-      hi1 = __reduce_max_sync(0xffffffffu, hi1);
-      if (lane == 0) {
-        atomicMin(&S.kmin[0], lo0);
-        atomicMax(&S.kmax[0], hi0);
-        atomicMin(&S.kmin[1], lo1);
-        atomicMax(&S.kmax[1], hi1);
-      }
-      __syncthreads();
-      // block-wide exclusive scan of both histograms (NKEY + 1 entries each)
-      {
-        int v0[SCAN_PER_THREAD], v1[SCAN_PER_THREAD];
-        int s0v = 0, s1v = 0;
-#pragma unroll
-        for (int k = 0; k < SCAN_PER_THREAD; ++k) {
-          const int idx = tid * SCAN_PER_THREAD + k;
-          v0[k] = idx <= NKEY ? S.hist[0][idx] : 0;
-          v1[k] = idx <= NKEY ? S.hist[1][idx] : 0;
-          s0v += v0[k];
-          s1v += v1[k];
-        }
-        int x0 = s0v, x1 = s1v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
-          if (lane >= o) {
-            x0 += y0;
-            x1 += y1;
-          }
-        }
-        if (lane == 31) {
-          S.scan[0][warp] = x0;
-          S.scan[1][warp] = x1;
-        }
-        __syncthreads();
-        int e0 = x0 - s0v, e1 = x1 - s1v;
-        for (int q = 0; q < warp; ++q) {
-          e0 += S.scan[0][q];
-          e1 += S.scan[1][q];
-        }
-#pragma unroll
-        for (int k = 0; k < SCAN_PER_THREAD; ++k) {
-          const int idx = tid * SCAN_PER_THREAD + k;
-          if (idx <= NKEY) {
-            S.hist[0][idx] = e0;
-            S.hist[1][idx] = e1;
-          }
-          e0 += v0[k];
-          e1 += v1[k];
-        }
-      }
-      __syncthreads();
-      // scatter particle indices into key order; hist[key] advances to the bucket's end
-      for (int i = tid; i < m; i += THREADS) {
-        const int keys = S.sp[i].x;
-        if (keys < 0) continue;
-        S.perm[0][atomicAdd(&S.hist[0][keys & 0xffff], 1)] = (unsigned short)i;
-        if (interlace) S.perm[1][atomicAdd(&S.hist[1][keys >> 16], 1)] = (unsigned short)i;
-      }
-      __syncthreads();
-      // walk: the first NW0 warps grid 1, the others grid 2 (warp-uniform grid)
-      const bool last = c0 + CH >= end;
-      if (warp < NW0)
-        walk_range<P, 0, W>(S, wk, last, warp, lane, scale);
-      else if (interlace)
-        walk_range<P, 1, W>(S, wk, last, warp - NW0, lane, scale);
-      __syncthreads();
-    }
-    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
-    __syncthreads();
-  }
-}
+}  // namespace tiles
 
 // a3, FP32, direct scatter: a block takes tiles in a grid-stride sequence and their pieces in
 // order, the copy of the next piece overlapping the use of the current one; particles are spread over
 // the lanes of a warp q = ceil(m / 32) records apart (different cells, so a warp's atomics seldom meet
-// on one node); fixed-point regions are flushed to the grids as in k_assign_walk.
+// on one node); the fixed-point regions are added to the grids by flush_region.
 template <int P, bool W>
-__global__ void __launch_bounds__(walk::SCATTER_THREADS, 4)
+__global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
                      int64_t n, int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
                      int64_t cat_stride) {
-  using namespace walk;
+  using namespace tiles;
   constexpr int CH = scatter_chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
   {
     const int cat = blockIdx.y;
@@ -793,7 +459,7 @@ __global__ void __launch_bounds__(walk::SCATTER_THREADS, 4)
       cy0 = ty * T;
       cz0 = tz * T;
       for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
-      tile_scale<W>(w, cur.beg, cur.end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+      tile_scale<P, W>(w, cur.beg, cur.end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
     }
     // the other buffer was released by the synchronisation that ended the previous piece
     if (has_next && tid == 0)
@@ -840,6 +506,263 @@ __global__ void __launch_bounds__(walk::SCATTER_THREADS, 4)
   }
 }
 
+// ---- cells (dense tiles) ---------------------------------------------------------------------------
+// Per staged piece of a tile the particles are counting-sorted by key cell on each grid; the non-empty
+// key cells of both grids then form one list ordered by particle count, largest first. Thread t takes
+// item t of each round of 256 items in even rounds and item 255 - t in odd ones, so the 32 lanes of
+// a warp hold cells of nearly equal load and the warps' totals even out. A lane sums its cell's
+// particles into a register window of p^3 node values (the cell's whole stencil) and adds the window
+// to the tile's fixed-point region once. Pieces need no order inside the tile.
+namespace tiles {
+constexpr int CELL_THREADS = 256;
+constexpr int CNT_BINS = 64;  // particle counts above 63 share the first place of the ordering
+
+// Pieces of 64 KB of records: a key cell's window is added to the region once per piece, so larger
+// pieces mean fewer (and fuller) additions; two blocks still fit an SM.
+template <bool W>
+__host__ __device__ constexpr int cell_chunk() {
+  return W ? 2048 : 4096;
+}
+
+template <bool W>
+struct CellSmem {
+  int4 sp[cell_chunk<W>()];
+  unsigned short perm[2][cell_chunk<W>()];
+  int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
+  int reg[2][RVOL];
+  unsigned short order[2 * NKEY];  // non-empty key cells (grid in bit 15), largest bucket first
+  int cbin[CNT_BINS];
+  int nitems;
+  float red[CELL_THREADS / 32];
+  int scan[2][CELL_THREADS / 32];
+  unsigned long long mbar;
+  float sw[W ? cell_chunk<W>() : 1];
+};
+
+// Window operands of one particle on grid g (a runtime grid: the lanes of a warp may hold cells of
+// either grid).
+template <int P>
+__device__ __forceinline__ Operands<P> cell_operands(const int4 r, float wgt, bool g) {
+  int4 q = r;
+  if (g) {  // the shifted grid samples the particle displaced by H/2: the same offsets as grid_key<P, 1>
+    float f;
+    half_shift(__int_as_float(r.y), &f);
+    q.y = __float_as_int(f);
+    half_shift(__int_as_float(r.z), &f);
+    q.z = __float_as_int(f);
+    half_shift(__int_as_float(r.w), &f);
+    q.w = __float_as_int(f);
+  }
+  return particle_operands<P, 0>(q, wgt);
+}
+
+// One key cell of grid g: its bucket of particles into a register window, then the window into the
+// region (nodes key + S0 + 1 .. key + S0 + p per axis). The fixed-point scale (a power of two) rides
+// on the particle weight, so the window already holds fixed-point values; the next record is loaded
+// before the current one is accumulated.
+template <int P, bool W>
+__device__ __forceinline__ void cell_key(const CellSmem<W>& S, int item, float wscale) {
+  const bool g = item >> 15;
+  const int key = item & 0x7fff;
+  const int* ends = S.hist[g];
+  const unsigned short* perm = S.perm[g];
+  const int jb = key == 0 ? 0 : ends[key - 1], je = ends[key];
+  const int kx = key % K, kz = (key / K) % K, ky = key / (K * K);
+  Window<P> win;
+  win.zero();
+  int4 r = make_int4(0, 0, 0, 0);
+  float rw = 1.0f;
+  if (jb < je) {
+    const int i = perm[jb];
+    r = S.sp[i];
+    if (W) rw = S.sw[i];
+  }
+  for (int j = jb; j < je; ++j) {
+    const int4 c = r;
+    const float cw = rw;
+    if (j + 1 < je) {
+      const int i = perm[j + 1];
+      r = S.sp[i];
+      if (W) rw = S.sw[i];
+    }
+    win.add(cell_operands<P>(c, cw * wscale, g));
+  }
+  const unsigned base =
+      smem_u32(&S.reg[g][0] + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1);
+#pragma unroll
+  for (int a = 0; a < P; ++a)
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      float v[P];
+      win.row(a, b, v);
+#pragma unroll
+      for (int c = 0; c < P; ++c) red_shared(base + 4u * ((a * RS + b) * RS + c), __float2int_rn(v[c]));
+    }
+}
+}  // namespace tiles
+
+template <int P, bool W>
+__global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
+    k_assign_cells(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
+                   int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
+                   int64_t cat_stride) {
+  using namespace tiles;
+  constexpr int CH = cell_chunk<W>(), THREADS = CELL_THREADS, NWARP = THREADS / 32;
+  constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
+  static_assert(CNT_BINS == 64, "count bins: two per lane of one warp");
+  {  // blockIdx.y selects a catalogue of a batch: its grids and its tile offsets
+    const int cat = blockIdx.y;
+    g1 += cat * cat_stride;
+    if (g2) g2 += cat * cat_stride;
+    toff += int64_t(cat) * ntile * ntile * ntile;
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CellSmem<W>& S = *reinterpret_cast<CellSmem<W>*>(smem_raw);
+  const int ngrid = interlace ? 2 : 1;
+  const int ntiles = ntile * ntile * ntile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  }
+  __syncthreads();
+  unsigned parity = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
+    if (beg >= end) continue;
+    const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
+    const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
+    for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
+    float scale, inv_scale;
+    tile_scale<P, W>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+    const float wscale = scale * weight_scale<P>();
+    for (int64_t c0 = beg; c0 < end; c0 += CH) {
+      const int m = int(min(int64_t(CH), end - c0));
+      if (tid == 0) bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
+      if (W)
+        for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
+      for (int i = tid; i < 2 * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
+      if (tid < CNT_BINS) S.cbin[tid] = 0;
+      const bool arrived = bulk_wait(&S.mbar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!arrived)) {  // the copy did not complete: report, drain, stop
+        if (tid == 0) {
+          raise_err(PK_DERR_TIMEOUT);
+          bulk_wait(&S.mbar, parity ^ 1u);
+        }
+        return;
+      }
+      // key cells of both grids (the record's cell word becomes the two keys, or -1 when skipped)
+      for (int i = tid; i < m; i += THREADS) {
+        const int4 r = S.sp[i];
+        const uint32_t cell = uint32_t(r.x);
+        const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
+        if ((cell >> 30) == 0 && unsigned(lx) < unsigned(T) && unsigned(ly) < unsigned(T) && unsigned(lz) < unsigned(T)) {
+          float t;
+          const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
+          const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + lx + grid_key<P, 0>(fx, &t);
+          atomicAdd(&S.hist[0][k1], 1);
+          int k2 = 0;
+          if (interlace) {
+            k2 = ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + lx + grid_key<P, 1>(fx, &t);
+            atomicAdd(&S.hist[1][k2], 1);
+          }
+          S.sp[i].x = k1 | (k2 << 16);
+        } else {
+          raise_err(PK_DERR_CELLRANGE);
+          S.sp[i].x = -1;
+        }
+      }
+      __syncthreads();
+      // the non-empty key cells of both grids counted by bucket size (bin 0: the largest)
+      for (int i = tid; i < ngrid * NKEY; i += THREADS) {
+        const int cnt = (&S.hist[0][0])[i + i / NKEY];  // grid i / NKEY, key i % NKEY
+        if (cnt > 0) atomicAdd(&S.cbin[CNT_BINS - 1 - min(cnt, CNT_BINS - 1)], 1);
+      }
+      __syncthreads();
+      // block-wide exclusive scan of both histograms; warp 0 also scans the count bins
+      {
+        int v0[SCAN_PER_THREAD], v1[SCAN_PER_THREAD];
+        int s0v = 0, s1v = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+          const int idx = tid * SCAN_PER_THREAD + k;
+          v0[k] = idx <= NKEY ? S.hist[0][idx] : 0;
+          v1[k] = idx <= NKEY ? S.hist[1][idx] : 0;
+          s0v += v0[k];
+          s1v += v1[k];
+        }
+        int x0 = s0v, x1 = s1v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+          if (lane >= o) {
+            x0 += y0;
+            x1 += y1;
+          }
+        }
+        if (lane == 31) {
+          S.scan[0][warp] = x0;
+          S.scan[1][warp] = x1;
+        }
+        if (warp == 0) {  // 64 count bins, two per lane
+          const int a0 = S.cbin[2 * lane], a1 = S.cbin[2 * lane + 1];
+          int x = a0 + a1;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+          }
+          const int ex = x - a0 - a1;
+          S.cbin[2 * lane] = ex;
+          S.cbin[2 * lane + 1] = ex + a0;
+          if (lane == 31) S.nitems = x;
+        }
+        __syncthreads();
+        int e0 = x0 - s0v, e1 = x1 - s1v;
+        for (int q = 0; q < warp; ++q) {
+          e0 += S.scan[0][q];
+          e1 += S.scan[1][q];
+        }
+#pragma unroll
+        for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+          const int idx = tid * SCAN_PER_THREAD + k;
+          if (idx <= NKEY) {
+            // the key's place in the count order, taken while its count is at hand
+            if (idx < NKEY) {
+              if (v0[k] > 0) S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1)] = (unsigned short)idx;
+              if (v1[k] > 0)
+                S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1)] = (unsigned short)(idx | 0x8000);
+            }
+            S.hist[0][idx] = e0;
+            S.hist[1][idx] = e1;
+          }
+          e0 += v0[k];
+          e1 += v1[k];
+        }
+      }
+      __syncthreads();
+      // particle indices into key order; hist[key] advances to the bucket's end
+      for (int i = tid; i < m; i += THREADS) {
+        const int keys = S.sp[i].x;
+        if (keys < 0) continue;
+        S.perm[0][atomicAdd(&S.hist[0][keys & 0xffff], 1)] = (unsigned short)i;
+        if (interlace) S.perm[1][atomicAdd(&S.hist[1][keys >> 16], 1)] = (unsigned short)i;
+      }
+      __syncthreads();
+      const int nitems = S.nitems;
+      for (int r0 = 0; r0 < nitems; r0 += 2 * THREADS) {  // two rounds: ascending, then descending
+        if (r0 + tid < nitems) cell_key<P, W>(S, S.order[r0 + tid], wscale);
+        const int i1 = r0 + 2 * THREADS - 1 - tid;
+        if (i1 < nitems) cell_key<P, W>(S, S.order[i1], wscale);
+      }
+      __syncthreads();
+    }
+    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
+    __syncthreads();
+  }
+}
+
 // Shared-memory opt-in and resident blocks per SM of a kernel, set up once per (kernel, device): later
 // launches make no attribute or occupancy calls, so a call captured in a CUDA graph holds launches only.
 static cudaError_t kernel_setup(const void* kernel, int threads, size_t smem, int* per_sm) {
@@ -862,10 +785,18 @@ static cudaError_t kernel_setup(const void* kernel, int threads, size_t smem, in
   return cudaSuccess;
 }
 
-// Mean particles per tile below which the direct scatter replaces the walk. Measured per tile on one
-// GB300: the walk costs about 73 ns + 0.018 ns per particle of block time, the scatter 19 ns + 0.048 ns,
-// so they cross near 1800 particles per tile (8^3 cells).
-constexpr int64_t kScatterMaxMean = 1536;
+// Mean particles per tile below which the direct scatter replaces the key-cell kernel, per order.
+// Measured on one GB300 over uniform catalogues of 256 .. 8192 particles per tile (8^3 cells, both
+// grids): PCS crosses near 750, TSC near 1400, CIC near 7000; for NGP (one node per particle) the
+// scatter stays ahead throughout.
+static int64_t scatter_max_mean(int order) {
+  switch (order) {
+    case 4: return 768;
+    case 3: return 1408;
+    case 2: return 6144;
+    default: return INT64_MAX / (int64_t(1) << 40);  // the product with the tile count cannot overflow
+  }
+}
 
 template <int P, bool W>
 static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
@@ -873,54 +804,60 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
                                      int64_t cat_stride) {
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
-  const size_t smem = sizeof(walk::ScatterSmem<W>);
+  const size_t smem = sizeof(tiles::ScatterSmem<W>);
   int per_sm = 1;
-  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W>), walk::SCATTER_THREADS, smem, &per_sm);
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W>), tiles::SCATTER_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
-  k_assign_scatter<P, W><<<blocks, walk::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
+  k_assign_scatter<P, W><<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
                                                                      cat_stride);
   count_launch();
   return cudaGetLastError();
 }
 
-bool assign_uses_scatter(int64_t n, int ng, int ncat) {
+bool assign_uses_scatter(int64_t n, int ng, int ncat, int order) {
   const int64_t nt = tiles_per_axis(ng);
-  return n < kScatterMaxMean * nt * nt * nt * ncat;
+  return n < scatter_max_mean(order) * nt * nt * nt * ncat;
 }
 
 template <int P, bool W>
-static cudaError_t launch_walk_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
-                                  float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
+static cudaError_t launch_cells_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                   bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
+                                   int64_t cat_stride) {
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
-  if (assign_uses_scatter(n, ng, ncat))  // sparse tiles: the direct scatter
-    return launch_scatter_pw<P, W>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-  const size_t smem = sizeof(walk::Smem<W>);
+  const size_t smem = sizeof(tiles::CellSmem<W>);
   int per_sm = 1;
-  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_walk<P, W>), walk::threads<P>(), smem, &per_sm);
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_cells<P, W>), tiles::CELL_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
-  k_assign_walk<P, W><<<blocks, walk::threads<P>(), smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, cat_stride);
+  k_assign_cells<P, W><<<blocks, tiles::CELL_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
+                                                                 cat_stride);
   count_launch();
   return cudaGetLastError();
 }
 
+// Sparse tiles: the scatter; dense ones: the key cells (NGP: always the scatter).
 template <int P>
-static cudaError_t launch_walk_p(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
-                                 float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
-  return w ? launch_walk_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
-           : launch_walk_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+static cudaError_t launch_tiles_p(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
+                                  float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
+  if (P == 1 || assign_uses_scatter(n, ng, ncat, P))
+    return w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
+             : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+  if constexpr (P > 1)
+    return w ? launch_cells_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
+             : launch_cells_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_assign_walk_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
-                                   bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
-                                   int64_t cat_stride) {
+cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
+                                    int64_t cat_stride) {
   switch (order) {
-    case 1: return launch_walk_p<1>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 2: return launch_walk_p<2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 3: return launch_walk_p<3>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 4: return launch_walk_p<4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 1: return launch_tiles_p<1>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 2: return launch_tiles_p<2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 3: return launch_tiles_p<3>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 4: return launch_tiles_p<4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
     case 5:
     case 6:  // orders beyond PCS: the direct scatter of the records (box unused for packed records)
       if (ncat != 1) return cudaErrorInvalidValue;

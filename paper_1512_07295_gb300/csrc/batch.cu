@@ -116,16 +116,16 @@ pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* off
     // a2: batched counting sort (sorted indices relative to the group's first particle)
     CatRanges rel = r;
     for (int c = 0; c <= nb; ++c) rel.off[c] = r.off[c] - r.off[0];
-    // the direct scatter of sparse tiles needs no slab order: tile-only binning through shared memory
-    if (assign_uses_scatter(rel.off[nb], ng, nb) && int64_t(nt) * nt * nt <= kSmemBinTiles)
+    // the assignment needs no order inside a tile: tile-only binning through shared memory
+    if (int64_t(nt) * nt * nt <= kSmemBinTiles)
       e = launch_bin_batch_tiles(base + r.off[0], rel, nt, L.sorted, L.offsets, L.counts, L.scan, s);
     else
       e = launch_bin_batch(base + r.off[0], rel, ng, nt, L.sorted, L.offsets, L.counts, L.sub, L.scan, s);
     if (e != cudaSuccess) return cuda_fail(e, "batch bin");
     // a3: all catalogues' grid pairs
     if ((e = cudaMemsetAsync(L.grids, 0, size_t(2) * nb * per * sizeof(float), s)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = launch_assign_walk_f32(cfg->order, L.sorted, nullptr, L.offsets, rel.off[nb], ng, true, L.grids, L.grids + per,
-                                    ng + 2, s, nb, 2 * per)) != cudaSuccess)
+    if ((e = launch_assign_tiles_f32(cfg->order, L.sorted, nullptr, L.offsets, rel.off[nb], ng, true, L.grids, L.grids + per,
+                                     ng + 2, s, nb, 2 * per)) != cudaSuccess)
       return cuda_fail(e, "batch assign");
     k_batch_sums<<<1, kMaxBatch, 0, s>>>(L.wsums, rel); count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch sums");

@@ -16,7 +16,7 @@ void count_launch(int k = 1);  // number of kernels this library launched (pk_pr
 // Per-translation-unit device error words (see PK_ERR_ACCESSOR): OR into *acc and clear.
 int take_err_prepare(unsigned* acc);
 int take_err_assign(unsigned* acc);
-int take_err_walk(unsigned* acc);
+int take_err_tiles(unsigned* acc);
 int take_err_direct(unsigned* acc);
 // Raises a kernel's dynamic shared-memory limit to at least smem bytes, once per (kernel, device) and
 // size: calls captured in a CUDA graph after the first eager call then issue launches only.
@@ -51,7 +51,7 @@ struct CatRanges {  // particle ranges of the catalogues of one batch group (abs
   int nb;
   int ng;
 };
-// Batched binning by tile only (no slab order inside a tile, for the direct scatter), counted and
+// Batched binning by tile only (no slab order inside a tile), counted and
 // placed through per-block shared-memory histograms: one global atomic per (block, tile) instead of
 // one per particle. Needs ntile^3 <= kSmemBinTiles; counts: nb ntile^3 entries.
 constexpr int kSmemBinTiles = 8192;
@@ -67,14 +67,15 @@ cudaError_t launch_assign_direct_f32(int order, const void* pos, int fmt, const 
                                      bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
 cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
-// FP32 column-walk assignment (assign_walk.cu), same layout and binned input as the tiled kernel;
-// ncat > 1: catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids g + c * cat_stride.
-// Whether launch_assign_walk_f32 takes the direct scatter (sparse tiles) for n particles over ncat
-// catalogues of side ng; the scatter needs no slab order inside a tile.
-bool assign_uses_scatter(int64_t n, int ng, int ncat);
-cudaError_t launch_assign_walk_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
-                                   bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
-                                   int64_t cat_stride = 0);
+// FP32 tile assignment (assign_tiles.cu: the scatter on sparse tiles, the key-cell kernel on dense
+// ones), same layout and binned input as the tiled kernel, any particle order inside a tile; ncat > 1:
+// catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids g + c * cat_stride.
+// Whether launch_assign_tiles_f32 takes the direct scatter for n particles of order `order` over ncat
+// catalogues of side ng.
+bool assign_uses_scatter(int64_t n, int ng, int ncat, int order);
+cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
+                                    int64_t cat_stride = 0);
 // Batch: ncat catalogues (unit weights, interlaced), catalogue c's tile offsets at toff + c * ntiles and
 // its two grids at grids + c * 2 * ng*ng*ldz.
 cudaError_t launch_assign_tile_batch(int order, const pk_cellpos* p, const int64_t* toff, int64_t n, int ng, int ncat,

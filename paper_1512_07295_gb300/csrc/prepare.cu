@@ -3,8 +3,9 @@
 // a1 (Sec. 2.3, s = (x_j - x)/H): an FP64 position is wrapped into [0, L) (periodic box) and split
 // into the integer cell c = floor(x/H) and the offset f = x/H - c in [0, 1), stored as FP32.
 // a2: particles are grouped by tile of T^3 cells with a counting sort (histogram, exclusive scan,
-// scatter), and inside a tile by half-cell slab along x (key tile * 2T + 2 (c_x mod T) + [f_x >= 1/2]):
-// the assignment walks a tile's slabs in order and can stage a large tile in several pieces.
+// scatter), and inside a tile by half-cell slab along x (key tile * 2T + 2 (c_x mod T) + [f_x >= 1/2]),
+// which keeps neighbouring cells' particles together in a staged piece; the assignment itself
+// accepts any order inside a tile.
 // Histogram and scatter use warp-aggregated atomics: consecutive particles of a spatially ordered
 // catalogue share a key, and one atomic per distinct key per warp replaces 32. Particles are
 // validated on the way (an invalid record is reported and binned as cell 0, offset 0).

@@ -16,7 +16,7 @@ PK_FP64, PK_FP32, PK_FIXED64 = 0, 1, 2
 PK_POS_F64_XYZ, PK_POS_CELL_F32OFF = 0, 1
 (PK_WS_ASSIGN, PK_WS_FFT_ESTIMATE, PK_WS_POWER, PK_WS_POWER_BINNED, PK_WS_BIN, PK_WS_BACKWARD, PK_WS_BISPECTRUM,
  PK_WS_BISPECTRUM_COUNTS, PK_WS_POWER_HOST, PK_WS_DIRECT, PK_WS_CROSS, PK_WS_ALIASING) = range(12)
-PK_DERR_NONFINITE, PK_DERR_CELLRANGE, PK_DERR_TIMEOUT, PK_DERR_ORDER = 1, 2, 4, 8
+PK_DERR_NONFINITE, PK_DERR_CELLRANGE, PK_DERR_TIMEOUT = 1, 2, 4
 
 
 class PkConfig(ctypes.Structure):
