@@ -254,6 +254,11 @@ __device__ __forceinline__ Operands<P> particle_operands(const int4 r, float wgt
   return o;
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned source) from global memory into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Bulk copy (TMA) of `bytes` from global to shared memory, completing on the mbarrier at bar.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
@@ -638,7 +643,16 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     const float wscale = scale * weight_scale<P>();
     for (int64_t c0 = beg; c0 < end; c0 += CH) {
       const int m = int(min(int64_t(CH), end - c0));
-      if (tid == 0) bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
+      if (tid == 0) {
+        bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
+        // the block's next piece (of this tile, else of one of its next 8 tiles) moves to L2 meanwhile
+        int64_t nb = c0 + CH, ne = end;
+        for (int t = tile + gridDim.x, k = 0; nb >= ne && t < ntiles && k < 8; t += gridDim.x, ++k) {
+          nb = max(toff[t], int64_t(0));
+          ne = min(toff[t + 1], n);
+        }
+        if (nb < ne) bulk_prefetch_l2(p + nb, unsigned(min(int64_t(CH), ne - nb)) * 16u);
+      }
       if (W)
         for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
       for (int i = tid; i < 2 * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
@@ -652,25 +666,34 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         }
         return;
       }
-      // key cells of both grids (the record's cell word becomes the two keys, or -1 when skipped)
-      for (int i = tid; i < m; i += THREADS) {
-        const int4 r = S.sp[i];
-        const uint32_t cell = uint32_t(r.x);
-        const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        if ((cell >> 30) == 0 && unsigned(lx) < unsigned(T) && unsigned(ly) < unsigned(T) && unsigned(lz) < unsigned(T)) {
-          float t;
-          const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
-          const int k1 = ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + lx + grid_key<P, 0>(fx, &t);
-          atomicAdd(&S.hist[0][k1], 1);
-          int k2 = 0;
-          if (interlace) {
-            k2 = ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + lx + grid_key<P, 1>(fx, &t);
-            atomicAdd(&S.hist[1][k2], 1);
+      // key cells of both grids (the record's cell word becomes the two keys, or -1 when skipped);
+      // four records per thread and pass, loaded before any is used
+      for (int i0 = tid; i0 < m; i0 += 4 * THREADS) {
+        int4 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = i0 + u * THREADS < m ? S.sp[i0 + u * THREADS] : make_int4(-1, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * THREADS;
+          if (i >= m) break;
+          const uint32_t cell = uint32_t(r[u].x);
+          const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
+          if ((cell >> 30) == 0 && unsigned(lx) < unsigned(T) && unsigned(ly) < unsigned(T) && unsigned(lz) < unsigned(T)) {
+            float t;
+            const float fx = __int_as_float(r[u].y), fy = __int_as_float(r[u].z), fz = __int_as_float(r[u].w);
+            const int k1 =
+                ((ly + grid_key<P, 0>(fy, &t)) * K + (lz + grid_key<P, 0>(fz, &t))) * K + lx + grid_key<P, 0>(fx, &t);
+            atomicAdd(&S.hist[0][k1], 1);
+            int k2 = 0;
+            if (interlace) {
+              k2 = ((ly + grid_key<P, 1>(fy, &t)) * K + (lz + grid_key<P, 1>(fz, &t))) * K + lx + grid_key<P, 1>(fx, &t);
+              atomicAdd(&S.hist[1][k2], 1);
+            }
+            S.sp[i].x = k1 | (k2 << 16);
+          } else {
+            raise_err(PK_DERR_CELLRANGE);
+            S.sp[i].x = -1;
           }
-          S.sp[i].x = k1 | (k2 << 16);
-        } else {
-          raise_err(PK_DERR_CELLRANGE);
-          S.sp[i].x = -1;
         }
       }
       __syncthreads();
@@ -742,12 +765,23 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         }
       }
       __syncthreads();
-      // particle indices into key order; hist[key] advances to the bucket's end
-      for (int i = tid; i < m; i += THREADS) {
-        const int keys = S.sp[i].x;
-        if (keys < 0) continue;
-        S.perm[0][atomicAdd(&S.hist[0][keys & 0xffff], 1)] = (unsigned short)i;
-        if (interlace) S.perm[1][atomicAdd(&S.hist[1][keys >> 16], 1)] = (unsigned short)i;
+      // particle indices into key order; hist[key] advances to the bucket's end. Four records per
+      // thread and pass, so that eight atomics are in flight before their slots are written.
+      for (int i0 = tid; i0 < m; i0 += 4 * THREADS) {
+        int keys[4], at0[4], at1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) keys[u] = i0 + u * THREADS < m ? S.sp[i0 + u * THREADS].x : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          at0[u] = keys[u] >= 0 ? atomicAdd(&S.hist[0][keys[u] & 0xffff], 1) : 0;
+          at1[u] = keys[u] >= 0 && interlace ? atomicAdd(&S.hist[1][keys[u] >> 16], 1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (keys[u] < 0) continue;
+          S.perm[0][at0[u]] = (unsigned short)(i0 + u * THREADS);
+          if (interlace) S.perm[1][at1[u]] = (unsigned short)(i0 + u * THREADS);
+        }
       }
       __syncthreads();
       const int nitems = S.nitems;
