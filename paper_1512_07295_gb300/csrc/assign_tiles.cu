@@ -285,38 +285,42 @@ __device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned pari
 }
 
 // Adds a tile's node regions (origin: node (cx0-1, cy0-1, cz0-1); grid gi at reg + gi RVOL),
-// converted back from fixed point, to the grids. A thread owns one of 8 slots along z for its whole
-// share of the rows: slot 0 is node 0 of a row, slots 1..5 the node pairs (1,2)..(9,10), whose global
-// z index is even so each pair is one 8-byte vector reduction, slot 6 node 11, slot 7 idle. The
-// slot's z indices are computed once, outside the row loop.
-__device__ __forceinline__ void flush_region(const int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
+// converted back from fixed point, to the grids, and clears them for the next tile. A thread takes
+// whole z rows of RS = 12 nodes: three 16-byte shared loads and stores, then the nodes into the grid
+// row. The tile's first z index cz0 is a multiple of 8 (even), so away from the periodic seam nodes
+// 1..10 of a row form five pairs at even z, one 8-byte vector reduction each (row bases are 8-byte
+// aligned: ldz even), and nodes 0 and 11 go alone; rows that wrap in z take one node at a time.
+// Zero nodes are skipped.
+__device__ __forceinline__ void flush_region(int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
                                              float inv_scale, float* g1, float* g2, int tid, int nthreads) {
-  const int slot = tid & 7;
-  if (slot == 7) return;
-  const bool pair = slot >= 1 && slot <= 5;
-  const int rz = slot == 0 ? 0 : (slot == 6 ? RS - 1 : 2 * slot - 1);
-  const int z = wrap(cz0 - 1 + rz, ng);
-  const bool vec = pair && z + 1 < ng;  // z even, row bases 8-byte aligned (ldz even)
-  const int z1 = pair ? wrap(z + 1, ng) : 0;
+  static_assert(RS == 12 && (RVOL * 4) % 16 == 0, "rows of 12 nodes, 16-byte aligned");
+  const bool seam = cz0 == 0 || cz0 + RS - 1 > ng;  // some node of a row wraps in z
+  const int z0 = cz0 - 1;
   const int nrows = ngrid * RS * RS;
-  for (int row = tid >> 3; row < nrows; row += nthreads >> 3) {
-    const int gi = row / (RS * RS), rr = row - gi * (RS * RS);
+  for (int row = tid; row < nrows; row += nthreads) {
+    const int gi = row >= RS * RS ? 1 : 0, rr = row - gi * (RS * RS);
     const int rx = rr / RS, ry = rr - rx * RS;
-    const int* src = reg + gi * RVOL + rr * RS + rz;
+    int4* src = reinterpret_cast<int4*>(reg + gi * RVOL + rr * RS);
+    const int4 qa = src[0], qb = src[1], qc = src[2];
+    const int4 zero = make_int4(0, 0, 0, 0);
+    src[0] = zero;
+    src[1] = zero;
+    src[2] = zero;
+    const int iv[RS] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w, qc.x, qc.y, qc.z, qc.w};
     float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
-    const float v0 = float(src[0]) * inv_scale;
-    if (!pair) {
-      if (v0 != 0.0f) atomicAdd(gg + z, v0);
+    if (!seam) {
+      if (iv[0] != 0) atomicAdd(gg + z0, float(iv[0]) * inv_scale);
+#pragma unroll
+      for (int k = 1; k < RS - 1; k += 2)
+        if ((iv[k] | iv[k + 1]) != 0)
+          asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(gg + z0 + k), "f"(float(iv[k]) * inv_scale),
+                       "f"(float(iv[k + 1]) * inv_scale)
+                       : "memory");
+      if (iv[RS - 1] != 0) atomicAdd(gg + z0 + RS - 1, float(iv[RS - 1]) * inv_scale);
     } else {
-      const float v1 = float(src[1]) * inv_scale;
-      if (v0 != 0.0f || v1 != 0.0f) {
-        if (vec) {
-          asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(gg + z), "f"(v0), "f"(v1) : "memory");
-        } else {
-          atomicAdd(gg + z, v0);
-          atomicAdd(gg + z1, v1);
-        }
-      }
+#pragma unroll
+      for (int k = 0; k < RS; ++k)
+        if (iv[k] != 0) atomicAdd(gg + wrap(z0 + k, ng), float(iv[k]) * inv_scale);
     }
   }
 }
@@ -362,13 +366,13 @@ constexpr int SCATTER_THREADS = 256;
 // Pieces of the scatter are staged in two buffers: the next piece is copied while this one is used.
 template <bool W>
 __host__ __device__ constexpr int scatter_chunk() {
-  return W ? 512 : 1024;
+  return 512;
 }
 
 template <bool W>
 struct ScatterSmem {
   int4 sp[2][scatter_chunk<W>()];
-  int reg[2][RVOL];
+  alignas(16) int reg[2][2][RVOL];  // two tiles' regions in turn: one is flushed while the next is filled
   float red[SCATTER_THREADS / 32];
   unsigned long long mbar[2];
   float sw[2][W ? scatter_chunk<W>() : 1];
@@ -404,7 +408,9 @@ __device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int l
 // a3, FP32, direct scatter: a block takes tiles in a grid-stride sequence and their pieces in
 // order, the copy of the next piece overlapping the use of the current one; particles are spread over
 // the lanes of a warp q = ceil(m / 32) records apart (different cells, so a warp's atomics seldom meet
-// on one node); the fixed-point regions are added to the grids by flush_region.
+// on one node). Tiles use two regions in turn: a finished tile's region is added to the grids (and
+// cleared) by flush_region in the same phase as the scatter of the next piece, so one block barrier
+// per piece separates all uses of the staging buffers and regions.
 template <int P, bool W>
 __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
@@ -427,6 +433,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar[tid]));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   }
+  for (int i = tid; i < 2 * 2 * RVOL; i += THREADS) (&S.reg[0][0][0])[i] = 0;
   __syncthreads();
   // the block's pieces: (tile, first record c0, tile's records [beg, end))
   struct Piece {
@@ -450,39 +457,52 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
   cur.c0 = -CH;
   if (!advance(cur)) return;
   if (tid == 0) bulk_load(S.sp[0], p + cur.c0, unsigned(min(int64_t(CH), cur.end - cur.c0)) * 16u, &S.mbar[0]);
+  if (W)
+    for (int i = tid; i < int(min(int64_t(CH), cur.end - cur.c0)); i += THREADS) S.sw[0][i] = w[cur.c0 + i];
   Piece nxt = cur;
   bool has_next = advance(nxt);
   unsigned parity = 0u;  // bit b: the phase buffer b waits for next
   int buf = 0;
+  int rb = 1;  // region of the current tile (switched at each tile's first piece)
   float scale = 1.0f, inv_scale = 1.0f;
   int cx0 = 0, cy0 = 0, cz0 = 0;
+  bool pending = false;  // the previous tile's region (rb ^ 1) is still to be flushed
+  int pcx0 = 0, pcy0 = 0, pcz0 = 0;
+  float pinv = 1.0f;
   while (true) {
     const int m = int(min(int64_t(CH), cur.end - cur.c0));
-    if (cur.c0 == cur.beg) {  // first piece of a tile: clear the region, take the tile's scale
-      const int tz = cur.tile % ntile, ty = (cur.tile / ntile) % ntile, tx = cur.tile / (ntile * ntile);
-      cx0 = tx * T;
-      cy0 = ty * T;
-      cz0 = tz * T;
-      for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
-      tile_scale<P, W>(w, cur.beg, cur.end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
-    }
-    // the other buffer was released by the synchronisation that ended the previous piece
-    if (has_next && tid == 0)
-      bulk_load(S.sp[buf ^ 1], p + nxt.c0, unsigned(min(int64_t(CH), nxt.end - nxt.c0)) * 16u, &S.mbar[buf ^ 1]);
-    if (W)
-      for (int i = tid; i < m; i += THREADS) S.sw[buf][i] = w[cur.c0 + i];
     const bool arrived = bulk_wait(&S.mbar[buf], (parity >> buf) & 1u);
     parity ^= 1u << buf;
     if (__syncthreads_or(!arrived)) {  // a copy did not complete: report, drain what is in flight, stop
       if (tid == 0) {
         raise_err(PK_DERR_TIMEOUT);
         bulk_wait(&S.mbar[buf], ((parity >> buf) & 1u) ^ 1u);
-        if (has_next) bulk_wait(&S.mbar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
       }
       return;
     }
+    // every use of the other buffer and of the flushed region ended before the barrier above
+    if (has_next) {
+      const int mn = int(min(int64_t(CH), nxt.end - nxt.c0));
+      if (tid == 0) bulk_load(S.sp[buf ^ 1], p + nxt.c0, unsigned(mn) * 16u, &S.mbar[buf ^ 1]);
+      if (W)
+        for (int i = tid; i < mn; i += THREADS) S.sw[buf ^ 1][i] = w[nxt.c0 + i];
+    }
+    if (cur.c0 == cur.beg) {  // first piece of a tile: the other region, the tile's origin and scale
+      rb ^= 1;
+      const int tz = cur.tile % ntile, ty = (cur.tile / ntile) % ntile, tx = cur.tile / (ntile * ntile);
+      cx0 = tx * T;
+      cy0 = ty * T;
+      cz0 = tz * T;
+      tile_scale<P, W>(w, cur.beg, cur.end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+    }
+    if (pending) {
+      flush_region(&S.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+      pending = false;
+    }
     const int4* sp = S.sp[buf];
     const float* sw = S.sw[buf];
+    int* reg0 = S.reg[rb][0];
+    int* reg1 = S.reg[rb][1];
     const int q = (m + 31) / 32;
     for (int i = tid; i < 32 * q; i += THREADS) {
       const int j = (i & 31) * q + (i >> 5);
@@ -496,19 +516,23 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
       }
       const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
       const float sc = (W ? sw[j] : 1.0f) * weight_scale<P>() * scale;
-      scatter_particle<P, 0>(S.reg[0], lx, ly, lz, fx, fy, fz, sc);
-      if (interlace) scatter_particle<P, 1>(S.reg[1], lx, ly, lz, fx, fy, fz, sc);
+      scatter_particle<P, 0>(reg0, lx, ly, lz, fx, fy, fz, sc);
+      if (interlace) scatter_particle<P, 1>(reg1, lx, ly, lz, fx, fy, fz, sc);
     }
-    __syncthreads();
-    if (cur.c0 + CH >= cur.end) {  // last piece of the tile
-      flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
-      __syncthreads();
+    if (cur.c0 + CH >= cur.end) {  // last piece of the tile: its region is flushed with the next piece
+      pending = true;
+      pcx0 = cx0;
+      pcy0 = cy0;
+      pcz0 = cz0;
+      pinv = inv_scale;
     }
     if (!has_next) break;
     cur = nxt;
     buf ^= 1;
     has_next = advance(nxt);
   }
+  __syncthreads();
+  if (pending) flush_region(&S.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
 }
 
 // ---- cells (dense tiles) ---------------------------------------------------------------------------
@@ -534,7 +558,7 @@ struct CellSmem {
   int4 sp[cell_chunk<W>()];
   unsigned short perm[2][cell_chunk<W>()];
   int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
-  int reg[2][RVOL];
+  alignas(16) int reg[2][RVOL];
   unsigned short order[2 * NKEY];  // non-empty key cells (grid in bit 15), largest bucket first
   int cbin[CNT_BINS];
   int nitems;
@@ -630,6 +654,7 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   }
+  for (int i = tid; i < 2 * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;  // flush_region clears it after each tile
   __syncthreads();
   unsigned parity = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -637,7 +662,6 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     if (beg >= end) continue;
     const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
-    for (int i = tid; i < ngrid * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;
     float scale, inv_scale;
     tile_scale<P, W>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
     const float wscale = scale * weight_scale<P>();
