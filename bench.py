@@ -59,6 +59,7 @@ def parse():
                     help="time one secondary row on its own workload and print it (no P(k) step)")
     ap.add_argument("--ds-nside", type=int, default=128, help="--only-row direct: particles per side")
     ap.add_argument("--ds-ng", type=int, default=128, help="--only-row direct: grid size")
+    ap.add_argument("--batch-cats", type=int, default=512, help="--only-row batch: catalogues in the batch")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -254,15 +255,16 @@ def row_adjoint(dev):
     return rows["adjoint"]
 
 
-def row_batch(dev, profile_range=False):
+def row_batch(dev, profile_range=False, ncats=512):
     import torch
 
     from paper_1512_07295_gb300 import api, catalogs
 
     rows = {}
     # a9: 512 mock catalogues, N_P log-uniform in [1e5, 2e6], L = 1000, N_G = 128, PCS + interlacing, FP32
+    # (fewer with --batch-cats, for profiling captures)
     cfg = api.Config(ng=128, box=1000.0, prec="fp32")
-    sizes = catalogs.batch_sizes(512, 1e5, 2e6, seed=4)
+    sizes = catalogs.batch_sizes(ncats, 1e5, 2e6, seed=4)
     gen = torch.Generator(device=dev)
     gen.manual_seed(4)
     parts = []
@@ -281,8 +283,8 @@ def row_batch(dev, profile_range=False):
     # group size chosen by the library's autotuner, then the call timed eagerly and as a CUDA graph replay
     batch, tune_ms = api.autotune_batch(cells, offs, cfg, candidates=(32, 64, 128), reps=2)
     wsc = api.batch_workspace(cfg, batch, api.max_group_particles(offs, batch), dev)
-    pkb = torch.empty((512, cfg.nb), dtype=torch.float64, device=dev)
-    nmb = torch.empty((512, cfg.nb), dtype=torch.int64, device=dev)
+    pkb = torch.empty((ncats, cfg.nb), dtype=torch.float64, device=dev)
+    nmb = torch.empty((ncats, cfg.nb), dtype=torch.int64, device=dev)
     ms = _time_cuda(lambda: api.batch_power(cells, offs, cfg, batch=batch, ws=wsc, out=(pkb, nmb)), 3)
     if profile_range:  # one call bracketed for ncu --profile-from-start off
         torch.cuda.synchronize()
@@ -298,9 +300,9 @@ def row_batch(dev, profile_range=False):
             api.batch_power(cells, offs, cfg, batch=batch, ws=wsc, out=(pkb, nmb))
     torch.cuda.current_stream(dev).wait_stream(cap)
     ms_graph = _time_cuda(graph.replay, 3)
-    rows["batch"] = {"workload": f"512 catalogues, {int(sizes.sum())} particles, N_P log-uniform in [1e5, 2e6], L=1000, "
+    rows["batch"] = {"workload": f"{ncats} catalogues, {int(sizes.sum())} particles, N_P log-uniform in [1e5, 2e6], L=1000, "
                                  f"N_G=128, PCS+interlacing, FP32, groups of {batch} (autotuned)",
-                     "ms_per_call": ms, "pk_per_s": 512 / (ms * 1e-3), "particles_per_s": float(sizes.sum()) / (ms * 1e-3),
+                     "ms_per_call": ms, "pk_per_s": ncats / (ms * 1e-3), "particles_per_s": float(sizes.sum()) / (ms * 1e-3),
                      "graph_ms_per_call": ms_graph, "autotune_ms": {str(k): v for k, v in tune_ms.items()}}
     del graph
     del wsc, cells
@@ -458,7 +460,7 @@ def main():
     dev = torch.device("cuda", local)
     lib = ffi.lib()
     if a.only_row:
-        row = {"adjoint": lambda: row_adjoint(dev), "batch": lambda: row_batch(dev, a.profile_range),
+        row = {"adjoint": lambda: row_adjoint(dev), "batch": lambda: row_batch(dev, a.profile_range, a.batch_cats),
                "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng),
                "multigrid": lambda: row_multigrid(dev)}[a.only_row]()
         if rank == 0:
@@ -597,6 +599,20 @@ def main():
         def e2e_step():
             api.power_host(host64, cfg, ws=wsp, out=host_out, device=dev)
 
+        # context for e2e: the CPU-GPU link on a 2 GiB pinned copy, just before it. The link's throughput
+        # varies from run to run, so this is a sample, not a bound on e2e.
+        probe = torch.empty(1 << 28, dtype=torch.float64, device=dev)
+        probe_src = host64.view(-1)[: probe.numel()]
+        probe.copy_(probe_src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(2):
+            probe.copy_(probe_src, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        link_gbs = 2 * probe.numel() * 8 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del probe, probe_src
+
         e2e_step()
         torch.cuda.synchronize()
         ke = 3
@@ -608,6 +624,7 @@ def main():
         ms_e2e = e0.elapsed_time(e1) / ke
         result["e2e"] = {"value": n / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": 24 * n,
                          "d2h_bytes_per_step": 24 * cfg.nb, "ms_per_step": ms_e2e,
+                         "link_h2d_gbs_2gib_sample": link_gbs,
                          "path": "pk_power_host: pinned host FP64 xyz copied over the CPU-GPU link in 16 pieces by the "
                                  "copy engine, each prepared, binned and assigned while the next is in flight -> FFT -> "
                                  "estimate -> D2H of P(k), kmean, counts"}
