@@ -721,51 +721,50 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         }
       }
       __syncthreads();
-      // the non-empty key cells of both grids counted by bucket size (bin 0: the largest)
-      for (int i = tid; i < ngrid * NKEY; i += THREADS) {
-        const int cnt = (&S.hist[0][0])[i + i / NKEY];  // grid i / NKEY, key i % NKEY
-        if (cnt > 0) atomicAdd(&S.cbin[CNT_BINS - 1 - min(cnt, CNT_BINS - 1)], 1);
+      // Counts of both histograms, read once: the non-empty key cells are counted by bucket size
+      // (bin 0: the largest) and the warps scan the counts.
+      int v0[SCAN_PER_THREAD], v1[SCAN_PER_THREAD];
+      int x0, x1, s0v = 0, s1v = 0;
+#pragma unroll
+      for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        const int idx = tid * SCAN_PER_THREAD + k;
+        v0[k] = idx <= NKEY ? S.hist[0][idx] : 0;
+        v1[k] = idx <= NKEY ? S.hist[1][idx] : 0;
+        if (v0[k] > 0) atomicAdd(&S.cbin[CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1);  // entry NKEY is 0
+        if (v1[k] > 0) atomicAdd(&S.cbin[CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1);
+        s0v += v0[k];
+        s1v += v1[k];
+      }
+      x0 = s0v;
+      x1 = s1v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+        if (lane >= o) {
+          x0 += y0;
+          x1 += y1;
+        }
+      }
+      if (lane == 31) {
+        S.scan[0][warp] = x0;
+        S.scan[1][warp] = x1;
       }
       __syncthreads();
-      // block-wide exclusive scan of both histograms; warp 0 also scans the count bins
-      {
-        int v0[SCAN_PER_THREAD], v1[SCAN_PER_THREAD];
-        int s0v = 0, s1v = 0;
-#pragma unroll
-        for (int k = 0; k < SCAN_PER_THREAD; ++k) {
-          const int idx = tid * SCAN_PER_THREAD + k;
-          v0[k] = idx <= NKEY ? S.hist[0][idx] : 0;
-          v1[k] = idx <= NKEY ? S.hist[1][idx] : 0;
-          s0v += v0[k];
-          s1v += v1[k];
-        }
-        int x0 = s0v, x1 = s1v;
+      // exclusive offsets of both histograms; warp 0 scans the count bins (64 bins, two per lane)
+      if (warp == 0) {
+        const int a0 = S.cbin[2 * lane], a1 = S.cbin[2 * lane + 1];
+        int x = a0 + a1;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const int y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
-          if (lane >= o) {
-            x0 += y0;
-            x1 += y1;
-          }
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
         }
-        if (lane == 31) {
-          S.scan[0][warp] = x0;
-          S.scan[1][warp] = x1;
-        }
-        if (warp == 0) {  // 64 count bins, two per lane
-          const int a0 = S.cbin[2 * lane], a1 = S.cbin[2 * lane + 1];
-          int x = a0 + a1;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-          }
-          const int ex = x - a0 - a1;
-          S.cbin[2 * lane] = ex;
-          S.cbin[2 * lane + 1] = ex + a0;
-          if (lane == 31) S.nitems = x;
-        }
-        __syncthreads();
+        const int ex = x - a0 - a1;
+        S.cbin[2 * lane] = ex;
+        S.cbin[2 * lane + 1] = ex + a0;
+        if (lane == 31) S.nitems = x;
+      }
+      {
         int e0 = x0 - s0v, e1 = x1 - s1v;
         for (int q = 0; q < warp; ++q) {
           e0 += S.scan[0][q];
@@ -775,12 +774,6 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         for (int k = 0; k < SCAN_PER_THREAD; ++k) {
           const int idx = tid * SCAN_PER_THREAD + k;
           if (idx <= NKEY) {
-            // the key's place in the count order, taken while its count is at hand
-            if (idx < NKEY) {
-              if (v0[k] > 0) S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1)] = (unsigned short)idx;
-              if (v1[k] > 0)
-                S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1)] = (unsigned short)(idx | 0x8000);
-            }
             S.hist[0][idx] = e0;
             S.hist[1][idx] = e1;
           }
@@ -789,8 +782,16 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         }
       }
       __syncthreads();
-      // particle indices into key order; hist[key] advances to the bucket's end. Four records per
-      // thread and pass, so that eight atomics are in flight before their slots are written.
+      // each non-empty key cell takes its place in the count order (its count still at hand), and
+      // the particle indices go into key order: hist[key] advances to the bucket's end. Four records
+      // per thread and pass, so that eight atomics are in flight before their slots are written.
+#pragma unroll
+      for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        const int idx = tid * SCAN_PER_THREAD + k;
+        if (v0[k] > 0) S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1)] = (unsigned short)idx;
+        if (v1[k] > 0)
+          S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1)] = (unsigned short)(idx | 0x8000);
+      }
       for (int i0 = tid; i0 < m; i0 += 4 * THREADS) {
         int keys[4], at0[4], at1[4];
 #pragma unroll
