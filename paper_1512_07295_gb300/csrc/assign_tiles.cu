@@ -357,6 +357,25 @@ __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t 
   *inv_scale = ldexpf(1.0f, ex - 30);
 }
 
+// The first tile t + k stride (k >= 0) below ntiles whose population end - beg lies in [lo, hi], else
+// ntiles. Warp-parallel: 32 candidates per round of loads and a ballot; every lane of a full warp
+// calls it with the same arguments and gets the same answer, so all warps of a block agree.
+__device__ __forceinline__ int next_tile(const int64_t* toff, int64_t n, int t, int stride, int ntiles, int64_t lo,
+                                         int64_t hi) {
+  const int lane = threadIdx.x & 31;
+  for (; t < ntiles; t += 32 * stride) {
+    const int c = t + lane * stride;
+    bool ok = false;
+    if (c < ntiles) {
+      const int64_t cnt = min(toff[c + 1], n) - max(toff[c], int64_t(0));
+      ok = cnt >= lo && cnt <= hi;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (m) return t + (__ffs(m) - 1) * stride;
+  }
+  return ntiles;
+}
+
 // ---- direct scatter (sparse tiles) ------------------------------------------------------------------
 // Sorting a piece by key cell costs a fixed amount per piece (histograms, scans, the count order);
 // on sparse tiles that fixed cost dominates. There, each thread adds its particles' p^3 weights per
@@ -415,7 +434,7 @@ template <int P, bool W>
 __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
                      int64_t n, int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                     int64_t cat_stride) {
+                     int64_t cat_stride, int max_count) {
   using namespace tiles;
   constexpr int CH = scatter_chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
   {
@@ -440,15 +459,16 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     int tile;
     int64_t beg, end, c0;
   };
-  auto advance = [&](Piece& c) -> bool {  // next piece of this tile, else the first of the next non-empty tile
+  // next piece of this tile, else the first of the block's next tile of 1 .. max_count particles
+  // (called by every thread alike)
+  auto advance = [&](Piece& c) -> bool {
     c.c0 += CH;
-    while (c.c0 >= c.end) {
-      c.tile += gridDim.x;
-      if (c.tile >= ntiles) return false;
-      c.beg = max(toff[c.tile], int64_t(0));
-      c.end = min(toff[c.tile + 1], n);
-      c.c0 = c.beg;
-    }
+    if (c.c0 < c.end) return true;
+    c.tile = next_tile(toff, n, c.tile + int(gridDim.x), int(gridDim.x), ntiles, 1, max_count);
+    if (c.tile >= ntiles) return false;
+    c.beg = max(toff[c.tile], int64_t(0));
+    c.end = min(toff[c.tile + 1], n);
+    c.c0 = c.beg;
     return true;
   };
   Piece cur;
@@ -634,7 +654,7 @@ template <int P, bool W>
 __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     k_assign_cells(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
                    int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                   int64_t cat_stride) {
+                   int64_t cat_stride, int min_count) {
   using namespace tiles;
   constexpr int CH = cell_chunk<W>(), THREADS = CELL_THREADS, NWARP = THREADS / 32;
   constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
@@ -657,9 +677,11 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
   for (int i = tid; i < 2 * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;  // flush_region clears it after each tile
   __syncthreads();
   unsigned parity = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  constexpr int64_t kAny = INT64_MAX;
+  // the block's tiles of at least min_count particles (the scatter takes the others)
+  for (int tile = next_tile(toff, n, blockIdx.x, gridDim.x, ntiles, min_count, kAny), nt = 0; tile < ntiles; tile = nt) {
+    nt = next_tile(toff, n, tile + int(gridDim.x), int(gridDim.x), ntiles, min_count, kAny);
     const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
-    if (beg >= end) continue;
     const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
     float scale, inv_scale;
@@ -669,11 +691,11 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
       const int m = int(min(int64_t(CH), end - c0));
       if (tid == 0) {
         bulk_load(S.sp, p + c0, unsigned(m) * 16u, &S.mbar);
-        // the block's next piece (of this tile, else of one of its next 8 tiles) moves to L2 meanwhile
+        // the block's next piece (of this tile, else of its next tile) moves to L2 meanwhile
         int64_t nb = c0 + CH, ne = end;
-        for (int t = tile + gridDim.x, k = 0; nb >= ne && t < ntiles && k < 8; t += gridDim.x, ++k) {
-          nb = max(toff[t], int64_t(0));
-          ne = min(toff[t + 1], n);
+        if (nb >= ne && nt < ntiles) {
+          nb = max(toff[nt], int64_t(0));
+          ne = min(toff[nt + 1], n);
         }
         if (nb < ne) bulk_prefetch_l2(p + nb, unsigned(min(int64_t(CH), ne - nb)) * 16u);
       }
@@ -844,16 +866,19 @@ static cudaError_t kernel_setup(const void* kernel, int threads, size_t smem, in
   return cudaSuccess;
 }
 
-// Mean particles per tile below which the direct scatter replaces the key-cell kernel, per order.
-// Measured on one GB300 over uniform catalogues of 256 .. 8192 particles per tile (8^3 cells, both
-// grids): PCS crosses near 750, TSC near 1400, CIC near 7000; for NGP (one node per particle) the
-// scatter stays ahead throughout.
-static int64_t scatter_max_mean(int order) {
+// Tile population from which the key-cell kernel takes a tile instead of the scatter, per order. Speed
+// alone (uniform catalogues of 256 .. 8192 particles per tile, both grids, one GB300) puts the crossover
+// near 750 for PCS, 1400 for TSC and 7000 for CIC. Accuracy caps it lower: the scatter rounds every
+// particle's contribution to a node, so its error grows as the square root of the tile's population
+// (CIC at 5500 per tile: 4.6e-6 of the largest node; PCS in a 3250-particle tile: 2.1e-6), while the
+// key-cell kernel rounds once per key cell. NGP stays on the scatter: its unit contributions at a
+// power-of-two scale are exact.
+static int cells_min_count(int order) {
   switch (order) {
     case 4: return 768;
-    case 3: return 1408;
-    case 2: return 6144;
-    default: return INT64_MAX / (int64_t(1) << 40);  // the product with the tile count cannot overflow
+    case 3: return 1024;
+    case 2: return 512;
+    default: return INT_MAX;
   }
 }
 
@@ -869,14 +894,9 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
   if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
   k_assign_scatter<P, W><<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
-                                                                     cat_stride);
+                                                                     cat_stride, cells_min_count(P) - 1);
   count_launch();
   return cudaGetLastError();
-}
-
-bool assign_uses_scatter(int64_t n, int ng, int ncat, int order) {
-  const int64_t nt = tiles_per_axis(ng);
-  return n < scatter_max_mean(order) * nt * nt * nt * ncat;
 }
 
 template <int P, bool W>
@@ -891,22 +911,23 @@ static cudaError_t launch_cells_pw(const pk_cellpos* p, const float* w, const in
   if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
   k_assign_cells<P, W><<<blocks, tiles::CELL_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
-                                                                 cat_stride);
+                                                                 cat_stride, cells_min_count(P));
   count_launch();
   return cudaGetLastError();
 }
 
-// Sparse tiles: the scatter; dense ones: the key cells (NGP: always the scatter).
+// Tiles of fewer than cells_min_count(P) particles: the scatter; the others: the key cells (NGP: all
+// on the scatter). Each kernel skips the other's tiles, so both launch whatever the populations.
 template <int P>
 static cudaError_t launch_tiles_p(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
                                   float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
-  if (P == 1 || assign_uses_scatter(n, ng, ncat, P))
-    return w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
-             : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+  cudaError_t e = w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
+                    : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+  if (e != cudaSuccess) return e;
   if constexpr (P > 1)
-    return w ? launch_cells_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
-             : launch_cells_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-  return cudaErrorInvalidValue;
+    e = w ? launch_cells_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
+          : launch_cells_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+  return e;
 }
 
 cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,

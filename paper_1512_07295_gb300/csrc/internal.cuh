@@ -68,11 +68,9 @@ cudaError_t launch_assign_direct_f32(int order, const void* pos, int fmt, const 
 cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
 // FP32 tile assignment (assign_tiles.cu: the scatter on sparse tiles, the key-cell kernel on dense
-// ones), same layout and binned input as the tiled kernel, any particle order inside a tile; ncat > 1:
-// catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids g + c * cat_stride.
-// Whether launch_assign_tiles_f32 takes the direct scatter for n particles of order `order` over ncat
-// catalogues of side ng.
-bool assign_uses_scatter(int64_t n, int ng, int ncat, int order);
+// ones, chosen per tile), same layout and binned input as the tiled kernel, any particle order inside
+// a tile; ncat > 1: catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids
+// g + c * cat_stride.
 cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
                                     int64_t cat_stride = 0);
