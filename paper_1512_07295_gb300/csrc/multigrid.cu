@@ -80,7 +80,9 @@ __global__ void k_shift_cells(const pk_cellpos* __restrict__ in, int64_t n, int 
   }
 }
 
-// Per-slot tables: 1/W_1d(n) and e^{i pi n/N} (n the signed index of the slot), FP64.
+// Per-slot tables (n the signed index of the slot), FP64: 1/W_1d(n), then e^{i pi n h/N} for h = 1 and
+// h = 2 (cosine row, sine row each).
+constexpr int kMultiTabRows = 5;
 __global__ void k_multi_tables(double* __restrict__ tab, int ng, int order) {
   for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < ng; i += blockDim.x * gridDim.x) {
     const int n = signed_mode(i, ng);
@@ -88,11 +90,14 @@ __global__ void k_multi_tables(double* __restrict__ tab, int ng, int order) {
     const double s = n == 0 ? 1.0 : sinpi(x) / (3.14159265358979323846 * x);
     double w = 1.0;
     for (int k = 0; k < order; ++k) w *= s;
-    double sn, cs;
+    double sn, cs, sn2, cs2;
     sincospi(x, &sn, &cs);
+    sincospi(2.0 * x, &sn2, &cs2);
     tab[i] = 1.0 / w;
     tab[ng + i] = cs;
     tab[2 * ng + i] = sn;
+    tab[3 * ng + i] = cs2;
+    tab[4 * ng + i] = sn2;
   }
 }
 
@@ -108,79 +113,134 @@ struct MultiArgs {
   void* delta_out;
 };
 
-// e^{i pi n h / N} for h in {0, 1, 2} from the slot's table entry e^{i pi n/N}.
-__device__ __forceinline__ double2 shift_phase(double c, double s, int h) {
-  if (h == 0) return make_double2(1.0, 0.0);
-  if (h == 1) return make_double2(c, s);
-  return make_double2(c * c - s * s, 2.0 * c * s);
+template <typename R>
+struct Cx {
+  R x, y;
+};
+template <typename R>
+__device__ __forceinline__ Cx<R> cmr(Cx<R> a, Cx<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-__device__ __forceinline__ double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
+// Shifted-grid combine of J transformed grids and k-shell sums (eq:intdelta generalised to the shift
+// set h_j, Sec. 3.1). Per stored mode n (and its partner -n on the half-complex layout):
+//   delta(n) = sum_j e^{i pi n.h_j / N} G_j(n) / (J sum(w) W(n)),
+// the per-axis phases e^{i pi n h/N} (h = 0, 1, 2) read from tables; the arithmetic runs in the grids'
+// precision (FP32 grids: FP32 combine), the shell sums in FP64 (|k| sums from an FP64 square root).
+// Consecutive lanes hold consecutive i_z, so a warp's modes fall in few shells: runs of equal shell
+// are summed with a segmented warp scan and one lane per run adds them to shared memory.
 template <typename V>
 __global__ void __launch_bounds__(256) k_estimate_multi(const V* __restrict__ G, const double* __restrict__ tab_g, MultiArgs a) {
+  using R = decltype(V{}.x);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ng = a.ng;
-  double* tab = reinterpret_cast<double*>(smem_raw);  // [3][ng]
-  double* s_sum = tab + 3 * ng;
+  double* s_sum = reinterpret_cast<double*>(smem_raw);
   double* s_k = s_sum + a.nbins;
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_k + a.nbins);
-  for (int i = threadIdx.x; i < 3 * ng; i += blockDim.x) tab[i] = tab_g[i];
+  R* tab = reinterpret_cast<R*>(s_cnt + a.nbins);  // [kMultiTabRows][ng], the grids' precision
+  for (int i = threadIdx.x; i < kMultiTabRows * ng; i += blockDim.x) tab[i] = R(tab_g[i]);
   for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
     s_sum[i] = 0.0;
     s_k[i] = 0.0;
     s_cnt[i] = 0ull;
   }
   __syncthreads();
-  const double norm = 1.0 / (double(a.J) * a.wsums[0]);
+  const R norm = R(1.0 / (double(a.J) * a.wsums[0]));
+  const R vol = R(a.vol);
   const int H = ng / 2 + 1;
   const int64_t count = int64_t(ng) * ng * H;
-  for (int64_t m = gtid(); m < count; m += gstride()) {
-    const int iz = int(m % H);
-    const int64_t xy = m / H;
-    const int iy = int(xy % ng), ix = int(xy / ng);
-    const int slot[3] = {ix, iy, iz};
-    int pslot[3];  // slots of the partner -n
-    for (int d = 0; d < 3; ++d) pslot[d] = slot[d] == 0 ? 0 : ng - slot[d];
-    const double iw = tab[ix] * tab[iy] * tab[iz] * norm;
-    double2 dn = make_double2(0.0, 0.0), dp = make_double2(0.0, 0.0);
-    for (int j = 0; j < a.J; ++j) {
-      const V g = G[j * a.grid_stride + m];
-      const double2 gv = make_double2(double(g.x), double(g.y));
-      double2 ph = make_double2(1.0, 0.0), pp = make_double2(1.0, 0.0);
-      for (int d = 0; d < 3; ++d) {
-        ph = cm(ph, shift_phase(tab[ng + slot[d]], tab[2 * ng + slot[d]], a.h[j][d]));
-        pp = cm(pp, shift_phase(tab[ng + pslot[d]], tab[2 * ng + pslot[d]], a.h[j][d]));
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  // whole warps step together (the shell sums are warp-collective)
+  for (int64_t m0 = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); m0 < count; m0 += stride) {
+    const int64_t m = m0 + lane;
+    int b = -1, mult = 0;
+    R pv = R(0);
+    double kv = 0.0;
+    if (m < count) {
+      const int iz = int(m % H);
+      const int64_t xy = m / H;
+      const int iy = int(xy % ng), ix = int(xy / ng);
+      const int slot[3] = {ix, iy, iz};
+      int pslot[3];  // slots of the partner -n
+#pragma unroll
+      for (int d = 0; d < 3; ++d) pslot[d] = slot[d] == 0 ? 0 : ng - slot[d];
+      const R iw = tab[ix] * tab[iy] * tab[iz] * norm;
+      // per-axis phase factors for h = 1, 2 at n and at -n
+      Cx<R> e[3][2], q[3][2];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          e[d][h] = {tab[(1 + 2 * h) * ng + slot[d]], tab[(2 + 2 * h) * ng + slot[d]]};
+          q[d][h] = {tab[(1 + 2 * h) * ng + pslot[d]], tab[(2 + 2 * h) * ng + pslot[d]]};
+        }
+      Cx<R> dn = {R(0), R(0)}, dp = {R(0), R(0)};
+      for (int j = 0; j < a.J; ++j) {
+        const V g = G[j * a.grid_stride + m];
+        Cx<R> ph = {R(1), R(0)}, pp = {R(1), R(0)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int h = a.h[j][d];  // uniform across the block
+          if (h != 0) {
+            ph = cmr(ph, h == 1 ? e[d][0] : e[d][1]);
+            pp = cmr(pp, h == 1 ? q[d][0] : q[d][1]);
+          }
+        }
+        const Cx<R> t = cmr(Cx<R>{g.x, g.y}, ph);
+        const Cx<R> u = cmr(Cx<R>{g.x, -g.y}, pp);  // G(-n) = conj G(n)
+        dn.x += t.x;
+        dn.y += t.y;
+        dp.x += u.x;
+        dp.y += u.y;
       }
-      const double2 t = cm(gv, ph);
-      const double2 u = cm(make_double2(gv.x, -gv.y), pp);  // G(-n) = conj G(n)
-      dn.x += t.x;
-      dn.y += t.y;
-      dp.x += u.x;
-      dp.y += u.y;
-    }
-    dn.x *= iw;
-    dn.y *= iw;
-    dp.x *= iw;
-    dp.y *= iw;
-    if (m == 0) dn = make_double2(0.0, 0.0);
-    if (a.delta_out) {
-      V o;
-      o.x = dn.x;
-      o.y = dn.y;
-      static_cast<V*>(a.delta_out)[m] = o;
+      dn.x *= iw;
+      dn.y *= iw;
+      dp.x *= iw;
+      dp.y *= iw;
+      if (m == 0) dn = {R(0), R(0)};
+      if (a.delta_out) {
+        V o;
+        o.x = dn.x;
+        o.y = dn.y;
+        static_cast<V*>(a.delta_out)[m] = o;
+      }
+      if (a.nbins > 0) {
+        const long long nx = signed_mode(ix, ng), ny = signed_mode(iy, ng), nz = signed_mode(iz, ng);
+        const long long n2 = nx * nx + ny * ny + nz * nz;
+        b = bin_of(4 * n2, a.lo2, a.w2, a.nbins);
+        if (b >= 0) {
+          const bool partner = iz != 0 && iz != ng / 2;
+          pv = vol * (dn.x * dn.x + dn.y * dn.y);
+          if (partner) pv += vol * (dp.x * dp.x + dp.y * dp.y);
+          mult = partner ? 2 : 1;
+          kv = double(mult) * sqrt(double(n2));
+        }
+      }
     }
     if (a.nbins == 0) continue;
-    const long long nx = signed_mode(ix, ng), ny = signed_mode(iy, ng), nz = signed_mode(iz, ng);
-    const long long n2 = nx * nx + ny * ny + nz * nz;
-    const int b = bin_of(4 * n2, a.lo2, a.w2, a.nbins);
-    if (b < 0) continue;
-    const bool partner = iz != 0 && iz != ng / 2;
-    double p = a.vol * (dn.x * dn.x + dn.y * dn.y);
-    if (partner) p += a.vol * (dp.x * dp.x + dp.y * dp.y);
-    const int mult = partner ? 2 : 1;
-    atomicAdd(&s_sum[b], p);
-    atomicAdd(&s_k[b], double(mult) * sqrt(double(n2)));
-    atomicAdd(&s_cnt[b], (unsigned long long)mult);
+    // segmented inclusive scan over runs of equal b; the last lane of each run adds the run's sums
+    const int bprev = __shfl_up_sync(0xffffffffu, b, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || bprev != b);
+    const int start = 31 - __clz(heads & ((2u << lane) - 1u));
+    const int bnext = __shfl_down_sync(0xffffffffu, b, 1);
+    const bool end = lane == 31 || bnext != b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const R tv = __shfl_up_sync(0xffffffffu, pv, o);
+      const double tk = __shfl_up_sync(0xffffffffu, kv, o);
+      const int tc = __shfl_up_sync(0xffffffffu, mult, o);
+      if (lane - o >= start) {
+        pv += tv;
+        kv += tk;
+        mult += tc;
+      }
+    }
+    if (end && b >= 0) {
+      atomicAdd(&s_sum[b], double(pv));
+      atomicAdd(&s_k[b], kv);
+      atomicAdd(&s_cnt[b], (unsigned long long)mult);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
@@ -224,7 +284,7 @@ pk_status carve_multi(const pk_config* c, int J, int64_t n, Carver& cv, MultiLay
     L->offsets = cv.take<int64_t>(size_t(int64_t(nt) * nt * nt + 1));
   }
   L->wsums = cv.take<double>(3);
-  L->tab = cv.take<double>(size_t(3) * c->ng);
+  L->tab = cv.take<double>(size_t(kMultiTabRows) * c->ng);
   L->bin_sum = cv.take<double>(c->nbins);
   L->bin_k = cv.take<double>(c->nbins);
   L->bin_cnt = cv.take<unsigned long long>(c->nbins);
@@ -342,7 +402,8 @@ pk_status pk_power_multigrid(const pk_config* cfg, int32_t ngrids, const void* p
   a.delta_out = delta_k_dev;
   const int64_t hc = half_count(ng);
   const int eblocks = int(std::min<int64_t>(int64_t(num_sms()) * 4, (hc + 255) / 256));
-  const size_t smem = sizeof(double) * 3 * size_t(ng) + nb * (2 * sizeof(double) + sizeof(unsigned long long));
+  // bins first (8-byte entries), then the tables in the grids' precision
+  const size_t smem = nb * (2 * sizeof(double) + sizeof(unsigned long long)) + (dbl ? 8 : 4) * size_t(kMultiTabRows) * ng;
   if (dbl) {
     if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_estimate_multi<double2>), smem)) != cudaSuccess)
       return cuda_fail(e, "estimate smem");
