@@ -68,6 +68,10 @@ __global__ void k_shift_cells(const pk_cellpos* __restrict__ in, int64_t n, int 
       if (!h[a]) continue;
       float g;
       c[a] += half_shift(f[a], &g);
+      if (g >= 1.0f) {  // f = 0.5 - 2^-25: f + 1/2 rounds to 1 in FP32, which is the next cell's 0
+        g = 0.0f;
+        c[a] += 1;
+      }
       f[a] = g;
       if (c[a] >= ng) c[a] -= ng;
     }
@@ -352,25 +356,33 @@ pk_status pk_power_multigrid(const pk_config* cfg, int32_t ngrids, const void* p
   sub.interlace = sh.pairs ? 1 : 0;
   const int blocks = int(std::min<int64_t>(int64_t(num_sms()) * 8, (n + 255) / 256));
   const double half = 0.5 * cfg->box / ng;
+  // FP32 from FP64 positions: the first (unshifted) base prepares the packed records once; later bases
+  // shift those records instead of preparing shifted FP64 positions again
+  const bool reuse_prepared = cfg->prec == PK_FP32 && pos_format == PK_POS_F64_XYZ;
   for (int b = 0; b < sh.bases; ++b) {
     const int* hb = sh.h[sh.pairs ? 2 * b : b];
     const void* pos = pos_dev;
+    int fmt = pos_format;
     if (hb[0] | hb[1] | hb[2]) {
-      if (pos_format == PK_POS_F64_XYZ)
+      if (reuse_prepared) {  // base 0 is unshifted, so L.b.cells holds the prepared records
+        k_shift_cells<<<blocks, 256, 0, s>>>(L.b.cells, n, ng, hb[0], hb[1], hb[2], static_cast<pk_cellpos*>(L.shifted));
+        fmt = PK_POS_CELL_F32OFF;
+      } else if (pos_format == PK_POS_F64_XYZ) {
         k_shift_f64<<<blocks, 256, 0, s>>>(static_cast<const double*>(pos_dev), n, hb[0] * half, hb[1] * half, hb[2] * half,
                                            static_cast<double*>(L.shifted));
-      else
+      } else {
         k_shift_cells<<<blocks, 256, 0, s>>>(static_cast<const pk_cellpos*>(pos_dev), n, ng, hb[0], hb[1], hb[2],
                                              static_cast<pk_cellpos*>(L.shifted));
+      }
       count_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "shift");
       pos = L.shifted;
     }
     void* grids = static_cast<char*>(L.grids) + gbytes * size_t(sh.pairs ? 2 * b : b);
     if (cfg->prec == PK_FP64) {
-      st = run_assign_into(&sub, pos, pos_format, nullptr, w_dev, nullptr, n, L.wsums, grids, ng + 2, s);
+      st = run_assign_into(&sub, pos, fmt, nullptr, w_dev, nullptr, n, L.wsums, grids, ng + 2, s);
     } else {
-      if ((st = run_bin(&sub, pos, pos_format, w_dev, n, L.b, L.sorted, w_dev ? L.wsorted : nullptr, L.offsets, s)) != PK_OK)
+      if ((st = run_bin(&sub, pos, fmt, w_dev, n, L.b, L.sorted, w_dev ? L.wsorted : nullptr, L.offsets, s)) != PK_OK)
         return st;
       st = run_assign_into(&sub, nullptr, PK_POS_CELL_F32OFF, L.sorted, w_dev ? L.wsorted : nullptr, L.offsets, n, L.wsums,
                            grids, ng + 2, s);

@@ -81,3 +81,27 @@ def test_multigrid_rejects_other_grid_counts():
     for bad in (0, 3, 16):
         with pytest.raises(ffi.PkError):
             api.power_multigrid(pos, cfg, bad)
+
+
+@pytest.mark.parametrize("fmt", ["records", "f64"])
+def test_offsets_whose_half_shift_rounds_to_one(fmt):
+    # f = 1/2 - 2^-25 is the one FP32 offset below 1/2 whose f + 1/2 rounds to 1: the shifted record
+    # must move to the next cell (offset 0) rather than be reported invalid and dropped. Packed records
+    # carry it directly; from FP64 positions, x = (c + f) H prepares to the same offset.
+    box, ng, p = 64.0, 16, 4
+    rng = np.random.default_rng(76)
+    u = rng.uniform(0, ng, (3000, 3))
+    f = np.float64(np.float32(0.5) - np.float32(2.0 ** -25))
+    edge = np.floor(rng.uniform(0, ng, (60, 3))) + f  # every axis at the edge offset
+    uu = np.concatenate([u, edge])
+    cells = _ref.pack_cellpos(uu, ng)
+    exact = _ref.cellpos_to_units(cells, ng)
+    assert np.array_equal(exact[-60:], edge)  # the edge offsets survive packing
+    ref_pk, _, ref_cnt, _ = _oracle(exact, ng, p, box, 8)
+    cfg = api.Config(ng=ng, box=box, order=p, prec="fp32")
+    pos = _t(cells) if fmt == "records" else _t(exact * (box / ng))
+    api.device_error()
+    pk, _, cnt = api.power_multigrid(pos, cfg, 8)
+    assert api.device_error() == 0
+    assert np.array_equal(cnt.cpu().numpy(), ref_cnt)
+    assert _ref.rel(pk.cpu().numpy(), ref_pk) <= 1e-5
