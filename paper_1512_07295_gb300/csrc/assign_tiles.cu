@@ -556,12 +556,13 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
 }
 
 // ---- cells (dense tiles) ---------------------------------------------------------------------------
-// Per staged piece of a tile the particles are counting-sorted by key cell on each grid; the non-empty
-// key cells of both grids then form one list ordered by particle count, largest first. Thread t takes
-// item t of each round of 256 items in even rounds and item 255 - t in odd ones, so the 32 lanes of
-// a warp hold cells of nearly equal load and the warps' totals even out. A lane sums its cell's
-// particles into a register window of p^3 node values (the cell's whole stencil) and adds the window
-// to the tile's fixed-point region once. Pieces need no order inside the tile.
+// Per staged piece of a tile the particles are counting-sorted by key cell on each grid; each grid's
+// non-empty key cells then form a list ordered by particle count, largest first. Even warps take grid
+// 1's list and odd warps grid 2's (all warps grid 1's without interlacing); thread t of a grid's nt
+// threads takes item t of each round of nt items in even rounds and item nt - 1 - t in odd ones, so
+// the 32 lanes of a warp hold cells of nearly equal load and the warps' totals even out. A lane sums
+// its cell's particles into a register window of p^3 node values (the cell's whole stencil) and adds
+// the window to the tile's fixed-point region once. Pieces need no order inside the tile.
 namespace tiles {
 constexpr int CELL_THREADS = 256;
 constexpr int CNT_BINS = 64;  // particle counts above 63 share the first place of the ordering
@@ -579,42 +580,23 @@ struct CellSmem {
   unsigned short perm[2][cell_chunk<W>()];
   int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
   alignas(16) int reg[2][RVOL];
-  unsigned short order[2 * NKEY];  // non-empty key cells (grid in bit 15), largest bucket first
-  int cbin[CNT_BINS];
-  int nitems;
+  unsigned short order[2][NKEY];  // non-empty key cells per grid, largest bucket first
+  int cbin[2][CNT_BINS];
+  int nitems[2];
   float red[CELL_THREADS / 32];
   int scan[2][CELL_THREADS / 32];
   unsigned long long mbar;
   float sw[W ? cell_chunk<W>() : 1];
 };
 
-// Window operands of one particle on grid g (a runtime grid: the lanes of a warp may hold cells of
-// either grid).
-template <int P>
-__device__ __forceinline__ Operands<P> cell_operands(const int4 r, float wgt, bool g) {
-  int4 q = r;
-  if (g) {  // the shifted grid samples the particle displaced by H/2: the same offsets as grid_key<P, 1>
-    float f;
-    half_shift(__int_as_float(r.y), &f);
-    q.y = __float_as_int(f);
-    half_shift(__int_as_float(r.z), &f);
-    q.z = __float_as_int(f);
-    half_shift(__int_as_float(r.w), &f);
-    q.w = __float_as_int(f);
-  }
-  return particle_operands<P, 0>(q, wgt);
-}
-
-// One key cell of grid g: its bucket of particles into a register window, then the window into the
+// One key cell of grid G: its bucket of particles into a register window, then the window into the
 // region (nodes key + S0 + 1 .. key + S0 + p per axis). The fixed-point scale (a power of two) rides
 // on the particle weight, so the window already holds fixed-point values; the next record is loaded
 // before the current one is accumulated.
-template <int P, bool W>
-__device__ __forceinline__ void cell_key(const CellSmem<W>& S, int item, float wscale) {
-  const bool g = item >> 15;
-  const int key = item & 0x7fff;
-  const int* ends = S.hist[g];
-  const unsigned short* perm = S.perm[g];
+template <int P, bool W, int G>
+__device__ __forceinline__ void cell_key(const CellSmem<W>& S, int key, float wscale) {
+  const int* ends = S.hist[G];
+  const unsigned short* perm = S.perm[G];
   const int jb = key == 0 ? 0 : ends[key - 1], je = ends[key];
   const int kx = key % K, kz = (key / K) % K, ky = key / (K * K);
   Window<P> win;
@@ -634,10 +616,10 @@ __device__ __forceinline__ void cell_key(const CellSmem<W>& S, int item, float w
       r = S.sp[i];
       if (W) rw = S.sw[i];
     }
-    win.add(cell_operands<P>(c, cw * wscale, g));
+    win.add(particle_operands<P, G>(c, cw * wscale));
   }
   const unsigned base =
-      smem_u32(&S.reg[g][0] + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1);
+      smem_u32(&S.reg[G][0] + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1);
 #pragma unroll
   for (int a = 0; a < P; ++a)
 #pragma unroll
@@ -702,7 +684,7 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
       if (W)
         for (int i = tid; i < m; i += THREADS) S.sw[i] = w[c0 + i];
       for (int i = tid; i < 2 * (NKEY + 1); i += THREADS) (&S.hist[0][0])[i] = 0;
-      if (tid < CNT_BINS) S.cbin[tid] = 0;
+      if (tid < 2 * CNT_BINS) (&S.cbin[0][0])[tid] = 0;
       const bool arrived = bulk_wait(&S.mbar, parity);
       parity ^= 1u;
       if (__syncthreads_or(!arrived)) {  // the copy did not complete: report, drain, stop
@@ -752,8 +734,8 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         const int idx = tid * SCAN_PER_THREAD + k;
         v0[k] = idx <= NKEY ? S.hist[0][idx] : 0;
         v1[k] = idx <= NKEY ? S.hist[1][idx] : 0;
-        if (v0[k] > 0) atomicAdd(&S.cbin[CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1);  // entry NKEY is 0
-        if (v1[k] > 0) atomicAdd(&S.cbin[CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1);
+        if (v0[k] > 0) atomicAdd(&S.cbin[0][CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1);  // entry NKEY is 0
+        if (v1[k] > 0) atomicAdd(&S.cbin[1][CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1);
         s0v += v0[k];
         s1v += v1[k];
       }
@@ -772,9 +754,10 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         S.scan[1][warp] = x1;
       }
       __syncthreads();
-      // exclusive offsets of both histograms; warp 0 scans the count bins (64 bins, two per lane)
-      if (warp == 0) {
-        const int a0 = S.cbin[2 * lane], a1 = S.cbin[2 * lane + 1];
+      // exclusive offsets of both histograms; warp g scans grid g's count bins (64 bins, two per lane)
+      if (warp < 2) {
+        int* cb = S.cbin[warp];
+        const int a0 = cb[2 * lane], a1 = cb[2 * lane + 1];
         int x = a0 + a1;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -782,9 +765,9 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
           if (lane >= o) x += y;
         }
         const int ex = x - a0 - a1;
-        S.cbin[2 * lane] = ex;
-        S.cbin[2 * lane + 1] = ex + a0;
-        if (lane == 31) S.nitems = x;
+        cb[2 * lane] = ex;
+        cb[2 * lane + 1] = ex + a0;
+        if (lane == 31) S.nitems[warp] = x;
       }
       {
         int e0 = x0 - s0v, e1 = x1 - s1v;
@@ -810,9 +793,8 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
 #pragma unroll
       for (int k = 0; k < SCAN_PER_THREAD; ++k) {
         const int idx = tid * SCAN_PER_THREAD + k;
-        if (v0[k] > 0) S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1)] = (unsigned short)idx;
-        if (v1[k] > 0)
-          S.order[atomicAdd(&S.cbin[CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1)] = (unsigned short)(idx | 0x8000);
+        if (v0[k] > 0) S.order[0][atomicAdd(&S.cbin[0][CNT_BINS - 1 - min(v0[k], CNT_BINS - 1)], 1)] = (unsigned short)idx;
+        if (v1[k] > 0) S.order[1][atomicAdd(&S.cbin[1][CNT_BINS - 1 - min(v1[k], CNT_BINS - 1)], 1)] = (unsigned short)idx;
       }
       for (int i0 = tid; i0 < m; i0 += 4 * THREADS) {
         int keys[4], at0[4], at1[4];
@@ -831,11 +813,26 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         }
       }
       __syncthreads();
-      const int nitems = S.nitems;
-      for (int r0 = 0; r0 < nitems; r0 += 2 * THREADS) {  // two rounds: ascending, then descending
-        if (r0 + tid < nitems) cell_key<P, W>(S, S.order[r0 + tid], wscale);
-        const int i1 = r0 + 2 * THREADS - 1 - tid;
-        if (i1 < nitems) cell_key<P, W>(S, S.order[i1], wscale);
+      // interlaced: even warps take grid 1's key cells and odd warps grid 2's (the grid is then a
+      // compile-time constant of the inner loop); otherwise all warps take grid 1's. Within a grid,
+      // thread t of the grid's nt threads takes item t of each round of nt in even rounds and item
+      // nt - 1 - t in odd ones.
+      {
+        const int gsel = interlace ? (warp & 1) : 0;
+        const int nt = interlace ? THREADS / 2 : THREADS;
+        const int t = interlace ? (warp >> 1) * 32 + lane : tid;
+        const int nitems = S.nitems[gsel];
+        const unsigned short* order = S.order[gsel];
+        for (int r0 = 0; r0 < nitems; r0 += 2 * nt) {  // two rounds: ascending, then descending
+          const int i0 = r0 + t, i1 = r0 + 2 * nt - 1 - t;
+          if (gsel == 0) {
+            if (i0 < nitems) cell_key<P, W, 0>(S, order[i0], wscale);
+            if (i1 < nitems) cell_key<P, W, 0>(S, order[i1], wscale);
+          } else {
+            if (i0 < nitems) cell_key<P, W, 1>(S, order[i0], wscale);
+            if (i1 < nitems) cell_key<P, W, 1>(S, order[i1], wscale);
+          }
+        }
       }
       __syncthreads();
     }
