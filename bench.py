@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--box", type=float, default=2000.0)
     ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
-    ap.add_argument("--only-row", choices=["adjoint", "batch", "direct", "multigrid"], default=None,
+    ap.add_argument("--only-row", choices=["adjoint", "batch", "direct", "multigrid", "e2e"], default=None,
                     help="time one secondary row on its own workload and print it (no P(k) step)")
     ap.add_argument("--ds-nside", type=int, default=128, help="--only-row direct: particles per side")
     ap.add_argument("--ds-ng", type=int, default=128, help="--only-row direct: grid size")
@@ -394,6 +394,31 @@ def row_multigrid(dev):
     return out
 
 
+def row_e2e(dev, nside, ng, box, profile_range=False):
+    """pk_power_host alone on the benchmark's catalogue (pinned host FP64 positions), for profiling."""
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs, ffi
+
+    cfg = api.Config(ng=ng, box=box, order=4, interlace=True, prec="fp32")
+    n = nside ** 3
+    host64 = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    host64.copy_(catalogs.zeldovich_torch(nside, box, RMS_DISP, seed=replica_seed(0), device=dev))
+    torch.cuda.empty_cache()
+    wsp = api.workspace(cfg, n, ffi.PK_WS_POWER_HOST, dev)
+    host_out = (torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True),
+                torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True),
+                torch.empty(cfg.nb, dtype=torch.int64, pin_memory=True))
+    ms = _time_cuda(lambda: api.power_host(host64, cfg, ws=wsp, out=host_out, device=dev), 3)
+    if profile_range:  # one call bracketed for ncu --profile-from-start off
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        api.power_host(host64, cfg, ws=wsp, out=host_out, device=dev)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    return {"workload": f"pk_power_host, {n} particles from pinned host FP64 positions, N_G={ng}", "ms_per_call": ms}
+
+
 def measure_rows(dev, host64, big_box, alu_peak_tflops):
     """Times the other hot-path rows on their own workloads (one GB300)."""
     return {"bispectrum": row_bispectrum(dev, host64, big_box), "adjoint": row_adjoint(dev), "batch": row_batch(dev),
@@ -462,7 +487,8 @@ def main():
     if a.only_row:
         row = {"adjoint": lambda: row_adjoint(dev), "batch": lambda: row_batch(dev, a.profile_range, a.batch_cats),
                "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng),
-               "multigrid": lambda: row_multigrid(dev)}[a.only_row]()
+               "multigrid": lambda: row_multigrid(dev),
+               "e2e": lambda: row_e2e(dev, a.nside, a.ng, a.box, a.profile_range)}[a.only_row]()
         if rank == 0:
             print(json.dumps({"row": a.only_row, **row}), flush=True)
         return

@@ -15,23 +15,60 @@ namespace pk {
 
 PK_ERR_ACCESSOR(take_err_prepare)
 
+// floor(u) and the fraction u - floor(u) rounded to FP32 (to nearest, ties to even) for 0 <= u < 2^20,
+// read from u's bits with integer operations: FP64 arithmetic is scarce on this GPU, and the fraction
+// of a double is exact in its significand, so this equals float(u - floor(u)) bit for bit.
+__device__ __forceinline__ void split_units(double u, int* c, float* f) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(u));
+  const int e = int((b >> 52) & 0x7ff) - 1023;
+  if (e < 0) {  // u in [0, 1), or -0: floor 0 (+ 0.0f makes -0 the +0 that u - floor(u) gives)
+    *c = 0;
+    *f = __double2float_rn(u) + 0.0f;
+    return;
+  }
+  const int sh = 52 - e;  // fraction bits of the significand (32 < sh <= 52 for u < 2^20)
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  *c = int(m >> sh);
+  const unsigned long long fr = m & ((1ull << sh) - 1);  // u - floor(u) = fr 2^-sh exactly
+  if (fr == 0) {
+    *f = 0.0f;
+    return;
+  }
+  const int top = 63 - __clzll(static_cast<long long>(fr));  // fr in [2^top, 2^(top+1)), top < sh
+  unsigned long long m24;  // 24-bit significand, rounded; 2^24 when the rounding carries
+  if (top >= 24) {
+    const int d = top - 23;
+    m24 = fr >> d;
+    const unsigned long long rem = fr & ((1ull << d) - 1), half = 1ull << (d - 1);
+    if (rem > half || (rem == half && (m24 & 1ull))) ++m24;
+  } else {
+    m24 = fr << (23 - top);
+  }
+  const int ex = top - sh + 127;  // biased exponent of 2^(top - sh), >= 75
+  *f = __int_as_float(int((unsigned(ex - 1) << 23) + unsigned(m24)));
+}
+
 __device__ __forceinline__ pk_cellpos prepare_one(const double* p, int ng, double box, double scale) {
   pk_cellpos r;
   int c[3];
   float fo[3];
   bool bad = false;
+  const unsigned long long box_bits = static_cast<unsigned long long>(__double_as_longlong(box));
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double x = p[a];
-    if (!isfinite(x)) { bad = true; x = 0.0; }
-    x = fmod(x, box);
-    if (x < 0.0) x += box;
-    const double u = x * scale;
-    double fl = floor(u);
-    int ci = int(fl);
-    double f = u - fl;
+    const unsigned long long xb = static_cast<unsigned long long>(__double_as_longlong(x));
+    if (((xb >> 52) & 0x7ff) == 0x7ff) {  // NaN or infinite
+      bad = true;
+      x = 0.0;
+    } else if (xb >= box_bits) {  // negative (sign bit) or >= L: another periodic image
+      x = fmod(x, box);
+      if (x < 0.0) x += box;
+    }
+    int ci;
+    float ff;
+    split_units(x * scale, &ci, &ff);
     if (ci >= ng) { ci -= ng; }
-    float ff = float(f);
     if (ff >= 1.0f) {  // f rounded up to 1 in FP32: the particle sits on the next node
       ff = 0.0f;
       ci = ci + 1 == ng ? 0 : ci + 1;
