@@ -120,8 +120,10 @@ __global__ void k_gather(const void* __restrict__ pos, int fmt, const float* __r
       for (int a = 0; a < 3; ++a) {
         double x = p[a];
         if (!isfinite(x)) { ok = false; x = 0.0; }
-        x = fmod(x, box);
-        if (x < 0.0) x += box;
+        if (!(x >= 0.0 && x < box)) {  // another periodic image (fmod is the identity on [0, L))
+          x = fmod(x, box);
+          if (x < 0.0) x += box;
+        }
         const double u = x * scale;
         const double fl = floor(u);
         int ci = int(fl);
