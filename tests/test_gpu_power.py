@@ -145,6 +145,37 @@ def test_prepare_offsets_and_cells():
     assert np.all((f >= 0) & (f < 1))
 
 
+def test_prepare_is_the_fp64_definition_bit_for_bit():
+    # N = L, so u = x exactly: the record must hold c = floor(u) and f = float32(u - c) (round to
+    # nearest, ties to even; an f that rounds to 1 moves to the next cell, periodically). Random
+    # positions, exact FP32 ties of the fraction, fractions that round up to 1 and the last cell.
+    ng = 64
+    box = float(ng)
+    rng = np.random.default_rng(43)
+    x = [rng.uniform(0.0, box, 200000)]
+    k = rng.integers(0, ng, 4000).astype(np.float64)
+    j = rng.integers(0, 2 ** 20, 4000).astype(np.float64)
+    x.append(k + 0.25 + (2 * j + 1) * 2.0 ** -26)  # halfway between FP32 neighbours in [1/4, 1/2)
+    x.append(k + 0.5 + (2 * j + 1) * 2.0 ** -25)  # halfway in [1/2, 1)
+    x.append(k + 1.0 - 2.0 ** -26)  # rounds up to 1: next cell
+    x.append(k + 1.0 - 3 * 2.0 ** -26)
+    x.append(np.array([box - 2.0 ** -40, box - 2.0 ** -26, 0.0, 2.0 ** -60, 0.5 - 2.0 ** -25]))
+    x = np.concatenate(x)
+    x = x[(x >= 0.0) & (x < box)]
+    pos = np.stack([x, np.roll(x, 1), np.roll(x, 2)], axis=1)
+    cells = api.prepare(_t(pos), api.Config(ng=ng, box=box)).cpu().numpy()
+    c = np.floor(pos).astype(np.int64)
+    f = (pos - c).astype(np.float32)
+    up = f >= np.float32(1.0)
+    c = np.where(up, c + 1, c) % ng
+    f = np.where(up, np.float32(0.0), f).astype(np.float32)
+    got_c = cells[:, 0].view(np.uint32).astype(np.int64)
+    assert np.array_equal((got_c >> 20) & 1023, c[:, 0])
+    assert np.array_equal((got_c >> 10) & 1023, c[:, 1])
+    assert np.array_equal(got_c & 1023, c[:, 2])
+    assert np.array_equal(cells[:, 1:], f.view(np.int32))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fixed64"])
 def test_edge_positions_and_tiny_grid(prec):
     # positions on the box faces, outside the box and on nodes; ng = 8 makes the shared-memory
