@@ -546,3 +546,105 @@ def test_single_node_value_closed_forms():
     assert assign.node_value(u, 8, 2, (2, 3, 4)) == pytest.approx(1.0, rel=1e-15)
     v = np.array([[2.5, 3.0, 4.0]])
     assert assign.node_value(v, 8, 4, (2, 3, 4)) == pytest.approx(23.0 / 48.0 * (2.0 / 3.0) ** 2, rel=1e-15)
+
+
+# --- k_eff, the weighted shot noise and the bispectrum normalisation ---------------------------------
+
+def test_keff_is_the_mean_wavenumber_of_the_enumerated_modes():
+    # k_eff of a bin is the mean |k| of its modes, with k = k_f n and k_f = 2 pi / L (Sec. 2.2). Every
+    # integer vector of the grid is listed one at a time, its |n| taken in floating point and its bin
+    # found by rounding |n| to the nearest integer (the default bins are centred on b k_f); the mean of
+    # 2 pi |n| / L per bin must equal the oracle's k_eff. The first two bins also have closed forms from
+    # the number of ways r3(m) to write m as a sum of three squares (r3 = 6, 12, 8, 6, 24, 24 for
+    # m = 1..6). Planted mistakes this fails: k_f = 1/L or pi/L, |k| from 4|n|^2 without the 1/4, a mode
+    # set that leaves out the Nyquist planes.
+    ng, box = 8, 7.3
+    kf = 2.0 * math.pi / box
+    sums, cnts = {}, {}
+    rng_n = range(-ng // 2, ng // 2)
+    for nx, ny, nz in itertools.product(rng_n, rng_n, rng_n):
+        m2 = nx * nx + ny * ny + nz * nz
+        if m2 == 0:
+            continue
+        r = math.sqrt(m2)
+        b = int(math.floor(r + 0.5))
+        if 1 <= b <= ng // 2:
+            sums[b] = sums.get(b, 0.0) + kf * r
+            cnts[b] = cnts.get(b, 0) + 1
+    delta = np.random.default_rng(5).standard_normal((ng, ng, ng)) + 0j
+    _, keff, cnt = power.power_spectrum(delta, box)
+    for b in range(1, ng // 2 + 1):
+        assert cnt[b - 1] == cnts[b]
+        assert keff[b - 1] == pytest.approx(sums[b] / cnts[b], rel=1e-14)
+    assert keff[0] == pytest.approx(kf * (6 * 1.0 + 12 * math.sqrt(2.0)) / 18, rel=1e-14)
+    k2 = kf * (8 * math.sqrt(3.0) + 6 * 2.0 + 24 * math.sqrt(5.0) + 24 * math.sqrt(6.0)) / 62
+    assert keff[1] == pytest.approx(k2, rel=1e-14)
+
+
+def test_weighted_poisson_power_matches_weighted_shot_noise():
+    # With fixed weights w_i on independent uniform positions, E|sum_i w_i e^{-i k.x_i}|^2 = sum_i w_i^2
+    # for k != 0 (the cross terms average to zero), so after the division by sum w the window-corrected
+    # power averages to V sum w^2 / (sum w)^2 times the same aliasing sum as the unweighted Poisson case
+    # (eq:Pknoint, interlaced form). The level is taken from power.shot_noise(box, weights). The weights
+    # are spread (coefficient of variation about 0.8), so V/N_P differs from the weighted level by
+    # about 60 %. Planted mistakes this fails (each by many sigma): 1/nbar = V/N_P with the weights
+    # ignored, sum w in place of (sum w)^2, (sum w^2)^2 in the numerator, a missing V.
+    p, ng, box, npart, nseeds = 4, 8, 100.0, 400, 300
+    w = np.random.default_rng(77).lognormal(0.0, 0.7, size=npart)
+    shot_w = power.shot_noise(box, w)
+    assert abs(shot_w / (box ** 3 / npart) - 1.0) > 0.3
+    edges = power.default_edges(ng)
+    b = power.bin_index(ng, edges)
+    half = ng // 2
+    sn = fourier.signed_index(ng)
+    nvec = np.stack(np.meshgrid(sn, sn, sn, indexing="ij"), axis=-1)
+    sel = b >= 0
+    e_mode = aliasing.shot_noise_expectation(nvec[sel], ng, p, True, 1.0, mmax=3000) * shot_w
+    cnt = np.bincount(b[sel], minlength=half)
+    expect = np.bincount(b[sel], weights=e_mode, minlength=half) / cnt
+    var_mode = np.bincount(b[sel], weights=e_mode ** 2, minlength=half) / cnt
+    acc = np.zeros(half)
+    for s in range(nseeds):
+        pos = catalogs.poisson(npart, box, seed=5000 + s)
+        r1 = assign.assign(pos, box, ng, p, weights=w)
+        r2 = assign.assign(pos, box, ng, p, weights=w, shift=True)
+        pk, _, _ = power.power_spectrum(fourier.density_modes(r1, p, r2), box, edges)
+        acc += pk
+    mean = acc / nseeds
+    sigma = np.sqrt(var_mode / (cnt / 2.0) / nseeds)
+    z = (mean - expect) / sigma
+    assert np.max(np.abs(z)) < 4.5, z
+    # subtracting the weighted shot noise leaves only the aliasing excess, a small fraction of it
+    pk_sub, _, _ = power.power_spectrum(fourier.density_modes(r1, p, r2), box, edges, subtract=shot_w)
+    assert np.allclose(pk_sub, pk - shot_w, rtol=0, atol=1e-9 * shot_w)
+
+
+def test_poisson_bispectrum_is_the_squared_shot_noise():
+    # For independent uniform positions (P = B = 0) only the shot-noise terms of B_tot (Sec. 4.1)
+    # remain: with delta_q = (1/N) sum_i e^{-i q.x_i}, a closed triplet q1 + q2 + q3 = 0 of non-zero
+    # modes averages to E[delta_q1 delta_q2 delta_q3] = N / N^3 (only i = j = l survives), so the
+    # estimator of eq:Best, V^2 times the mean over the triplets, averages to (V/N)^2 = 1/nbar^2 at
+    # low k (the grid's images change it by far less than the statistical error here). Planted
+    # mistakes this fails: V in place of V^2 (box = 37, a factor 5e4), a missing or squared N_c, a
+    # triplet count off by a factor, a sign flip of the triple product.
+    ng, box, npart, nseeds, p = 12, 37.0, 200, 200, 4
+    nbar_inv2 = (box ** 3 / npart) ** 2
+    tri = bispectrum.triangles(3)
+    acc = np.zeros(len(tri))
+    acc2 = np.zeros(len(tri))
+    counts = None
+    for s in range(nseeds):
+        pos = catalogs.poisson(npart, box, seed=9000 + s)
+        r1 = assign.assign(pos, box, ng, p)
+        r2 = assign.assign(pos, box, ng, p, shift=True)
+        delta = fourier.density_modes(r1, p, r2)
+        bk, counts = bispectrum.bispectrum_fft(delta, box, 1, 1, 3)
+        acc += bk / nbar_inv2
+        acc2 += (bk / nbar_inv2) ** 2
+    ok = counts > 0
+    assert ok.sum() >= 6
+    mean = acc / nseeds
+    err = np.sqrt(np.maximum(acc2 / nseeds - mean ** 2, 0.0) / nseeds)
+    z = (mean[ok] - 1.0) / err[ok]
+    assert np.max(np.abs(z)) < 4.5, (mean, err)
+    assert np.all(np.abs(mean[ok] - 1.0) < 0.25)
