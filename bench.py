@@ -55,11 +55,12 @@ def parse():
     ap.add_argument("--box", type=float, default=2000.0)
     ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
-    ap.add_argument("--only-row", choices=["adjoint", "batch", "direct", "multigrid", "e2e"], default=None,
+    ap.add_argument("--only-row", choices=["adjoint", "batch", "bispectrum", "direct", "multigrid", "e2e"], default=None,
                     help="time one secondary row on its own workload and print it (no P(k) step)")
     ap.add_argument("--ds-nside", type=int, default=128, help="--only-row direct: particles per side")
     ap.add_argument("--ds-ng", type=int, default=128, help="--only-row direct: grid size")
     ap.add_argument("--batch-cats", type=int, default=512, help="--only-row batch: catalogues in the batch")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the measured CPU oracle rows (c1 and c2 configurations)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -171,6 +172,141 @@ def oracle_sample_rate(pos_sample, n_full, box, ng, with_fft=True):
                              "t_full_extrapolated_s": t_full}
 
 
+def _oracle_assign_chunk(args):
+    """One worker's share of the oracle's assignment (both grids): u in grid units."""
+    import oracle
+
+    u, ng, p = args
+    return oracle.assign.assign_units(u, ng, p), oracle.assign.assign_units(u, ng, p, shift=True)
+
+
+def oracle_power_parallel(pos, box, ng, p, workers):
+    """The FP64 oracle's P(k) (PCS + interlacing at p = 4) with its assignment split over worker
+    processes by particle chunk (the oracle's own function on each chunk, the chunk grids summed); the
+    FFT, deconvolution and binning run in this process (scipy.fft with every core). Returns
+    (pk, t_assign_s, t_rest_s)."""
+    import concurrent.futures
+    import multiprocessing
+
+    import oracle
+
+    t0 = time.perf_counter()
+    u = oracle.assign.grid_units(pos, box, ng)
+    chunks = np.array_split(u, workers)
+    with concurrent.futures.ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+        r1 = r2 = None
+        for a, b in ex.map(_oracle_assign_chunk, [(c, ng, p) for c in chunks]):
+            r1 = a if r1 is None else r1 + a
+            r2 = b if r2 is None else r2 + b
+    t_assign = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pk, _, _ = oracle.power.power_spectrum(oracle.fourier.density_modes(r1, p, r2), box)
+    return pk, t_assign, time.perf_counter() - t0
+
+
+def measured_oracle_rows(steps=3):
+    """The FP64 CPU oracle timed end to end (assignment of both grids, FFT, deconvolution, interlacing,
+    binning) on the two smaller benchmark configurations, median of `steps` runs, assignment over a
+    process pool of every host core: c1, 64^3 Poisson particles in L = 1000 Mpc/h on N_G = 64; c2,
+    256^3 Zel'dovich particles in L = 1500 Mpc/h on N_G = 256 (PCS + interlacing both)."""
+    from paper_1512_07295_gb300 import catalogs
+
+    cores = len(os.sched_getaffinity(0))
+    out = {"cores": cores, "kind": "oracle", "runs": steps}
+    cases = {"c1_poisson_64cube_ng64": (catalogs.poisson(64 ** 3, 1000.0, seed=1), 1000.0, 64),
+             "c2_zeldovich_256cube_ng256": (catalogs.zeldovich(256, 1500.0, rms=RMS_DISP, seed=2), 1500.0, 256)}
+    for name, (pos, box, ng) in cases.items():
+        walls, parts = [], []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            _, ta, tr = oracle_power_parallel(pos, box, ng, 4, cores)
+            walls.append(time.perf_counter() - t0)
+            parts.append((ta, tr))
+        i = int(np.argsort(walls)[len(walls) // 2])
+        out[name] = {"particles": int(len(pos)), "s_per_pk_median": float(walls[i]),
+                     "particles_per_s": float(len(pos) / walls[i]), "t_assign_s": float(parts[i][0]),
+                     "t_fft_estimate_s": float(parts[i][1]), "all_s": [float(x) for x in walls]}
+    return out
+
+
+def _rel_per_bin(a, b):
+    a = a.double().cpu().numpy()
+    b = b.double().cpu().numpy()
+    return np.abs(a / b - 1.0)
+
+
+def _sig(x, digits=3):
+    return [float(f"{v:.{digits}g}") for v in np.asarray(x, dtype=np.float64)]
+
+
+def row_accuracy_c2(dev):
+    """FP32 against FP64, per k-bin, on the 256^3 Zel'dovich catalogue (L = 1500 Mpc/h, N_G = 256):
+    CIC, TSC, PCS, each with and without interlacing. FP64: pk_power from the FP64 positions (the
+    oracle-parity mode); FP32: pk_power on the same positions, which splits them into cell + FP32
+    offset records (a1) and runs the FP32 grids and transforms with FP64 shell sums. The difference is
+    the whole FP32 path's error: positions, assignment, FFT and estimate."""
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs
+
+    pos = catalogs.zeldovich_torch(256, 1500.0, RMS_DISP, seed=2, device=dev)
+    out = {"workload": "256^3 ZA particles, L=1500 Mpc/h, N_G=256: FP32 (cell + FP32 offset) vs FP64 positions and "
+                       "grids, |P32/P64 - 1| per k-bin", "cases": {}}
+    for p, name in ((2, "CIC"), (3, "TSC"), (4, "PCS")):
+        for inter in (False, True):
+            c64 = api.Config(ng=256, box=1500.0, order=p, interlace=inter, prec="fp64")
+            c32 = api.Config(ng=256, box=1500.0, order=p, interlace=inter, prec="fp32")
+            pk64, _, n64 = api.power(pos, c64)
+            ws = api.workspace(c32, pos.shape[0], api.ffi.PK_WS_POWER, dev)
+            pk32, _, n32 = api.power(pos, c32, ws=ws)
+            ms = _time_cuda(lambda: api.power(pos, c32, ws=ws), 3)
+            rel = _rel_per_bin(pk32, pk64)
+            out["cases"][f"{name}{'+interlace' if inter else ''}"] = {
+                "max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+                "counts_equal": bool(torch.equal(n32, n64)), "fp32_ms_per_pk": ms, "per_bin": _sig(rel, 2)}
+            del ws
+    del pos
+    torch.cuda.empty_cache()
+    return out
+
+
+def numa_report(host_tensor, dev_index):
+    """Where a pinned host buffer's pages live and which NUMA node the GPU hangs off (Linux sysfs and
+    /proc/self/numa_maps), to explain the CPU-GPU link rate of the end-to-end call."""
+    rep = {}
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev_index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
+        dom, rest = out.split(":", 1)
+        sysfs = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/numa_node"
+        rep["gpu_pci"] = out
+        rep["gpu_numa_node"] = int(open(sysfs).read().strip()) if os.path.exists(sysfs) else None
+    except Exception as e:  # pragma: no cover - depends on the host
+        rep["gpu_numa_node_error"] = type(e).__name__
+    try:
+        addr = host_tensor.data_ptr()
+        end = addr + host_tensor.numel() * host_tensor.element_size()
+        pages = {}
+        for line in open("/proc/self/numa_maps"):
+            parts = line.split()
+            start = int(parts[0], 16)
+            if addr <= start < end or start <= addr < start + (1 << 32):
+                for f in parts[1:]:
+                    if f.startswith("N") and "=" in f:
+                        k, v = f.split("=")
+                        pages[k] = pages.get(k, 0) + int(v)
+        rep["buffer_pages_per_node"] = pages
+    except Exception as e:  # pragma: no cover
+        rep["numa_maps_error"] = type(e).__name__
+    try:
+        rep["cpus"] = len(os.sched_getaffinity(0))
+        rep["host_nodes"] = sorted(int(d[4:]) for d in os.listdir("/sys/devices/system/node")
+                                   if d.startswith("node") and d[4:].isdigit())
+    except Exception:  # pragma: no cover
+        pass
+    return rep
+
+
 def _time_cuda(fn, reps, warm=1):
     import torch
 
@@ -228,6 +364,17 @@ def row_bispectrum(dev, host64, big_box):
     del ws, delta, counts, out
     torch.cuda.empty_cache()
     return rows["bispectrum"]
+
+
+def row_bispectrum_only(dev, a):
+    """The bispectrum row on its own: the catalogue generated on the GPU, then row_bispectrum."""
+    import torch
+
+    from paper_1512_07295_gb300 import catalogs
+
+    pos = catalogs.zeldovich_torch(a.nside, a.box, RMS_DISP, seed=replica_seed(0), device=dev).cpu()
+    torch.cuda.empty_cache()
+    return row_bispectrum(dev, pos, a.box)
 
 
 def row_adjoint(dev):
@@ -426,39 +573,59 @@ def measure_rows(dev, host64, big_box, alu_peak_tflops):
 
 
 def run_reference(a):
-    """The reference arm: the FP64 CPU oracle, one bounded sample of the workload per step."""
+    """The reference arm: the FP64 CPU oracle on the host cores, one bounded sample of the workload per
+    step: the oracle's assignment (both grids) of 2^20 particles over a process pool of every core,
+    scaled linearly to the full catalogue, plus the oracle's FFT, deconvolution, interlacing and binning
+    of one full N_G grid pair (timed once, added to every step)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import concurrent.futures
+    import multiprocessing
+
+    import oracle
     from paper_1512_07295_gb300 import catalogs
 
     n_full = a.nside ** 3
-    # a Zel'dovich catalogue of the same box and displacement recipe; the oracle's cost per particle
-    # does not depend on the clustering, so a 64^3 lattice stands in for the sample source
-    src = catalogs.zeldovich(64, a.box, rms=RMS_DISP, seed=3)
-    rng = np.random.default_rng(5)
-    sample = 1 << 14
-    rates = []
-    t_start = time.perf_counter()
-    for step in range(a.warmup + a.steps):
-        pos = src[rng.choice(len(src), size=sample, replace=False)]
-        rate, det = oracle_sample_rate(pos, n_full, a.box, a.ng, with_fft=True)
-        if step >= a.warmup:
-            rates.append(rate)
-    wall = time.perf_counter() - t_start
-    value = float(np.median(rates))
     cores = len(os.sched_getaffinity(0))
+    # a Zel'dovich catalogue of the same box and displacement recipe, 128^3 particles: the oracle's cost
+    # per particle does not depend on the clustering, so it stands in as the sample source
+    src = catalogs.zeldovich(128, a.box, rms=RMS_DISP, seed=3)
+    rng = np.random.default_rng(5)
+    sample = 1 << 20
+    t0 = time.perf_counter()
+    r1 = oracle.assign.assign_units(oracle.assign.grid_units(src[:4096], a.box, a.ng), a.ng, 4)
+    r2 = oracle.assign.assign_units(oracle.assign.grid_units(src[:4096], a.box, a.ng), a.ng, 4, shift=True)
+    t1 = time.perf_counter()
+    oracle.power.power_spectrum(oracle.fourier.density_modes(r1, 4, r2), a.box)
+    t_fft = time.perf_counter() - t1
+    del r1, r2
+    rates = []
+    with concurrent.futures.ProcessPoolExecutor(cores, mp_context=multiprocessing.get_context("spawn")) as ex:
+        for step in range(a.warmup + a.steps):
+            pos = src[rng.choice(len(src), size=sample, replace=False)]
+            u = oracle.assign.grid_units(pos, a.box, a.ng)
+            ts = time.perf_counter()
+            for _ in ex.map(_oracle_assign_chunk, [(c, a.ng, 4) for c in np.array_split(u, cores)]):
+                pass
+            t_assign = time.perf_counter() - ts
+            if step >= a.warmup:
+                rates.append(n_full / (t_assign * n_full / sample + t_fft))
+    wall = time.perf_counter() - t0
+    value = float(np.median(rates))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1e3 * n_full / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(a), "timed": "FP64 CPU oracle per step: 2^14-particle assignment of both "
-                   f"grids + one N_G={a.ng} FFT/deconvolution/binning, assignment time scaled to {n_full} particles"},
+        "config": {"workload": workload_name(a), "timed": "FP64 CPU oracle per step: 2^20-particle assignment of both grids "
+                   f"over {cores} worker processes, scaled to {n_full} particles, + one N_G={a.ng} FFT/deconvolution/"
+                   "binning (timed once)"},
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
-                         "sample": "2^14 particles per step (assignment, both grids, single-threaded NumPy) + full "
-                                   f"N_G={a.ng} FFT (scipy, {cores} workers) and binning; extrapolated linearly in N_P"},
+                         "sample": f"2^20 particles per step of a 128^3 Zel'dovich catalogue of the same recipe (assignment, "
+                                   f"both grids, {cores} processes) + one full N_G={a.ng} FFT (scipy, {cores} workers) and "
+                                   "binning; extrapolated linearly in N_P"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s": wall,
+        "wall_s": wall, "t_fft_estimate_s": t_fft,
     }
     print(json.dumps(line), flush=True)
 
@@ -486,6 +653,7 @@ def main():
     lib = ffi.lib()
     if a.only_row:
         row = {"adjoint": lambda: row_adjoint(dev), "batch": lambda: row_batch(dev, a.profile_range, a.batch_cats),
+               "bispectrum": lambda: row_bispectrum_only(dev, a),
                "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng),
                "multigrid": lambda: row_multigrid(dev),
                "e2e": lambda: row_e2e(dev, a.nside, a.ng, a.box, a.profile_range)}[a.only_row]()
@@ -578,24 +746,28 @@ def main():
                    "l2": "inputs (16 B x 1024^3 particles = 17.2 GB) far exceed the 129 MB L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "pk_per_s": pk_per_s,
+        # the dominant kernel against the HBM roofline (algorithmic bytes / CUDA-event time of the stage)
+        "roofline": {"kernel": "k_assign_cells<4,false>", "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                     "traffic_source": ASSIGN_TRAFFIC_SOURCE if traffic else None, "algorithmic_bytes": assign_bytes,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                     "timing": "CUDA events on the library's stream around the assignment stage (scatter pass + key-cell "
+                               f"kernel), mean over {nprof} steps",
+                     "note": "bound by shared-memory and instruction issue, not DRAM: see alu",
+                     "alu": {"achieved": achieved_tflops, "peak": alu_peak_tflops, "unit": "TFLOP/s",
+                             "frac": achieved_tflops / alu_peak_tflops,
+                             "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x the maximum SM clock"}},
         "path_hbm_roofline": {"algorithmic_bytes": path_bytes, "achieved_gbs": path_bytes / (ms_step * 1e-3) / 1e9,
                               "peak_gbs": hbm_peak, "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak},
         "stages_ms": {"weights": stages[0], "grid_clear": stages[1], "assign": stages[2], "fft": stages[3],
                       "estimate": stages[4]},
-        "roofline": {"kernel": "k_assign_cells<4,false>", "bound": "alu", "achieved": achieved_tflops,
-                     "peak": alu_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops,
-                     "traffic": traffic, "traffic_source": ASSIGN_TRAFFIC_SOURCE if traffic else None,
-                     "algorithmic_bytes": assign_bytes, "hbm_achieved_gbs": achieved_gbs,
-                     "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x the maximum SM clock",
-                     "timing": "CUDA events on the library's stream around the assignment launch, mean over "
-                               f"{nprof} steps"},
         "clocks": clk,
         "gpu_launches": int(launches),
     }
+    pk32_step = out[0].clone()
 
     if rank == 0 and not a.no_extras:
-        # ---- plain FP64 GPU path on the same catalogue --------------------------------------------
+        # ---- plain FP64 GPU path on the same binned catalogue ---------------------------------------
         del ws
         torch.cuda.empty_cache()
         cfg64 = api.Config(ng=a.ng, box=a.box, order=4, interlace=True, prec="fp64")
@@ -614,9 +786,35 @@ def main():
         del ws64, binned, sorted_, offsets
         torch.cuda.empty_cache()
 
+        # ---- the FP32 step's error per k-bin against FP64 from the FP64 positions ------------------
+        # (positions, assignment, transforms and estimate together), and pk_power from the unsorted
+        # device FP64 positions (a1 + a2 + the step: preparation and binning inside the timed call)
+        pos64 = catalogs.zeldovich_torch(a.nside, a.box, RMS_DISP, seed=replica_seed(rank), device=dev)
+        pk64, _, n64 = api.power(pos64, cfg64)
+        rel = _rel_per_bin(pk32_step, pk64)
+        result["fp32_vs_fp64_per_bin"] = {
+            "reference": "pk_power in PK_FP64 from the FP64 positions (FP64 grids and transforms; oracle parity 1e-10)",
+            "max_rel": float(rel.max()), "median_rel": float(np.median(rel)), "per_bin": _sig(rel, 2)}
+        torch.cuda.empty_cache()
+        wsu = api.workspace(cfg, n, ffi.PK_WS_POWER, dev)
+        out_u = (torch.empty(cfg.nb, dtype=torch.float64, device=dev), torch.empty(cfg.nb, dtype=torch.float64, device=dev),
+                 torch.empty(cfg.nb, dtype=torch.int64, device=dev))
+
+        def unsorted_step():
+            ffi.check(ffi.lib().pk_power(api.ctypes.byref(cfg.c()), api._p(pos64), ffi.PK_POS_F64_XYZ, None, n,
+                                         api._p(out_u[0]), api._p(out_u[1]), api._p(out_u[2]), None, api._p(wsu),
+                                         wsu.numel(), api._stream(dev)))
+
+        ms_u = _time_cuda(unsorted_step, 3)
+        result["from_unsorted_device_positions"] = {
+            "ms_per_step": ms_u, "value": n / (ms_u * 1e-3), "unit": "particles/s",
+            "path": "pk_power from device FP64 xyz: a1 prepare + a2 counting sort by tile + the timed step's a3..a6"}
+        del wsu
+        torch.cuda.empty_cache()
+
         # ---- e2e through pk_power_host from pinned host FP64 positions ------------------------------
-        # the GPU reads the positions over the CPU-GPU link while preparing them, and P(k), kmean and
-        # the mode counts come back to pinned host memory, all inside the timed region
+        # the positions cross the CPU-GPU link in pieces while the previous piece is processed; P(k),
+        # kmean and the mode counts come back to pinned host memory, all inside the timed region
         wsp = api.workspace(cfg, n, ffi.PK_WS_POWER_HOST, dev)
         host_out = (torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True),
                     torch.empty(cfg.nb, dtype=torch.float64, pin_memory=True),
@@ -625,19 +823,17 @@ def main():
         def e2e_step():
             api.power_host(host64, cfg, ws=wsp, out=host_out, device=dev)
 
-        # context for e2e: the CPU-GPU link on a 2 GiB pinned copy, just before it. The link's throughput
-        # varies from run to run, so this is a sample, not a bound on e2e.
-        probe = torch.empty(1 << 28, dtype=torch.float64, device=dev)
-        probe_src = host64.view(-1)[: probe.numel()]
-        probe.copy_(probe_src, non_blocking=True)
+        # context for e2e: the link's rate for the whole catalogue in one copy, just before it, and where
+        # the pinned buffer's pages and the GPU sit
+        pos64.copy_(host64, non_blocking=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(2):
-            probe.copy_(probe_src, non_blocking=True)
+        pos64.copy_(host64, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        link_gbs = 2 * probe.numel() * 8 / (e0.elapsed_time(e1) * 1e-3) / 1e9
-        del probe, probe_src
+        link_gbs = 24.0 * n / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del pos64
+        torch.cuda.empty_cache()
 
         e2e_step()
         torch.cuda.synchronize()
@@ -650,25 +846,36 @@ def main():
         ms_e2e = e0.elapsed_time(e1) / ke
         result["e2e"] = {"value": n / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": 24 * n,
                          "d2h_bytes_per_step": 24 * cfg.nb, "ms_per_step": ms_e2e,
-                         "link_h2d_gbs_2gib_sample": link_gbs,
+                         "link_h2d_gbs_one_copy": link_gbs,
+                         "one_copy_ms": 24.0 * n / (link_gbs * 1e9) * 1e3,
+                         "gpu_work_ms": ms_u, "numa": numa_report(host64, local),
                          "path": "pk_power_host: pinned host FP64 xyz copied over the CPU-GPU link in 16 pieces by the "
                                  "copy engine, each prepared, binned and assigned while the next is in flight -> FFT -> "
                                  "estimate -> D2H of P(k), kmean, counts"}
         del wsp
         torch.cuda.empty_cache()
 
-        # ---- FP64 CPU oracle on a bounded sample ---------------------------------------------------
-        rng = np.random.default_rng(11)
-        idx = np.sort(rng.choice(n, size=1 << 16, replace=False))
-        sample = host64[torch.from_numpy(idx)].numpy()
-        rate, det = oracle_sample_rate(sample, n, a.box, a.ng, with_fft=True)
-        cores = len(os.sched_getaffinity(0))
+        # ---- other hot-path rows and the 256^3 accuracy table ---------------------------------------
         result["rows"] = measure_rows(dev, host64, a.box, alu_peak_tflops)
-        result["cpu_baseline"] = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
-                                  "sample": f"2^16 random particles of the catalogue assigned to both grids (single-threaded "
-                                            f"NumPy) + one full N_G={a.ng} FFT (scipy, {cores} workers), deconvolution and "
-                                            "binning; assignment time scaled linearly to the full catalogue",
-                                  **det}
+        result["rows"]["accuracy_c2"] = row_accuracy_c2(dev)
+
+        # ---- FP64 CPU oracle ----------------------------------------------------------------------
+        cores = len(os.sched_getaffinity(0))
+        rng = np.random.default_rng(11)
+        idx = np.sort(rng.choice(n, size=1 << 20, replace=False))
+        sample = host64[torch.from_numpy(idx)].numpy()
+        t0 = time.perf_counter()
+        _, t_assign, t_rest = oracle_power_parallel(sample, a.box, a.ng, 4, cores)
+        t_full = t_assign * (n / len(sample)) + t_rest
+        result["cpu_baseline"] = {"value": n / t_full, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"2^20 random particles of the catalogue assigned to both grids (the oracle's "
+                                            f"assignment over {cores} worker processes) + one full N_G={a.ng} FFT, "
+                                            "deconvolution and binning; assignment time scaled linearly to the full "
+                                            "catalogue (extrapolated)",
+                                  "t_assign_s": t_assign, "t_fft_estimate_s": t_rest, "sample_particles": len(sample),
+                                  "t_full_extrapolated_s": t_full, "wall_s": time.perf_counter() - t0}
+        if not a.no_oracle:
+            result["cpu_oracle_measured"] = measured_oracle_rows()
     elif not a.no_extras:
         result["e2e"] = None
     if rank == 0:

@@ -102,6 +102,13 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) { return static_cast
 __device__ __forceinline__ void red_shared(unsigned addr, int v) {
   asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
 }
+// 64-bit two's-complement reduction (the region of the heavy tiles, below).
+__device__ __forceinline__ void red_shared(unsigned addr, long long v) {
+  asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(addr), "l"(v));
+}
+// Window value (already at the region's fixed-point scale) to the region's integer type, to nearest.
+__device__ __forceinline__ int to_fixed(float v, int*) { return __float2int_rn(v); }
+__device__ __forceinline__ long long to_fixed(float v, long long*) { return __float2ll_rn(v); }
 
 // Packed pairs of FP32 values in one 64-bit register (PTX .f32x2 arithmetic, sm_100 family).
 typedef unsigned long long f2x;
@@ -325,6 +332,25 @@ __device__ __forceinline__ void flush_region(int* reg, int ngrid, int cx0, int c
   }
 }
 
+// The same for 64-bit regions (heavy tiles): rows of RS nodes, each node converted and added on its
+// own (these tiles are few).
+__device__ __forceinline__ void flush_region(long long* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
+                                             float inv_scale, float* g1, float* g2, int tid, int nthreads) {
+  const int nrows = ngrid * RS * RS;
+  for (int row = tid; row < nrows; row += nthreads) {
+    const int gi = row >= RS * RS ? 1 : 0, rr = row - gi * (RS * RS);
+    const int rx = rr / RS, ry = rr - rx * RS;
+    long long* src = reg + gi * RVOL + rr * RS;
+    float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
+#pragma unroll
+    for (int k = 0; k < RS; ++k) {
+      const long long v = src[k];
+      src[k] = 0;
+      if (v != 0) atomicAdd(gg + wrap(cz0 - 1 + k, ng), float(v) * inv_scale);
+    }
+  }
+}
+
 // Largest share of a particle's weight that one node receives: the peak of the one-dimensional
 // window cubed (CIC and NGP 1, TSC 3/4 per axis, PCS 2/3 per axis).
 template <int P>
@@ -336,7 +362,7 @@ __host__ __device__ constexpr float node_share() {
 // node_share x the tile's total |weight| B, and that bound x 2^e < 2^30 leaves room for the rounding
 // of every addition. With weights, B is summed by the block (red: one float per warp); the caller
 // synchronises before the first use.
-template <int P, bool W>
+template <int P, bool W, int BITS = 30>
 __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t end, float* red, int nwarp, int tid,
                                            int nthreads, float* scale, float* inv_scale) {
   float bound = float(end - beg);
@@ -353,8 +379,8 @@ __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t 
   }
   int ex;
   frexpf(fmaxf(bound * node_share<P>(), 1.0f), &ex);  // node bound < 2^ex
-  *scale = ldexpf(1.0f, 30 - ex);
-  *inv_scale = ldexpf(1.0f, ex - 30);
+  *scale = ldexpf(1.0f, BITS - ex);
+  *inv_scale = ldexpf(1.0f, ex - BITS);
 }
 
 // The first tile t + k stride (k >= 0) below ntiles whose population end - beg lies in [lo, hi], else
@@ -574,12 +600,13 @@ __host__ __device__ constexpr int cell_chunk() {
   return W ? 2048 : 4096;
 }
 
-template <bool W>
+// R: the region's integer type, int (32-bit fixed point) or long long (64-bit, the heavy tiles).
+template <bool W, typename R = int>
 struct CellSmem {
   int4 sp[cell_chunk<W>()];
   unsigned short perm[2][cell_chunk<W>()];
   int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
-  alignas(16) int reg[2][RVOL];
+  alignas(16) R reg[2][RVOL];
   unsigned short order[2][NKEY];  // non-empty key cells per grid, largest bucket first
   int cbin[2][CNT_BINS];
   int nitems[2];
@@ -593,8 +620,8 @@ struct CellSmem {
 // region (nodes key + S0 + 1 .. key + S0 + p per axis). The fixed-point scale (a power of two) rides
 // on the particle weight, so the window already holds fixed-point values; the next record is loaded
 // before the current one is accumulated.
-template <int P, bool W, int G>
-__device__ __forceinline__ void cell_key(const CellSmem<W>& S, int key, float wscale) {
+template <int P, bool W, typename R, int G>
+__device__ __forceinline__ void cell_key(const CellSmem<W, R>& S, int key, float wscale) {
   const int* ends = S.hist[G];
   const unsigned short* perm = S.perm[G];
   const int jb = key == 0 ? 0 : ends[key - 1], je = ends[key];
@@ -627,16 +654,17 @@ __device__ __forceinline__ void cell_key(const CellSmem<W>& S, int key, float ws
       float v[P];
       win.row(a, b, v);
 #pragma unroll
-      for (int c = 0; c < P; ++c) red_shared(base + 4u * ((a * RS + b) * RS + c), __float2int_rn(v[c]));
+      for (int c = 0; c < P; ++c)
+        red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * RS + c), to_fixed(v[c], static_cast<R*>(nullptr)));
     }
 }
 }  // namespace tiles
 
-template <int P, bool W>
+template <int P, bool W, typename R>
 __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     k_assign_cells(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
                    int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                   int64_t cat_stride, int min_count) {
+                   int64_t cat_stride, int64_t min_count, int64_t max_count) {
   using namespace tiles;
   constexpr int CH = cell_chunk<W>(), THREADS = CELL_THREADS, NWARP = THREADS / 32;
   constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
@@ -648,7 +676,8 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     toff += int64_t(cat) * ntile * ntile * ntile;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CellSmem<W>& S = *reinterpret_cast<CellSmem<W>*>(smem_raw);
+  CellSmem<W, R>& S = *reinterpret_cast<CellSmem<W, R>*>(smem_raw);
+  constexpr int BITS = sizeof(R) == 8 ? 62 : 30;  // node bound x scale < 2^BITS
   const int ngrid = interlace ? 2 : 1;
   const int ntiles = ntile * ntile * ntile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -659,15 +688,15 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
   for (int i = tid; i < 2 * RVOL; i += THREADS) (&S.reg[0][0])[i] = 0;  // flush_region clears it after each tile
   __syncthreads();
   unsigned parity = 0;
-  constexpr int64_t kAny = INT64_MAX;
-  // the block's tiles of at least min_count particles (the scatter takes the others)
-  for (int tile = next_tile(toff, n, blockIdx.x, gridDim.x, ntiles, min_count, kAny), nt = 0; tile < ntiles; tile = nt) {
-    nt = next_tile(toff, n, tile + int(gridDim.x), int(gridDim.x), ntiles, min_count, kAny);
+  // the block's tiles of min_count .. max_count particles (the scatter takes the sparser ones, the 64-bit
+  // instance of this kernel the heavier ones)
+  for (int tile = next_tile(toff, n, blockIdx.x, gridDim.x, ntiles, min_count, max_count), nt = 0; tile < ntiles; tile = nt) {
+    nt = next_tile(toff, n, tile + int(gridDim.x), int(gridDim.x), ntiles, min_count, max_count);
     const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
     const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
     float scale, inv_scale;
-    tile_scale<P, W>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+    tile_scale<P, W, BITS>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
     const float wscale = scale * weight_scale<P>();
     for (int64_t c0 = beg; c0 < end; c0 += CH) {
       const int m = int(min(int64_t(CH), end - c0));
@@ -826,11 +855,11 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         for (int r0 = 0; r0 < nitems; r0 += 2 * nt) {  // two rounds: ascending, then descending
           const int i0 = r0 + t, i1 = r0 + 2 * nt - 1 - t;
           if (gsel == 0) {
-            if (i0 < nitems) cell_key<P, W, 0>(S, order[i0], wscale);
-            if (i1 < nitems) cell_key<P, W, 0>(S, order[i1], wscale);
+            if (i0 < nitems) cell_key<P, W, R, 0>(S, order[i0], wscale);
+            if (i1 < nitems) cell_key<P, W, R, 0>(S, order[i1], wscale);
           } else {
-            if (i0 < nitems) cell_key<P, W, 1>(S, order[i0], wscale);
-            if (i1 < nitems) cell_key<P, W, 1>(S, order[i1], wscale);
+            if (i0 < nitems) cell_key<P, W, R, 1>(S, order[i0], wscale);
+            if (i1 < nitems) cell_key<P, W, R, 1>(S, order[i1], wscale);
           }
         }
       }
@@ -896,21 +925,43 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
   return cudaGetLastError();
 }
 
+// Tiles of at least this many particles accumulate their region in 64-bit fixed point. A 32-bit region
+// rounds each window at 2^-30 of the tile's node bound (node share x total weight), so a node much
+// lighter than the tile's heaviest possible node keeps fewer significant bits: in a tile that holds a
+// dense clump (10^5 particles in a few cells) the background nodes would keep ~1e-4 relative accuracy.
+// With 62 bits every node keeps the accuracy of the FP32 window sums. The heavy tiles are few (the
+// 1024^3 Zel'dovich benchmark catalogue averages 4096 particles per tile), and their kernel instance,
+// with twice the region memory, runs one block per SM.
+constexpr int64_t kHeavyTile = 16384;
+
+template <int P, bool W, typename R>
+static cudaError_t launch_cells_one(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
+                                    int64_t cat_stride, int64_t lo, int64_t hi) {
+  const int ntile = tiles_per_axis(ng);
+  const int ntiles = ntile * ntile * ntile;
+  const size_t smem = sizeof(tiles::CellSmem<W, R>);
+  int per_sm = 1;
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_cells<P, W, R>), tiles::CELL_THREADS, smem, &per_sm);
+  if (e != cudaSuccess) return e;
+  const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
+  k_assign_cells<P, W, R><<<blocks, tiles::CELL_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
+                                                                    cat_stride, lo, hi);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// The key-cell kernel over the tiles of at least cells_min_count(P) particles: 32-bit regions below
+// kHeavyTile particles, 64-bit regions from there on.
 template <int P, bool W>
 static cudaError_t launch_cells_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
                                    int64_t cat_stride) {
-  const int ntile = tiles_per_axis(ng);
-  const int ntiles = ntile * ntile * ntile;
-  const size_t smem = sizeof(tiles::CellSmem<W>);
-  int per_sm = 1;
-  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_cells<P, W>), tiles::CELL_THREADS, smem, &per_sm);
+  cudaError_t e = launch_cells_one<P, W, int>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride,
+                                              cells_min_count(P), kHeavyTile - 1);
   if (e != cudaSuccess) return e;
-  const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
-  k_assign_cells<P, W><<<blocks, tiles::CELL_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
-                                                                 cat_stride, cells_min_count(P));
-  count_launch();
-  return cudaGetLastError();
+  return launch_cells_one<P, W, long long>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, kHeavyTile,
+                                           INT64_MAX);
 }
 
 // Tiles of fewer than cells_min_count(P) particles: the scatter; the others: the key cells (NGP: all

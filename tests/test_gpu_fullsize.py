@@ -84,3 +84,18 @@ def test_fullsize_modes_and_power_from_the_gpu_grids(big):
     assert np.array_equal(cnt.cpu().numpy(), ref_cnt)
     assert _ref.rel(pk.cpu().numpy(), ref_pk) <= 1e-5  # measured: 3.1e-7 at most, 2.8e-7 typical
     assert _ref.rel(km.cpu().numpy(), ref_k) <= 1e-6
+
+
+def test_fullsize_fp32_error_per_bin_against_fp64_positions(big):
+    # The benchmark's FP32 P(k) (cell + FP32 offset records, FP32 grids and transforms) against FP64
+    # from the FP64 positions (FP64 grids and transforms, the mode that matches the oracle at 1e-10):
+    # the whole FP32 path's error, positions and assignment included, bin by bin, within the FP32 bar.
+    cfg, cells, g1, g2 = big
+    pk32, _, n32 = api.power_binned(api.bin_particles(cells, cfg), cfg)
+    pos = catalogs.zeldovich_torch(NSIDE, BOX, 4.0, seed=3, device=DEV)
+    pk64, _, n64 = api.power(pos, api.Config(ng=NG, box=BOX, order=4, interlace=True, prec="fp64"))
+    del pos
+    torch.cuda.empty_cache()
+    assert torch.equal(n32, n64)
+    rel = np.abs(pk32.cpu().numpy() / pk64.cpu().numpy() - 1.0)
+    assert rel.max() <= 1e-5, rel.max()

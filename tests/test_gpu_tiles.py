@@ -76,3 +76,29 @@ def test_scatter_across_runs_of_empty_tiles(order):
     centres = np.array([[10.0, 20.0, 30.0], [70.0, 90.0, 110.0], [120.0, 5.0, 60.0]])
     pos = np.concatenate([c + rng.normal(0.0, 3.0, (300, 3)) for c in centres]) % box
     _check(pos, box, ng, order)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_dense_clump_keeps_sparse_nodes_accurate(order):
+    # 10^5 particles in a 2^3-cell cube inside one 8^3-cell tile, next to a background of one particle
+    # per cell: the clump's tile also holds background nodes ~10^4 times smaller than its peak. Every
+    # node of value >= 0.25 (background nodes are ~1) must match the FP64 oracle relative to its OWN
+    # value at 1e-5 (FP32 sums of the window products reach a few 1e-7). Tiles of at least 16384
+    # particles are accumulated in 64-bit fixed point: at 32 bits the clump tile's rounding step
+    # (2^-15 of a particle's weight) would leave ~1e-4 relative error on its quarter-unit nodes. Lighter
+    # nodes of ordinary tiles carry the 32-bit step of their own tile (absolute, ~1e-6 for CIC at one
+    # particle per cell), which the other grid tests bound against the largest node.
+    box, ng = 64.0, 32
+    rng = np.random.default_rng(91)
+    base = catalogs.poisson(ng ** 3, box, seed=92)
+    clump = rng.uniform(0.0, 4.0, (100000, 3)) + np.array([20.0, 36.0, 52.0])  # cells 10-11, 18-19, 26-27
+    pos = np.concatenate([base, clump])
+    cfg = api.Config(ng=ng, box=box, order=order, prec="fp32")
+    api.device_error()
+    g1, g2 = api.assign(_t(pos), cfg)
+    assert api.device_error() == 0
+    r1, r2 = _ref.grids(pos, box, ng, order)
+    for g, r in ((g1.cpu().numpy(), r1), (g2.cpu().numpy(), r2)):
+        sel = np.abs(r) >= 0.25
+        rel = np.abs(g[sel] - r[sel]) / np.abs(r[sel])
+        assert rel.max() <= 1e-5, (rel.max(), np.argmax(rel))
