@@ -566,6 +566,34 @@ def row_e2e(dev, nside, ng, box, profile_range=False):
     return {"workload": f"pk_power_host, {n} particles from pinned host FP64 positions, N_G={ng}", "ms_per_call": ms}
 
 
+def row_ng1024(dev, pos64, box, hbm_peak):
+    """The benchmark catalogue on an N_G = 1024 grid (PCS + interlacing, FP32, binned records resident):
+    one particle per cell, so every tile goes to the per-particle scatter."""
+    import torch
+
+    from paper_1512_07295_gb300 import api, ffi
+
+    cfg = api.Config(ng=1024, box=box, order=4, interlace=True, prec="fp32")
+    n = pos64.shape[0]
+    cells = api.prepare(pos64, cfg)
+    binned = api.bin_particles(cells, cfg)
+    del cells
+    torch.cuda.empty_cache()
+    ws = api.workspace(cfg, n, ffi.PK_WS_POWER_BINNED, dev)
+    out = (torch.empty(cfg.nb, dtype=torch.float64, device=dev), torch.empty(cfg.nb, dtype=torch.float64, device=dev),
+           torch.empty(cfg.nb, dtype=torch.int64, device=dev))
+    ms = _time_cuda(lambda: api.power_binned(binned, cfg, ws=ws, out=out), 5, 2)
+    ng = 1024
+    nh = ng * ng * (ng // 2 + 1)
+    path_bytes = 16.0 * n + 2 * (4.0 * ng ** 3 + (4.0 * ng ** 3 + 8.0 * nh) + 8.0 * nh)
+    del ws, binned
+    torch.cuda.empty_cache()
+    return {"workload": f"{n} ZA particles, L={box:g} Mpc/h, N_G=1024, PCS+interlacing, FP32 binned records",
+            "ms_per_call": ms, "particles_per_s": n / (ms * 1e-3), "pk_per_s": 1e3 / ms,
+            "path_hbm_roofline": {"algorithmic_bytes": path_bytes, "achieved_gbs": path_bytes / (ms * 1e-3) / 1e9,
+                                  "peak_gbs": hbm_peak, "frac": path_bytes / (ms * 1e-3) / 1e9 / hbm_peak}}
+
+
 def measure_rows(dev, host64, big_box, alu_peak_tflops):
     """Times the other hot-path rows on their own workloads (one GB300)."""
     return {"bispectrum": row_bispectrum(dev, host64, big_box), "adjoint": row_adjoint(dev), "batch": row_batch(dev),
@@ -811,6 +839,7 @@ def main():
             "path": "pk_power from device FP64 xyz: a1 prepare + a2 counting sort by tile + the timed step's a3..a6"}
         del wsu
         torch.cuda.empty_cache()
+        ng1024 = row_ng1024(dev, pos64, a.box, hbm_peak) if a.nside ** 3 >= 1024 ** 3 else None
 
         # ---- e2e through pk_power_host from pinned host FP64 positions ------------------------------
         # the positions cross the CPU-GPU link in pieces while the previous piece is processed; P(k),
@@ -858,6 +887,8 @@ def main():
         # ---- other hot-path rows and the 256^3 accuracy table ---------------------------------------
         result["rows"] = measure_rows(dev, host64, a.box, alu_peak_tflops)
         result["rows"]["accuracy_c2"] = row_accuracy_c2(dev)
+        if ng1024 is not None:
+            result["rows"]["ng1024"] = ng1024
 
         # ---- FP64 CPU oracle ----------------------------------------------------------------------
         cores = len(os.sched_getaffinity(0))

@@ -304,10 +304,12 @@ pk_status pk_aliasing_residual(const pk_config* cfg, double* fres_mean_dev, doub
  * nmodes_dev, nbins entries each).
  * Scratch: a fixed file-scope device array of about 56 KB in the library (held by every GPU that
  * loads the library until the process exits); N above 1024 or nbins above 1024 is rejected with
- * PK_ESIZE. The first call on a device looks up that array's device address (with the device
- * current), so make the first call on each device before any stream capture. All calls share the
- * array: calls that overlap on the GPU (other streams, other host threads) race and give wrong
- * results; serialise them. Nothing is allocated. */
+ * PK_ESIZE (and N above 1024 fails validation first, PK_EINVAL). A call outside stream capture looks
+ * up that array's device address (with the device current), which also follows a device reset; a
+ * call under capture uses the address of the device's last call outside capture, so make one call
+ * on each device before capturing (a capture that starts with the device's first call returns
+ * PK_EINVAL). All calls share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and give wrong results; serialise them. Nothing is allocated. */
 pk_status pk_estimate_noalloc(const pk_config* cfg, const void* g1_dev, const void* g2_dev, double wsum, double w2sum,
                               double* pk_dev, double* kmean_dev, int64_t* nmodes_dev, void* stream);
 

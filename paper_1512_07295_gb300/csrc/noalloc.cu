@@ -29,19 +29,25 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device. In host code the symbol is only a
-// host-side stand-in; the first call on each device looks the real address up (with that device
-// current) and caches it.
-pk_status noalloc_scratch(void** out) {
+// host-side stand-in, so the address is looked up (with that device current) on every call that is
+// not being captured into a CUDA graph, which also picks up a new address after a device reset; a
+// call under capture uses the address found by the device's last call outside capture (a capture may
+// not start with the first call on a device).
+pk_status noalloc_scratch(cudaStream_t s, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(PK_EINVAL, "device index %d out of range", dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
     g_noalloc_addr[dev] = p;
+  } else if (!g_noalloc_addr[dev]) {
+    return fail(PK_EINVAL, "pk_estimate_noalloc: make one call on device %d before capturing it into a graph", dev);
   }
   *out = g_noalloc_addr[dev];
   return PK_OK;
@@ -66,7 +72,7 @@ extern "C" pk_status pk_estimate_noalloc(const pk_config* cfg, const void* g1_de
   if (!(wsum > 0.0) || !(w2sum > 0.0)) return fail(PK_EINVAL, "wsum and w2sum must be > 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* base = nullptr;
-  if ((st = noalloc_scratch(&base)) != PK_OK) return st;
+  if ((st = noalloc_scratch(s, &base)) != PK_OK) return st;
   char* b = static_cast<char*>(base);
   void* tables = b;
   double* bin_sum = reinterpret_cast<double*>(b + kTablesBytes);
