@@ -10,6 +10,7 @@
 // (q1 in a, q2 in b) with q1 + q2 = m is C_ab(m) = (1/N_c) sum_x F_a F_b e^{-2 pi i m.x/N}, an
 // integer computed in FP64 (error far below 1/2) and rounded; N_tri = sum_{m in c} C_ab(m) in int64.
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "host.cuh"
@@ -212,6 +213,178 @@ __global__ void __launch_bounds__(kTriWarps * 32) k_triple_warp(const R* __restr
   __syncthreads();
   for (int t = threadIdx.x; t < ntri; t += blockDim.x) atomicAdd(&S[t], double(shi[t]) + double(slo[t]));
 }
+
+// The FP32 triple product for up to kRegShells shells with the triangles in registers. The triangle
+// list of kRegShells shells is fixed at compile time (kTri, the order of make_triangles; the list of
+// fewer shells is its first ntri entries), warp w of a block owns its triangles w kRegWarpTri ..
+// (w + 1) kRegWarpTri - 1, and the code of each warp is instantiated for its own triangles, so that the
+// shell indices are constants and the values of a point live in registers. Lane l takes the points l,
+// l + 32, l + 64, l + 96 of each staged tile and, per point, reads each shell its triangles use once from
+// shared memory (about 104 reads per point over the 8 warps, against one or more per triangle in
+// k_triple_warp), forms I_a I_b once per shell pair and adds I_a I_b I_c to the triangle's running sum.
+// Every kFlushTiles tiles the lane sums are added across the warp by a transposing butterfly (five
+// exchange steps leave lane l with the sums of the warp's triangles 2 l and 2 l + 1) and added to the
+// block's compensated FP32 pair of those triangles, as in k_triple_warp.
+constexpr int kRegShells = 16;
+constexpr int kRegWarpTri = 64;
+constexpr int kRegWarps = 8;
+constexpr int kRegTri = kRegWarps * kRegWarpTri;
+
+struct TriTable {
+  int n = 0;
+  int a[kRegTri] = {};
+  int b[kRegTri] = {};
+  int c[kRegTri] = {};
+  constexpr TriTable() {
+    for (int x = 0; x < kRegShells; ++x)
+      for (int y = 0; y <= x; ++y)
+        for (int z = 0; z <= y; ++z)
+          if (x <= y + z + 1) {
+            a[n] = x;
+            b[n] = y;
+            c[n] = z;
+            ++n;
+          }
+  }
+};
+constexpr TriTable kTri{};
+static_assert(kTri.n <= kRegTri, "the triangles of kRegShells shells must fit the warps' registers");
+
+template <int W, int J>
+__device__ __forceinline__ void reg_tri(const float (&v)[kRegShells], float& pab, float (&acc)[kRegWarpTri]) {
+  constexpr int t = W * kRegWarpTri + J;
+  if constexpr (t < kTri.n) {
+    constexpr int a = kTri.a[t], b = kTri.b[t], c = kTri.c[t];
+    if constexpr (J == 0 || a != kTri.a[t - 1] || b != kTri.b[t - 1]) pab = v[a] * v[b];
+    acc[J] = fmaf(pab, v[c], acc[J]);
+  }
+}
+
+template <int W, int... J>
+__device__ __forceinline__ void reg_tris(const float (&v)[kRegShells], float& pab, float (&acc)[kRegWarpTri],
+                                         std::integer_sequence<int, J...>) {
+  (reg_tri<W, J>(v, pab, acc), ...);
+}
+
+// The four points of lane l in the staged tile: col = vals + l, shell s of point l + 32 i at
+// col[s kRow + 32 i]. Reads of shells that warp W's triangles do not use are dead and dropped.
+template <int W>
+__device__ __forceinline__ void reg_tile(const float* col, float (&acc)[kRegWarpTri]) {
+#pragma unroll 1
+  for (int i = 0; i < kTX / 32; ++i) {
+    float v[kRegShells];
+#pragma unroll
+    for (int s = 0; s < kRegShells; ++s) v[s] = col[s * kRow + 32 * i];
+    float pab = 0.f;
+    reg_tris<W>(v, pab, acc, std::make_integer_sequence<int, kRegWarpTri>{});
+  }
+}
+
+// One exchange step of the transposing butterfly over n running sums: the lane with bit o clear keeps
+// the first half (adding its partner's first half), the other the second half.
+template <int N>
+__device__ __forceinline__ void fold_half(float (&acc)[kRegWarpTri], int lane, int o) {
+  const bool up = (lane & o) != 0;
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) {
+    const float lo = acc[j], hi = acc[j + N / 2];
+    const float send = up ? lo : hi;
+    const float keep = up ? hi : lo;
+    acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+}
+
+// cp.async groups: the 4-byte copies of a tile are one group (a copy of 0 source bytes writes a zero).
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(kRegWarps * 32, 2) k_triple_reg(const float* __restrict__ fields, int ng, int nshells,
+                                                                  int64_t buf_stride, int ntri, double* __restrict__ S) {
+  static_assert(kRegWarps * 32 == 2 * kTX, "two threads per staged point");
+  __shared__ float shi[kRegTri], slo[kRegTri];
+  __shared__ __align__(16) float vals[2][kRegShells * kRow];  // tile i in vals[i & 1], tile i + 1 arriving in the other
+  for (int t = threadIdx.x; t < kRegTri; t += blockDim.x) {
+    shi[t] = 0.f;
+    slo[t] = 0.f;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[kRegWarpTri];
+#pragma unroll
+  for (int j = 0; j < kRegWarpTri; ++j) acc[j] = 0.f;
+  const int64_t npts = int64_t(ng) * ng * ng;
+  const int64_t ntiles = (npts + kTX - 1) / kTX;
+  // staging: thread t copies point t mod kTX of the tile for the shells t / kTX + 2 u. The point's
+  // row (y, z plane index x / N) and column advance by a fixed step per tile of the block.
+  const int k = threadIdx.x % kTX, s0 = threadIdx.x / kTX;
+  const int64_t rows = int64_t(ng) * ng;
+  int64_t row = (int64_t(blockIdx.x) * kTX + k) / ng;
+  int col = int((int64_t(blockIdx.x) * kTX + k) - row * ng);
+  const int64_t step = int64_t(gridDim.x) * kTX;
+  const int64_t step_row = step / ng;
+  const int step_col = int(step - step_row * ng);
+  const float* fbase = fields + int64_t(s0) * buf_stride;
+  const int64_t fstride = 2 * buf_stride;
+  const unsigned sbase = static_cast<unsigned>(__cvta_generic_to_shared(&vals[0][s0 * kRow + k]));
+  constexpr unsigned kBufBytes = kRegShells * kRow * sizeof(float);
+  auto stage = [&](unsigned dst) {
+    const bool in_pt = row < rows;
+    const float* src = fbase + row * (ng + 2) + col;
+#pragma unroll
+    for (int u = 0; u < kRegShells / 2; ++u) {
+      const bool in = in_pt && s0 + 2 * u < nshells;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst + u * 2 * kRow * 4), "l"(in ? src : fields),
+                   "r"(in ? 4 : 0)
+                   : "memory");
+      src += fstride;
+    }
+    cp_async_commit();
+    row += step_row;
+    col += step_col;
+    if (col >= ng) {
+      col -= ng;
+      ++row;
+    }
+  };
+  if (blockIdx.x < ntiles) stage(sbase);
+  const bool busy = warp * kRegWarpTri < ntri;  // warp-uniform
+  int since_flush = 0, buf = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();  // tile in vals[buf] for every thread; every warp done with vals[buf ^ 1]
+    if (tile + gridDim.x < ntiles) stage(sbase + (buf ^ 1) * kBufBytes);
+    if (busy) {
+      const float* col = vals[buf] + lane;
+      switch (warp) {
+        case 0: reg_tile<0>(col, acc); break;
+        case 1: reg_tile<1>(col, acc); break;
+        case 2: reg_tile<2>(col, acc); break;
+        case 3: reg_tile<3>(col, acc); break;
+        case 4: reg_tile<4>(col, acc); break;
+        case 5: reg_tile<5>(col, acc); break;
+        case 6: reg_tile<6>(col, acc); break;
+        default: reg_tile<7>(col, acc); break;
+      }
+    }
+    if (++since_flush == kFlushTiles || tile + gridDim.x >= ntiles) {
+      // every warp folds (an idle warp's sums are zero): a fold under the warp's condition costs
+      // the compiler dozens of registers
+      since_flush = 0;
+      fold_half<64>(acc, lane, 16);
+      fold_half<32>(acc, lane, 8);
+      fold_half<16>(acc, lane, 4);
+      fold_half<8>(acc, lane, 2);
+      fold_half<4>(acc, lane, 1);
+      const int t0 = warp * kRegWarpTri + 2 * lane;
+      comp_add(&shi[t0], &slo[t0], acc[0]);
+      comp_add(&shi[t0 + 1], &slo[t0 + 1], acc[1]);
+#pragma unroll
+      for (int j = 0; j < kRegWarpTri; ++j) acc[j] = 0.f;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntri; t += blockDim.x) atomicAdd(&S[t], double(shi[t]) + double(slo[t]));
+}
+static_assert(kRegWarps == 8, "k_triple_reg dispatches eight warps");
 
 template <typename R>
 __global__ void __launch_bounds__(512) k_triple(const R* __restrict__ fields, int ng, int nshells, int64_t buf_stride,
@@ -456,7 +629,12 @@ pk_status pk_bispectrum(const pk_config* cfg, const void* delta_k_dev, int32_t s
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "shell filter");
   if ((st = exec_plan(L.plan, L.kind, L.fields, L.work, s)) != PK_OK) return st;
   if ((e = cudaMemsetAsync(L.S, 0, sizeof(double) * ntri, s)) != cudaSuccess) return cuda_fail(e, "memset");
-  if (ntri <= kTriWarps * kWarpTri && nshells <= kTriMaxShells) {  // lanes over points, warps over triangles
+  if (!dbl && nshells <= kRegShells) {  // triangles in registers
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_reg, kRegWarps * 32, 0) != cudaSuccess) per_sm = 1;
+    k_triple_reg<<<num_sms() * std::max(per_sm, 1), kRegWarps * 32, 0, s>>>(static_cast<const float*>(L.fields), ng, nshells,
+                                                                             pc, ntri, L.S);
+  } else if (ntri <= kTriWarps * kWarpTri && nshells <= kTriMaxShells) {  // lanes over points, warps over triangles
     const size_t wsmem = size_t(2 * ntri) * (dbl ? 8 : 4) + size_t((ntri + 3) / 4) * 16 + size_t(nshells) * kRow * (dbl ? 8 : 4);
     int per_sm = 1;
     if (dbl) {
@@ -474,26 +652,20 @@ pk_status pk_bispectrum(const pk_config* cfg, const void* delta_k_dev, int32_t s
       k_triple_warp<float><<<num_sms() * std::max(per_sm, 1), kTriWarps * 32, wsmem, s>>>(
           static_cast<const float*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S);
     }
-    count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "triple product");
-    const double vol = cfg->box * cfg->box * cfg->box;
-    const double scale = vol * vol / (double(ng) * ng * ng);
-    k_bisp_final<<<(ntri + 255) / 256, 256, 0, s>>>(L.S, reinterpret_cast<const long long*>(counts_dev), ntri, scale, B_dev);
-    count_launch();
-    e = cudaGetLastError();
-    return e == cudaSuccess ? PK_OK : cuda_fail(e, "bispectrum final");
+  } else {  // one thread per triangle
+    const size_t smem = size_t(nshells) * kRow * (dbl ? 8 : 4) + size_t(ntri) * 8;
+    if (smem > 48 * 1024) {
+      e = dbl ? ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple<double>), smem)
+              : ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple<float>), smem);
+      if (e != cudaSuccess) return cuda_fail(e, "triple smem");
+    }
+    const int tblocks = num_sms() * 2;
+    if (dbl)
+      k_triple<double><<<tblocks, 512, smem, s>>>(static_cast<const double*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S);
+    else
+      k_triple<float><<<tblocks, 512, smem, s>>>(static_cast<const float*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S);
   }
-  const size_t smem = size_t(nshells) * kRow * (dbl ? 8 : 4) + size_t(ntri) * 8;
-  if (smem > 48 * 1024) {
-    e = dbl ? ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple<double>), smem)
-            : ensure_dynamic_smem(reinterpret_cast<const void*>(k_triple<float>), smem);
-    if (e != cudaSuccess) return cuda_fail(e, "triple smem");
-  }
-  const int tblocks = num_sms() * 2;
-  if (dbl)
-    k_triple<double><<<tblocks, 512, smem, s>>>(static_cast<const double*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S);
-  else
-    k_triple<float><<<tblocks, 512, smem, s>>>(static_cast<const float*>(L.fields), ng, nshells, pc, L.tri, ntri, L.S); count_launch();
+  count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "triple product");
   const double vol = cfg->box * cfg->box * cfg->box;
   const double scale = vol * vol / (double(ng) * ng * ng);

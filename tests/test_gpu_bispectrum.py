@@ -33,8 +33,10 @@ def test_triangle_counts_brute_force_tiny():
     assert np.array_equal(counts, brute)
 
 
-# 5 shells run the pair-organised triple product; 23 shells (276 shell pairs) the per-triangle one
-@pytest.mark.parametrize("ng,lo,w,ns", [(32, 1, 2, 5), (72, 1, 1, 23)])
+# Up to 16 shells the FP32 triple product keeps the triangles in registers (16 shells: all 508 of them;
+# 11 shells on N = 36: a prefix of the list, tiles of 128 points that cross rows, a ragged last tile)
+# and the FP64 one takes warps over triangles; 23 shells (276 shell pairs) run the per-triangle kernel.
+@pytest.mark.parametrize("ng,lo,w,ns", [(32, 1, 2, 5), (36, 0, 1, 11), (64, 1, 1, 16), (72, 1, 1, 23)])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
 def test_bispectrum_matches_oracle(prec, tol, ng, lo, w, ns):
     box = 200.0
