@@ -55,11 +55,12 @@ def parse():
     ap.add_argument("--box", type=float, default=2000.0)
     ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
-    ap.add_argument("--only-row", choices=["adjoint", "batch", "bispectrum", "direct", "multigrid", "e2e"], default=None,
+    ap.add_argument("--only-row", choices=["adjoint", "batch", "bispectrum", "direct", "multigrid", "e2e", "ng1024"], default=None,
                     help="time one secondary row on its own workload and print it (no P(k) step)")
     ap.add_argument("--ds-nside", type=int, default=128, help="--only-row direct: particles per side")
     ap.add_argument("--ds-ng", type=int, default=128, help="--only-row direct: grid size")
     ap.add_argument("--batch-cats", type=int, default=512, help="--only-row batch: catalogues in the batch")
+    ap.add_argument("--row-ng", type=int, default=1024, help="--only-row ng1024: grid size (1024 for the row itself)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the measured CPU oracle rows (c1 and c2 configurations)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
@@ -572,14 +573,15 @@ def row_e2e(dev, nside, ng, box, profile_range=False):
     return {"workload": f"pk_power_host, {n} particles from pinned host FP64 positions, N_G={ng}", "ms_per_call": ms}
 
 
-def row_ng1024(dev, pos64, box, hbm_peak):
+def row_ng1024(dev, pos64, box, hbm_peak, ng=1024):
     """The benchmark catalogue on an N_G = 1024 grid (PCS + interlacing, FP32, binned records resident):
-    one particle per cell, so every tile goes to the per-particle scatter."""
+    one particle per cell, so every tile goes to the per-particle scatter. (ng: another grid size for
+    a smaller case of the same kind, e.g. 256^3 particles on N_G = 256 for a profile.)"""
     import torch
 
     from paper_1512_07295_gb300 import api, ffi
 
-    cfg = api.Config(ng=1024, box=box, order=4, interlace=True, prec="fp32")
+    cfg = api.Config(ng=ng, box=box, order=4, interlace=True, prec="fp32")
     n = pos64.shape[0]
     cells = api.prepare(pos64, cfg)
     binned = api.bin_particles(cells, cfg)
@@ -589,15 +591,33 @@ def row_ng1024(dev, pos64, box, hbm_peak):
     out = (torch.empty(cfg.nb, dtype=torch.float64, device=dev), torch.empty(cfg.nb, dtype=torch.float64, device=dev),
            torch.empty(cfg.nb, dtype=torch.int64, device=dev))
     ms = _time_cuda(lambda: api.power_binned(binned, cfg, ws=ws, out=out), 5, 2)
-    ng = 1024
+    lib = ffi.lib()
+    lib.pk_profile_enable(1)
+    stages = np.zeros(5)
+    buf = (ctypes.c_double * 5)()
+    for _ in range(3):
+        api.power_binned(binned, cfg, ws=ws, out=out)
+        lib.pk_profile_read(ctypes.cast(buf, ctypes.c_void_p), 5)
+        stages += np.array(list(buf)) / 3
+    lib.pk_profile_enable(0)
     nh = ng * ng * (ng // 2 + 1)
     path_bytes = 16.0 * n + 2 * (4.0 * ng ** 3 + (4.0 * ng ** 3 + 8.0 * nh) + 8.0 * nh)
     del ws, binned
     torch.cuda.empty_cache()
-    return {"workload": f"{n} ZA particles, L={box:g} Mpc/h, N_G=1024, PCS+interlacing, FP32 binned records",
+    return {"workload": f"{n} ZA particles, L={box:g} Mpc/h, N_G={ng}, PCS+interlacing, FP32 binned records",
             "ms_per_call": ms, "particles_per_s": n / (ms * 1e-3), "pk_per_s": 1e3 / ms,
+            "stages_ms": {"grid_clear": float(stages[1]), "assign": float(stages[2]), "fft": float(stages[3]),
+                          "estimate": float(stages[4])},
             "path_hbm_roofline": {"algorithmic_bytes": path_bytes, "achieved_gbs": path_bytes / (ms * 1e-3) / 1e9,
                                   "peak_gbs": hbm_peak, "frac": path_bytes / (ms * 1e-3) / 1e9 / hbm_peak}}
+
+
+def row_ng1024_only(dev, a):
+    """The N_G = 1024 row on its own: the catalogue generated on the GPU, then row_ng1024."""
+    from paper_1512_07295_gb300 import catalogs
+
+    pos = catalogs.zeldovich_torch(a.nside, a.box, RMS_DISP, seed=replica_seed(0), device=dev)
+    return row_ng1024(dev, pos, a.box, float((measured_peaks() or {}).get("hbm_gbs", 6800.0)), a.row_ng)
 
 
 def measure_rows(dev, host64, big_box, alu_peak_tflops):
@@ -690,7 +710,8 @@ def main():
                "bispectrum": lambda: row_bispectrum_only(dev, a),
                "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng),
                "multigrid": lambda: row_multigrid(dev),
-               "e2e": lambda: row_e2e(dev, a.nside, a.ng, a.box, a.profile_range)}[a.only_row]()
+               "e2e": lambda: row_e2e(dev, a.nside, a.ng, a.box, a.profile_range),
+               "ng1024": lambda: row_ng1024_only(dev, a)}[a.only_row]()
         if rank == 0:
             print(json.dumps({"row": a.only_row, **row}), flush=True)
         return

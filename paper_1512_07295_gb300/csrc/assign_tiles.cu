@@ -406,6 +406,17 @@ __device__ __forceinline__ int next_tile(const int64_t* toff, int64_t n, int t, 
 // Sorting a piece by key cell costs a fixed amount per piece (histograms, scans, the count order);
 // on sparse tiles that fixed cost dominates. There, each thread adds its particles' p^3 weights per
 // grid straight into the fixed-point region with integer shared atomics instead.
+//
+// Bank order. The region's rows are RS = 12 nodes and its planes 144 = 16 (mod 32) nodes, so the
+// stencil node (a, b, c) of a particle whose first node has index q lies in bank
+// (q + 16 a + 12 b + c) mod 32: two particles' additions meet in one bank at every step exactly when
+// their q agree mod 32, and never otherwise. A piece's particles are therefore bucketed per grid by
+// q mod 32, and round k gives lane l the k-th particle of bucket l, so the 32 additions of every
+// warp instruction go to 32 different banks. For even p the stencil's planes pair up (a, a ^ 1), and
+// a lane that adds plane a ^ 1 at step a moves all its additions by 16 banks: buckets are then taken
+// mod 16, lanes l and l + 16 share bucket l mod 16 (its particles 2 k and 2 k + 1 in round k), and
+// the lane whose bank half differs from its particle's flips the planes. Rounds then number the
+// largest bucket's size over two instead of over one.
 constexpr int SCATTER_THREADS = 256;
 
 // Pieces of the scatter are staged in two buffers: the next piece is copied while this one is used.
@@ -418,17 +429,52 @@ template <bool W>
 struct ScatterSmem {
   int4 sp[2][scatter_chunk<W>()];
   alignas(16) int reg[2][2][RVOL];  // two tiles' regions in turn: one is flushed while the next is filled
-  float red[SCATTER_THREADS / 32];
+  float red[2][SCATTER_THREADS / 32];
   unsigned long long mbar[2];
   float sw[2][W ? scatter_chunk<W>() : 1];
+  // the piece's buckets per grid: counts (then cleared), sizes and offsets, the records in bucket order
+  int cnt[2][32];
+  int nr[2][32];
+  int off[2][32];
+  int rounds[2];
+  unsigned short list[2][scatter_chunk<W>()];
 };
+static_assert(RVOL % 32 == 0, "each region starts in bank 0");
+
+// Index of the region node where grid G's stencil of a particle at local cell (lx, ly, lz) + f starts.
+template <int P, int G>
+__device__ __forceinline__ int stencil_origin(int lx, int ly, int lz, float fx, float fy, float fz) {
+  float t;
+  const int kx = lx + grid_key<P, G>(fx, &t), ky = ly + grid_key<P, G>(fy, &t), kz = lz + grid_key<P, G>(fz, &t);
+  return ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
+}
+
+// Fixed-point value of one addition. For PCS and TSC the product is rounded to an integer by the FMA
+// that adds 1.5 2^23 (the sum then lies in [2^23, 2^24], where the float's unit is 1, so its low
+// mantissa bits hold the integer; exact for |v| <= 2^22, which scatter_scale guarantees), which runs
+// on the FMA pipe instead of the conversion unit's quarter rate.
+template <int P>
+__device__ __forceinline__ int fixed_product(float x, float y) {
+  if constexpr (P >= 3) {
+    return __float_as_int(fmaf(x, y, 12582912.0f)) - 0x4B400000;
+  } else {
+    return __float2int_rn(x * y);
+  }
+}
+
+// Buckets of the bank order: 16 for even p (plane pairs), 32 otherwise; lanes per bucket.
+template <int P>
+__host__ __device__ constexpr int bank_buckets() {
+  return P % 2 == 0 ? 16 : 32;
+}
 
 // Adds one particle's p^3 weights on grid G to that grid's region (scale: the weight times the
 // region's fixed-point scale). Region nodes of the stencil: key + S0 + 1 .. key + S0 + p per axis.
-// (Rounding by adding 1.5 2^23 instead of a conversion would cap the scale at 2^21 per unit weight,
-// too coarse on sparse tiles: their nodes then miss the FP32 grid tolerance.)
+// lane: the caller's lane; for even p the planes are taken in pairs swapped when the lane's bank half
+// differs from the stencil origin's (the bank order above).
 template <int P, int G>
-__device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc) {
+__device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc,
+                                                 int lane) {
   float tx, ty, tz;
   const int kx = lx + grid_key<P, G>(fx, &tx), ky = ly + grid_key<P, G>(fy, &ty), kz = lz + grid_key<P, G>(fz, &tz);
   float wx[P], wy[P], wz[P];
@@ -437,25 +483,87 @@ __device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int l
   weights<P>(tz, wz);
 #pragma unroll
   for (int a = 0; a < P; ++a) wx[a] *= sc;
-  const unsigned base = smem_u32(reg + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1);
+  const int q = ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
+  unsigned base_even = smem_u32(reg + q), base_odd = base_even;
+  if constexpr (P % 2 == 0) {
+    if ((q ^ lane) & 16) {  // step a adds plane a ^ 1
 #pragma unroll
-  for (int a = 0; a < P; ++a)
+      for (int a = 0; a < P; a += 2) {
+        const float t = wx[a];
+        wx[a] = wx[a + 1];
+        wx[a + 1] = t;
+      }
+      base_even += 4u * RS * RS;
+      base_odd -= 4u * RS * RS;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    const unsigned base = (a & 1) ? base_odd : base_even;
 #pragma unroll
     for (int b = 0; b < P; ++b) {
       const float xy = wx[a] * wy[b];
 #pragma unroll
-      for (int c = 0; c < P; ++c) red_shared(base + 4u * ((a * RS + b) * RS + c), __float2int_rn(xy * wz[c]));
+      for (int c = 0; c < P; ++c) red_shared(base + 4u * ((a * RS + b) * RS + c), fixed_product<P>(xy, wz[c]));
     }
+  }
+}
+
+// Fixed-point scale 2^e of a sparse tile's region: tile_scale's bound (node share x total |weight| x
+// 2^e < 2^30) and, where fixed_product rounds by the 1.5 2^23 addition, node share x max |weight| x
+// 2^e <= 2^22 for every single addition. With weights the block reduces the sum and the maximum
+// (red: two floats per warp); the caller synchronises before the first use.
+template <int P, bool W>
+__device__ __forceinline__ void scatter_scale(const float* w, int64_t beg, int64_t end, float (*red)[SCATTER_THREADS / 32],
+                                              int tid, float* scale, float* inv_scale) {
+  constexpr int NW = SCATTER_THREADS / 32;
+  float bound = float(end - beg), wmax = 1.0f;
+  if (W) {
+    float a = 0.0f, m = 0.0f;
+    for (int64_t i = beg + tid; i < end; i += SCATTER_THREADS) {
+      a += fabsf(w[i]);
+      m = fmaxf(m, fabsf(w[i]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = a;
+      red[1][tid >> 5] = m;
+    }
+    __syncthreads();
+    bound = 0.0f;
+    wmax = 0.0f;
+    for (int q = 0; q < NW; ++q) {
+      bound += red[0][q];
+      wmax = fmaxf(wmax, red[1][q]);
+    }
+    bound *= 1.0001f;  // the FP32 sum's rounding
+  }
+  int ex;
+  frexpf(fmaxf(bound * node_share<P>(), 1.0f), &ex);  // node bound < 2^ex
+  int e = 30 - ex;
+  if (P >= 3) {
+    int ex1;
+    frexpf(fmaxf(wmax * node_share<P>(), 1e-30f), &ex1);  // one addition < 2^ex1
+    e = min(e, 22 - ex1);
+  }
+  *scale = ldexpf(1.0f, e);
+  *inv_scale = ldexpf(1.0f, -e);
 }
 
 }  // namespace tiles
 
 // a3, FP32, direct scatter: a block takes tiles in a grid-stride sequence and their pieces in
-// order, the copy of the next piece overlapping the use of the current one; particles are spread over
-// the lanes of a warp q = ceil(m / 32) records apart (different cells, so a warp's atomics seldom meet
-// on one node). Tiles use two regions in turn: a finished tile's region is added to the grids (and
-// cleared) by flush_region in the same phase as the scatter of the next piece, so one block barrier
-// per piece separates all uses of the staging buffers and regions.
+// order, the copy of the next piece overlapping the use of the current one. Per piece: each record's
+// stencil origin on each grid is bucketed by bank (counts with shared atomics, which also give the
+// record's place in its bucket); one warp per grid turns the counts into offsets; the records are
+// listed in bucket order; then the warps take rounds (grid 1's, then grid 2's), lane l of round k
+// scattering the k-th record of bucket l (even p: record 2 k + l / 16 of bucket l mod 16). Tiles use two regions in turn: a finished tile's region is
+// added to the grids (and cleared) by flush_region in the bucket phase of the next piece. The block
+// barrier at the top of each piece separates every use of the staging buffers, buckets and regions.
 template <int P, bool W>
 __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
@@ -479,6 +587,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   }
   for (int i = tid; i < 2 * 2 * RVOL; i += THREADS) (&S.reg[0][0][0])[i] = 0;
+  if (tid < 64) (&S.cnt[0][0])[tid] = 0;
   __syncthreads();
   // the block's pieces: (tile, first record c0, tile's records [beg, end))
   struct Piece {
@@ -539,7 +648,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
       cx0 = tx * T;
       cy0 = ty * T;
       cz0 = tz * T;
-      tile_scale<P, W>(w, cur.beg, cur.end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+      scatter_scale<P, W>(w, cur.beg, cur.end, S.red, tid, &scale, &inv_scale);
     }
     if (pending) {
       flush_region(&S.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
@@ -547,23 +656,75 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     }
     const int4* sp = S.sp[buf];
     const float* sw = S.sw[buf];
-    int* reg0 = S.reg[rb][0];
-    int* reg1 = S.reg[rb][1];
-    const int q = (m + 31) / 32;
-    for (int i = tid; i < 32 * q; i += THREADS) {
-      const int j = (i & 31) * q + (i >> 5);
-      if (j >= m) continue;
+    // buckets: stencil origin mod NB per grid, and the record's place in its bucket
+    constexpr int PER = (CH + THREADS - 1) / THREADS, NB = bank_buckets<P>(), LPB = 32 / NB;
+    int qb[PER][2], rk[PER][2];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int j = tid + u * THREADS;
+      qb[u][0] = -1;
+      if (j < m) {
+        const int4 r = sp[j];
+        const uint32_t cell = uint32_t(r.x);
+        const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
+        if ((cell >> 30) != 0 || unsigned(lx) >= unsigned(T) || unsigned(ly) >= unsigned(T) || unsigned(lz) >= unsigned(T)) {
+          raise_err(PK_DERR_CELLRANGE);
+          continue;
+        }
+        const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
+        qb[u][0] = stencil_origin<P, 0>(lx, ly, lz, fx, fy, fz) & (NB - 1);
+        rk[u][0] = atomicAdd(&S.cnt[0][qb[u][0]], 1);
+        if (interlace) {
+          qb[u][1] = stencil_origin<P, 1>(lx, ly, lz, fx, fy, fz) & (NB - 1);
+          rk[u][1] = atomicAdd(&S.cnt[1][qb[u][1]], 1);
+        }
+      }
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp < ngrid) {  // warp g: grid g's bucket offsets, sizes and round count; counts cleared
+      const int c = lane < NB ? S.cnt[warp][lane] : 0;
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      int mx = (c + LPB - 1) / LPB;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane < NB) {
+        S.off[warp][lane] = incl - c;
+        S.nr[warp][lane] = c;
+        S.cnt[warp][lane] = 0;
+      }
+      if (lane == 0) S.rounds[warp] = mx;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (qb[u][0] < 0) continue;
+      const unsigned short j = static_cast<unsigned short>(tid + u * THREADS);
+      S.list[0][S.off[0][qb[u][0]] + rk[u][0]] = j;
+      if (interlace) S.list[1][S.off[1][qb[u][1]] + rk[u][1]] = j;
+    }
+    __syncthreads();
+    // rounds: grid 1's rounds, then grid 2's, dealt to the warps in turn
+    const int r0 = S.rounds[0], rtot = r0 + (interlace ? S.rounds[1] : 0);
+    for (int item = warp; item < rtot; item += NWARP) {
+      const int g = item < r0 ? 0 : 1;
+      const int k = (g ? item - r0 : item) * LPB + lane / NB, bkt = lane % NB;
+      if (k >= S.nr[g][bkt]) continue;
+      const int j = S.list[g][S.off[g][bkt] + k];
       const int4 r = sp[j];
       const uint32_t cell = uint32_t(r.x);
       const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-      if ((cell >> 30) != 0 || unsigned(lx) >= unsigned(T) || unsigned(ly) >= unsigned(T) || unsigned(lz) >= unsigned(T)) {
-        raise_err(PK_DERR_CELLRANGE);
-        continue;
-      }
       const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
       const float sc = (W ? sw[j] : 1.0f) * weight_scale<P>() * scale;
-      scatter_particle<P, 0>(reg0, lx, ly, lz, fx, fy, fz, sc);
-      if (interlace) scatter_particle<P, 1>(reg1, lx, ly, lz, fx, fy, fz, sc);
+      if (g == 0)
+        scatter_particle<P, 0>(S.reg[rb][0], lx, ly, lz, fx, fy, fz, sc, lane);
+      else
+        scatter_particle<P, 1>(S.reg[rb][1], lx, ly, lz, fx, fy, fz, sc, lane);
     }
     if (cur.c0 + CH >= cur.end) {  // last piece of the tile: its region is flushed with the next piece
       pending = true;

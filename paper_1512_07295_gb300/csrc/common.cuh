@@ -186,6 +186,20 @@ __device__ __forceinline__ int bin_of(long long v4, int lo2, int w2, int nbins) 
   return b < nbins ? b : -1;
 }
 
+// bin_of in 32-bit integers, for 4|n|^2 < 2^31 (N <= 1024) and bin edges whose squares fit 32 bits
+// (bin_lo2 + (nbins + 1) bin_w2 <= 46340); r = sqrt(v4) from the caller, inv_w2 = 1 / bin_w2.
+__device__ __forceinline__ int bin_of32(int v4, float r, int lo2, int w2, float inv_w2, int nbins) {
+  if (v4 == 0) return -1;
+  int b = int(floorf((r - float(lo2)) * inv_w2));
+  if (b < 0) b = 0;
+  int e = lo2 + b * w2;
+  while (b > 0 && e * e > v4) { --b; e -= w2; }
+  if (e * e > v4) return -1;
+  int e1 = e + w2;
+  while (e1 * e1 <= v4) { ++b; e1 += w2; if (b >= nbins) return -1; }
+  return b < nbins ? b : -1;
+}
+
 // Fixed-point scale 2^F of the deterministic grids, F = 62 - ceil(log2(sum |w|)): no node can hold
 // more than the total mass, so the int64 sums cannot overflow.
 __device__ __forceinline__ float fixed_scale(double total) {

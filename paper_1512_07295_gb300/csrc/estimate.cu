@@ -46,6 +46,9 @@ __global__ void k_tables(R* tab, int ng, int order) {
 
 size_t estimate_table_bytes(int ng, bool dbl) { return size_t(3) * ng * (dbl ? 8 : 4); }
 
+// Shared-memory tables of k_estimate: the three global tables, the normalised i_z window and V.
+__host__ __device__ inline size_t estimate_smem_table_bytes(int ng, size_t elem) { return ((size_t(4) * ng + 1) * elem + 15) / 16 * 16; }
+
 // Per-warp private bin accumulators (single pass, non-deterministic mode). Within one warp item the
 // bins of the run ends are distinct (|n| grows with i_z), so a warp updates its own copy without
 // atomics: FP32 mode keeps each sum as an FP32 pair (value, compensation; Neumaier's summation,
@@ -62,6 +65,10 @@ struct PrivBin<float> {
   }
   __device__ __forceinline__ static double value(float2 acc) { return double(acc.x) + double(acc.y); }
   __device__ __forceinline__ static float2 zero() { return make_float2(0.0f, 0.0f); }
+  __device__ __forceinline__ static void merge(float2& acc, float2 o) {
+    add(acc, o.x);
+    acc.y += o.y;
+  }
 };
 template <>
 struct PrivBin<double> {
@@ -69,11 +76,12 @@ struct PrivBin<double> {
   __device__ __forceinline__ static void add(double& acc, double v) { acc += v; }
   __device__ __forceinline__ static double value(double acc) { return acc; }
   __device__ __forceinline__ static double zero() { return 0.0; }
+  __device__ __forceinline__ static void merge(double& acc, double o) { acc += o; }
 };
 constexpr int kEstWarps = 8;  // 256 threads
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, const C2<R>* __restrict__ G2,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 3) k_estimate(const C2<R>* __restrict__ G1, const C2<R>* __restrict__ G2,
                                                   const R* __restrict__ tab_g, EstimateArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {
@@ -86,14 +94,22 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
     a.bin_cnt += int64_t(cat) * a.nbins;
   }
   const int ng = a.ng;
-  R* tab = reinterpret_cast<R*>(smem_raw);  // 3 ng
-  unsigned char* bins_raw = smem_raw + ((size_t(3) * ng * sizeof(R) + 15) / 16) * 16;
+  R* tab = reinterpret_cast<R*>(smem_raw);  // 1/W, cos, sin (3 ng); 1/W times the norm (ng); V
+  unsigned char* bins_raw = smem_raw + estimate_smem_table_bytes(ng, sizeof(R));
   double* s_sum = reinterpret_cast<double*>(bins_raw);
   double* s_k = s_sum + a.nbins;
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_k + a.nbins);
   PrivBin<R>* pbin = reinterpret_cast<PrivBin<R>*>(bins_raw);  // [kEstWarps][nbins] when a.priv
   unsigned* pcnt = reinterpret_cast<unsigned*>(pbin + size_t(kEstWarps) * a.nbins);
-  for (int i = threadIdx.x; i < 3 * ng; i += blockDim.x) tab[i] = tab_g[i];
+  {
+    // the normalisation 1 / (2 sum w) (1 / sum w without interlacing) rides on the i_z window, and V
+    // is kept beside the tables: both are read from shared memory in the loop, not recomputed
+    const R wsum0 = R(a.wsums[0]);
+    const R norm0 = a.interlace ? R(0.5) / wsum0 : R(1) / wsum0;
+    for (int i = threadIdx.x; i < 3 * ng; i += blockDim.x) tab[i] = tab_g[i];
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) tab[3 * ng + i] = tab_g[i] * norm0;
+    if (threadIdx.x == 0) tab[4 * ng] = R(a.box * a.box * a.box);
+  }
   if (a.priv) {
     for (int i = threadIdx.x; i < kEstWarps * a.nbins; i += blockDim.x) {
       pbin[i].sum = PrivBin<R>::zero();
@@ -114,9 +130,11 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
   const int lane = threadIdx.x & 31;
   const int half = ng / 2;
   const int lz = half + 1;
-  const double vol = a.box * a.box * a.box;
-  const R wsum = R(a.wsums[0]);
-  const R norm = a.interlace ? R(0.5) / wsum : R(1) / wsum;
+  // bin edges whose squares fit 32 bits take the 32-bit bin test
+  const bool small_bins = int64_t(a.bin_lo2) + int64_t(a.nbins + 1) * a.bin_w2 <= 46340;
+  const float inv_w2 = 1.0f / float(a.bin_w2);
+  const R* winvz = tab + 3 * ng;
+  const R* vol = tab + 4 * ng;
   const int64_t rows = int64_t(ng) * ng;
   const int64_t warp_g = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -126,6 +144,18 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
   // current item is processed so that two loads per lane are in flight
   const int nslots = int(rows) * lz;  // <= 1024^2 * 513 < 2^31
   const int items = (nslots + 31) / 32;
+  // the item's first slot as (i_x, i_y, i_z), advanced by the grid stride of 32 nwarps slots per item
+  const int stride_slots = 32 * int(nwarps);
+  const int srow = stride_slots / lz, siz = stride_slots - srow * lz;
+  const int srow_x = srow / ng, srow_y = srow - srow_x * ng;
+  int iz0, iy0, ix0;
+  {
+    const int b0 = int(warp_g) * 32;
+    const int r0 = b0 / lz;
+    iz0 = b0 - r0 * lz;
+    ix0 = r0 / ng;
+    iy0 = r0 - ix0 * ng;
+  }
   C2<R> g1n = {R(0), R(0)}, g2n = {R(0), R(0)};
   if (warp_g < items) {
     const int sl = int(warp_g) * 32 + lane;
@@ -146,28 +176,41 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
         }
       }
     }
-    // this lane's slot: row (i_x, i_y) and i_z, from the item's first row by carrying along the rows
+    // this lane's slot: row (i_x, i_y) and i_z, from the item's first slot by carrying along the rows
     const int base = item * 32;
-    const int row0 = base / lz;
-    int iz = base - row0 * lz + lane, rseg = 0;
+    int iz = iz0 + lane, rseg = 0;
     while (iz >= lz) {
       iz -= lz;
       ++rseg;
     }
-    int ix = row0 / ng, iy = row0 - ix * ng;
-    iy += rseg;
+    int ix = ix0, iy = iy0 + rseg;
     while (iy >= ng) {
       iy -= ng;
       ++ix;
     }
-    const int row = row0 + rseg;
-    const int nx = signed_mode(ix, ng), ny = signed_mode(iy, ng);
+    const int row = ix * ng + iy;
+    ix = min(ix, ng - 1);  // lanes past the last slot read a valid table entry and are not used
+    {  // the next item's first slot
+      iz0 += siz;
+      int carry = 0;
+      if (iz0 >= lz) {
+        iz0 -= lz;
+        carry = 1;
+      }
+      iy0 += srow_y + carry;
+      ix0 += srow_x;
+      while (iy0 >= ng) {
+        iy0 -= ng;
+        ++ix0;
+      }
+    }
+    const int nx = signed_mode(ix, ng), ny = signed_mode(iy, ng);  // |n|^2 <= 3 (N/2)^2 < 2^20
     const R wxy = winv[ix] * winv[iy];
     const C2<R> phx = {pc[ix], ps[ix]}, phy = {pc[iy], ps[iy]};
     const C2<R> phxy = cmul(phx, phy);
     // partner phase per axis: conjugate except on the Nyquist slot
     const C2<R> phxy_p = cmul(ix == half ? phx : conj(phx), iy == half ? phy : conj(phy));
-    const long long nxy2 = (long long)nx * nx + (long long)ny * ny;
+    const int nxy2 = nx * nx + ny * ny;
     {
       const bool live = base + lane < nslots;
       int b = -1;
@@ -175,11 +218,11 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
       int cnt = 0;
       if (live) {
         const int nz = iz == half ? -half : iz;
-        const long long n2 = nxy2 + (long long)nz * nz;
+        const int n2 = nxy2 + nz * nz;
         const int64_t idx = int64_t(row) * lz + iz;
         C2<R> d = {R(0), R(0)};
         if (n2 != 0) {
-          const R c = norm * wxy * winv[iz];
+          const R c = wxy * winvz[iz];
           const C2<R> g1 = g1c;
           const bool partner = iz > 0 && iz < half;
           C2<R> dp;
@@ -194,7 +237,9 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
             d = {g1.x * c, g1.y * c};
             dp = conj(d);
           }
-          b = bin_of(4 * n2, a.bin_lo2, a.bin_w2, a.nbins);
+          const float rn = sqrtf(float(n2));
+          b = small_bins ? bin_of32(4 * n2, 2.0f * rn, a.bin_lo2, a.bin_w2, inv_w2, a.nbins)
+                         : bin_of(4 * (long long)n2, a.bin_lo2, a.bin_w2, a.nbins);
           if (b >= 0) {
             val = d.x * d.x + d.y * d.y;
             cnt = 1;
@@ -202,8 +247,8 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
               val += dp.x * dp.x + dp.y * dp.y;
               cnt = 2;
             }
-            val *= R(vol);
-            ks = R(cnt) * sqrt(R(n2));
+            val *= *vol;
+            ks = R(cnt) * (sizeof(R) == 4 ? R(rn) : sqrt(R(n2)));
           }
         }
         if (dout) dout[idx] = d;
@@ -218,18 +263,18 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
       const bool end = lane == 31 || bnext != b;
       if (a.det_pass == 0) {
         R sv = val, sk = ks;
-        int sc = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const R tv = __shfl_up_sync(0xffffffffu, sv, o);
           const R tk = __shfl_up_sync(0xffffffffu, sk, o);
-          const int tc = __shfl_up_sync(0xffffffffu, sc, o);
           if (lane - o >= start) {
             sv += tv;
             sk += tk;
-            sc += tc;
           }
         }
+        // the run's mode count: its lanes with one mode plus its lanes with two
+        const unsigned run = ((2u << lane) - 1u) & ~((1u << start) - 1u);
+        const int sc = __popc(__ballot_sync(0xffffffffu, cnt >= 1) & run) + __popc(__ballot_sync(0xffffffffu, cnt == 2) & run);
         if (!a.priv && end && b >= 0) {
           atomicAdd(&s_sum[b], double(sv));
           atomicAdd(&s_k[b], double(sk));
@@ -286,14 +331,17 @@ __global__ void __launch_bounds__(256) k_estimate(const C2<R>* __restrict__ G1, 
   if (a.nbins == 0) return;
   for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
     if (a.priv) {
-      double v = 0.0, k = 0.0;
+      // the warps' pairs combined in their own precision, converted to FP64 once (FP64 and
+      // conversions to it run at a small fraction of the FP32 rate on this GPU)
+      auto vs = PrivBin<R>::zero(), ks = PrivBin<R>::zero();
       unsigned long long c = 0;
       for (int q = 0; q < kEstWarps; ++q) {
         const PrivBin<R>& pb = pbin[q * a.nbins + i];
-        v += PrivBin<R>::value(pb.sum);
-        k += PrivBin<R>::value(pb.k);
+        PrivBin<R>::merge(vs, pb.sum);
+        PrivBin<R>::merge(ks, pb.k);
         c += pcnt[q * a.nbins + i];
       }
+      const double v = PrivBin<R>::value(vs), k = PrivBin<R>::value(ks);
       if (c) {
         atomicAdd(&a.bin_sum[i], v);
         atomicAdd(&a.bin_k[i], k);
@@ -359,14 +407,18 @@ cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, c
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   EstimateArgs b = a;
-  const size_t tab_bytes = ((size_t(3) * a.ng * sizeof(R) + 15) / 16) * 16;
+  const size_t tab_bytes = estimate_smem_table_bytes(a.ng, sizeof(R));
   const size_t priv_bytes = size_t(kEstWarps) * a.nbins * (sizeof(PrivBin<R>) + sizeof(unsigned));
   // private bins while they fit in a quarter of an SM's shared memory (nbins up to ~640 in FP32 mode)
   b.priv = (a.det_pass == 0 && priv_bytes <= 56 * 1024) ? 1 : 0;
   const size_t smem = tab_bytes + (b.priv ? priv_bytes : size_t(a.nbins) * 24);
   if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_estimate<R>), smem)) != cudaSuccess) return e;
   const int64_t rows = int64_t(a.ng) * a.ng;
-  const int bx = int(std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, std::max<int64_t>(1, int64_t(num_sms()) * 8 / a.ncat))));
+  // every block resident at once (the loop is grid-stride; a second partial wave would idle SMs)
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<R>, kEstWarps * 32, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int bx = int(std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, std::max<int64_t>(1, int64_t(num_sms()) * per_sm / a.ncat))));
   const dim3 blocks(bx, a.ncat);
   k_estimate<R><<<blocks, kEstWarps * 32, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
                                                      static_cast<const R*>(tables), b); count_launch();
