@@ -107,13 +107,6 @@ cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const 
   return launch_direct<double>(order, pos, fmt, w, n, ng, box, interlace, g1, g2, ldz, s);
 }
 
-// FP32 grids by the direct scatter (global FP32 atomics): the FP32 path of orders 5 and 6, whose
-// stencils the tiled kernels' shared-memory regions do not hold.
-cudaError_t launch_assign_direct_f32(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
-                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s) {
-  return launch_direct<float>(order, pos, fmt, w, n, ng, box, interlace, g1, g2, ldz, s);
-}
-
 // ---- tiled shared-memory path ---------------------------------------------------------------------
 
 template <typename Acc>

@@ -351,11 +351,33 @@ __device__ __forceinline__ void flush_region(long long* reg, int ngrid, int cx0,
   }
 }
 
+// Any region (edge E, first node O below the tile) added to the grids node by node and cleared: the
+// regions of orders 5 and 6 (rows of 14 nodes).
+template <int E, int O, typename R>
+__device__ __forceinline__ void flush_region_edge(R* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
+                                                  float inv_scale, float* g1, float* g2, int tid, int nthreads) {
+  constexpr int VOL = E * E * E;
+  const int nrows = ngrid * E * E;
+  for (int row = tid; row < nrows; row += nthreads) {
+    const int gi = row >= E * E ? 1 : 0, rr = row - gi * (E * E);
+    const int rx = rr / E, ry = rr - rx * E;
+    R* src = reg + gi * VOL + rr * E;
+    float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - O + rx, ng)) * ng + wrap(cy0 - O + ry, ng)) * ldz;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const R v = src[k];
+      src[k] = 0;
+      if (v != 0) atomicAdd(gg + wrap(cz0 - O + k, ng), float(v) * inv_scale);
+    }
+  }
+}
+
 // Largest share of a particle's weight that one node receives: the peak of the one-dimensional
 // window cubed (CIC and NGP 1, TSC 3/4 per axis, PCS 2/3 per axis).
 template <int P>
 __host__ __device__ constexpr float node_share() {
-  return P == 4 ? 8.0f / 27.0f : (P == 3 ? 27.0f / 64.0f : 1.0f);
+  // orders 5 and 6: centre values 115/192 and 11/20 of the one-dimensional B-spline, cubed, rounded up
+  return P == 4 ? 8.0f / 27.0f : (P == 3 ? 27.0f / 64.0f : (P == 5 ? 0.2149f : (P == 6 ? 0.1664f : 1.0f)));
 }
 
 // Fixed-point scale 2^e of a tile's region: no node (nor any partial sum of one) exceeds
@@ -425,10 +447,35 @@ __host__ __device__ constexpr int scatter_chunk() {
   return 512;
 }
 
-template <bool W>
+// Scatter region per order: nodes -1 .. T+2 of the tile (edge RS, first node one below the tile) up to
+// PCS; orders 5 and 6 reach two nodes below and four above a cell on either grid: nodes -2 .. T+3.
+template <int P>
+__host__ __device__ constexpr int region_edge() {
+  return P >= 5 ? T + 6 : RS;
+}
+template <int P>
+__host__ __device__ constexpr int region_off() {
+  return P >= 5 ? 2 : 1;
+}
+template <int P>
+__host__ __device__ constexpr int region_vol() {
+  return region_edge<P>() * region_edge<P>() * region_edge<P>();
+}
+
+// A finished scatter tile's region into the grids: rows of 12 nodes up to PCS, node by node beyond.
+template <int P, typename R>
+__device__ __forceinline__ void flush_scatter_region(R* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
+                                                     float inv_scale, float* g1, float* g2, int tid, int nthreads) {
+  if constexpr (P >= 5)
+    flush_region_edge<region_edge<P>(), region_off<P>()>(reg, ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, nthreads);
+  else
+    flush_region(reg, ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, nthreads);
+}
+
+template <int P, bool W, typename R = int>
 struct ScatterSmem {
   int4 sp[2][scatter_chunk<W>()];
-  alignas(16) int reg[2][2][RVOL];  // two tiles' regions in turn: one is flushed while the next is filled
+  alignas(16) R reg[2][2][region_vol<P>()];  // two tiles' regions in turn: one is flushed while the next is filled
   float red[2][SCATTER_THREADS / 32];
   unsigned long long mbar[2];
   float sw[2][W ? scatter_chunk<W>() : 1];
@@ -439,72 +486,110 @@ struct ScatterSmem {
   int rounds[2];
   unsigned short list[2][scatter_chunk<W>()];
 };
-static_assert(RVOL % 32 == 0, "each region starts in bank 0");
+
+// First stencil node on one axis of grid G, relative to the tile origin, for orders 5 and 6 (from the
+// B-spline's own stencil start), with the weights.
+template <int P, int G>
+__device__ __forceinline__ int high_start(int l, float f, float* w) {
+  float f2 = f;
+  int d = 0;
+  if constexpr (G == 1) d = half_shift(f, &f2);
+  return l + d + bspline<P>(f2, w);
+}
 
 // Index of the region node where grid G's stencil of a particle at local cell (lx, ly, lz) + f starts.
 template <int P, int G>
 __device__ __forceinline__ int stencil_origin(int lx, int ly, int lz, float fx, float fy, float fz) {
-  float t;
-  const int kx = lx + grid_key<P, G>(fx, &t), ky = ly + grid_key<P, G>(fy, &t), kz = lz + grid_key<P, G>(fz, &t);
-  return ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
+  constexpr int E = region_edge<P>(), O = region_off<P>();
+  if constexpr (P >= 5) {
+    float w[P];
+    const int sx = high_start<P, G>(lx, fx, w), sy = high_start<P, G>(ly, fy, w), sz = high_start<P, G>(lz, fz, w);
+    return ((sx + O) * E + sy + O) * E + sz + O;
+  } else {
+    float t;
+    const int kx = lx + grid_key<P, G>(fx, &t), ky = ly + grid_key<P, G>(fy, &t), kz = lz + grid_key<P, G>(fz, &t);
+    return ((kx + s0<P>() + O) * E + ky + s0<P>() + O) * E + kz + s0<P>() + O;
+  }
 }
 
 // Fixed-point value of one addition. For PCS and TSC the product is rounded to an integer by the FMA
 // that adds 1.5 2^23 (the sum then lies in [2^23, 2^24], where the float's unit is 1, so its low
 // mantissa bits hold the integer; exact for |v| <= 2^22, which scatter_scale guarantees), which runs
 // on the FMA pipe instead of the conversion unit's quarter rate.
-template <int P>
-__device__ __forceinline__ int fixed_product(float x, float y) {
-  if constexpr (P >= 3) {
+template <int P, typename R>
+__device__ __forceinline__ R fixed_product(float x, float y) {
+  if constexpr (sizeof(R) == 8) {
+    return __float2ll_rn(x * y);
+  } else if constexpr (P >= 3) {
     return __float_as_int(fmaf(x, y, 12582912.0f)) - 0x4B400000;
   } else {
     return __float2int_rn(x * y);
   }
 }
 
-// Buckets of the bank order: 16 for even p (plane pairs), 32 otherwise; lanes per bucket.
+// Buckets of the bank order: 16 for even p on the 12-node region (plane pairs 16 banks apart), 32
+// otherwise; lanes per bucket.
 template <int P>
 __host__ __device__ constexpr int bank_buckets() {
-  return P % 2 == 0 ? 16 : 32;
+  return (P % 2 == 0 && region_edge<P>() == 12) ? 16 : 32;
 }
 
 // Adds one particle's p^3 weights on grid G to that grid's region (scale: the weight times the
 // region's fixed-point scale). Region nodes of the stencil: key + S0 + 1 .. key + S0 + p per axis.
 // lane: the caller's lane; for even p the planes are taken in pairs swapped when the lane's bank half
 // differs from the stencil origin's (the bank order above).
-template <int P, int G>
-__device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc,
+template <int P, int G, typename R>
+__device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc,
                                                  int lane) {
-  float tx, ty, tz;
-  const int kx = lx + grid_key<P, G>(fx, &tx), ky = ly + grid_key<P, G>(fy, &ty), kz = lz + grid_key<P, G>(fz, &tz);
-  float wx[P], wy[P], wz[P];
-  weights<P>(tx, wx);
-  weights<P>(ty, wy);
-  weights<P>(tz, wz);
+  if constexpr (P >= 5) {  // orders 5 and 6: the B-spline weights and stencil start per axis
+    constexpr int E = region_edge<P>(), O = region_off<P>();
+    float wx[P], wy[P], wz[P];
+    const int sx = high_start<P, G>(lx, fx, wx), sy = high_start<P, G>(ly, fy, wy), sz = high_start<P, G>(lz, fz, wz);
 #pragma unroll
-  for (int a = 0; a < P; ++a) wx[a] *= sc;
-  const int q = ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
-  unsigned base_even = smem_u32(reg + q), base_odd = base_even;
-  if constexpr (P % 2 == 0) {
-    if ((q ^ lane) & 16) {  // step a adds plane a ^ 1
+    for (int a = 0; a < P; ++a) wx[a] *= sc;
+    const unsigned base = smem_u32(reg + ((sx + O) * E + sy + O) * E + sz + O);
 #pragma unroll
-      for (int a = 0; a < P; a += 2) {
-        const float t = wx[a];
-        wx[a] = wx[a + 1];
-        wx[a + 1] = t;
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b) {
+        const float xy = wx[a] * wy[b];
+#pragma unroll
+        for (int c = 0; c < P; ++c)
+          red_shared(base + unsigned(sizeof(R)) * ((a * E + b) * E + c), fixed_product<P, R>(xy, wz[c]));
       }
-      base_even += 4u * RS * RS;
-      base_odd -= 4u * RS * RS;
+  } else {
+    float tx, ty, tz;
+    const int kx = lx + grid_key<P, G>(fx, &tx), ky = ly + grid_key<P, G>(fy, &ty), kz = lz + grid_key<P, G>(fz, &tz);
+    float wx[P], wy[P], wz[P];
+    weights<P>(tx, wx);
+    weights<P>(ty, wy);
+    weights<P>(tz, wz);
+#pragma unroll
+    for (int a = 0; a < P; ++a) wx[a] *= sc;
+    const int q = ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
+    unsigned base_even = smem_u32(reg + q), base_odd = base_even;
+    if constexpr (bank_buckets<P>() == 16) {
+      if ((q ^ lane) & 16) {  // step a adds plane a ^ 1
+#pragma unroll
+        for (int a = 0; a < P; a += 2) {
+          const float t = wx[a];
+          wx[a] = wx[a + 1];
+          wx[a + 1] = t;
+        }
+        base_even += unsigned(sizeof(R)) * RS * RS;
+        base_odd -= unsigned(sizeof(R)) * RS * RS;
+      }
     }
-  }
 #pragma unroll
-  for (int a = 0; a < P; ++a) {
-    const unsigned base = (a & 1) ? base_odd : base_even;
+    for (int a = 0; a < P; ++a) {
+      const unsigned base = (a & 1) ? base_odd : base_even;
 #pragma unroll
-    for (int b = 0; b < P; ++b) {
-      const float xy = wx[a] * wy[b];
+      for (int b = 0; b < P; ++b) {
+        const float xy = wx[a] * wy[b];
 #pragma unroll
-      for (int c = 0; c < P; ++c) red_shared(base + 4u * ((a * RS + b) * RS + c), fixed_product<P>(xy, wz[c]));
+        for (int c = 0; c < P; ++c)
+          red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * RS + c), fixed_product<P, R>(xy, wz[c]));
+      }
     }
   }
 }
@@ -513,7 +598,7 @@ __device__ __forceinline__ void scatter_particle(int* reg, int lx, int ly, int l
 // 2^e < 2^30) and, where fixed_product rounds by the 1.5 2^23 addition, node share x max |weight| x
 // 2^e <= 2^22 for every single addition. With weights the block reduces the sum and the maximum
 // (red: two floats per warp); the caller synchronises before the first use.
-template <int P, bool W>
+template <int P, bool W, typename R>
 __device__ __forceinline__ void scatter_scale(const float* w, int64_t beg, int64_t end, float (*red)[SCATTER_THREADS / 32],
                                               int tid, float* scale, float* inv_scale) {
   constexpr int NW = SCATTER_THREADS / 32;
@@ -544,8 +629,8 @@ __device__ __forceinline__ void scatter_scale(const float* w, int64_t beg, int64
   }
   int ex;
   frexpf(fmaxf(bound * node_share<P>(), 1.0f), &ex);  // node bound < 2^ex
-  int e = 30 - ex;
-  if (P >= 3) {
+  int e = (sizeof(R) == 8 ? 62 : 30) - ex;
+  if (P >= 3 && sizeof(R) == 4) {
     int ex1;
     frexpf(fmaxf(wmax * node_share<P>(), 1e-30f), &ex1);  // one addition < 2^ex1
     e = min(e, 22 - ex1);
@@ -564,11 +649,11 @@ __device__ __forceinline__ void scatter_scale(const float* w, int64_t beg, int64
 // scattering the k-th record of bucket l (even p: record 2 k + l / 16 of bucket l mod 16). Tiles use two regions in turn: a finished tile's region is
 // added to the grids (and cleared) by flush_region in the bucket phase of the next piece. The block
 // barrier at the top of each piece separates every use of the staging buffers, buckets and regions.
-template <int P, bool W>
-__global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
+template <int P, bool W, typename R>
+__global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) == 8) ? 2 : 4)
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
                      int64_t n, int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                     int64_t cat_stride, int max_count) {
+                     int64_t cat_stride, int64_t min_count, int64_t max_count) {
   using namespace tiles;
   constexpr int CH = scatter_chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
   {
@@ -578,7 +663,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     toff += int64_t(cat) * ntile * ntile * ntile;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ScatterSmem<W>& S = *reinterpret_cast<ScatterSmem<W>*>(smem_raw);
+  ScatterSmem<P, W, R>& S = *reinterpret_cast<ScatterSmem<P, W, R>*>(smem_raw);
   const int ngrid = interlace ? 2 : 1;
   const int ntiles = ntile * ntile * ntile;
   const int tid = threadIdx.x;
@@ -586,7 +671,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar[tid]));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   }
-  for (int i = tid; i < 2 * 2 * RVOL; i += THREADS) (&S.reg[0][0][0])[i] = 0;
+  for (int i = tid; i < 2 * 2 * region_vol<P>(); i += THREADS) (&S.reg[0][0][0])[i] = 0;
   if (tid < 64) (&S.cnt[0][0])[tid] = 0;
   __syncthreads();
   // the block's pieces: (tile, first record c0, tile's records [beg, end))
@@ -594,12 +679,12 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     int tile;
     int64_t beg, end, c0;
   };
-  // next piece of this tile, else the first of the block's next tile of 1 .. max_count particles
+  // next piece of this tile, else the first of the block's next tile of min_count .. max_count particles
   // (called by every thread alike)
   auto advance = [&](Piece& c) -> bool {
     c.c0 += CH;
     if (c.c0 < c.end) return true;
-    c.tile = next_tile(toff, n, c.tile + int(gridDim.x), int(gridDim.x), ntiles, 1, max_count);
+    c.tile = next_tile(toff, n, c.tile + int(gridDim.x), int(gridDim.x), ntiles, min_count, max_count);
     if (c.tile >= ntiles) return false;
     c.beg = max(toff[c.tile], int64_t(0));
     c.end = min(toff[c.tile + 1], n);
@@ -648,10 +733,10 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
       cx0 = tx * T;
       cy0 = ty * T;
       cz0 = tz * T;
-      scatter_scale<P, W>(w, cur.beg, cur.end, S.red, tid, &scale, &inv_scale);
+      scatter_scale<P, W, R>(w, cur.beg, cur.end, S.red, tid, &scale, &inv_scale);
     }
     if (pending) {
-      flush_region(&S.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+      flush_scatter_region<P>(&S.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
       pending = false;
     }
     const int4* sp = S.sp[buf];
@@ -739,7 +824,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, 4)
     has_next = advance(nxt);
   }
   __syncthreads();
-  if (pending) flush_region(&S.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+  if (pending) flush_scatter_region<P>(&S.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
 }
 
 // ---- cells (dense tiles) ---------------------------------------------------------------------------
@@ -1069,19 +1154,19 @@ static int cells_min_count(int order) {
   }
 }
 
-template <int P, bool W>
+template <int P, bool W, typename R = int>
 static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                      bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
-                                     int64_t cat_stride) {
+                                     int64_t cat_stride, int64_t lo, int64_t hi) {
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
-  const size_t smem = sizeof(tiles::ScatterSmem<W>);
+  const size_t smem = sizeof(tiles::ScatterSmem<P, W, R>);
   int per_sm = 1;
-  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W>), tiles::SCATTER_THREADS, smem, &per_sm);
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W, R>), tiles::SCATTER_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
-  k_assign_scatter<P, W><<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
-                                                                     cat_stride, cells_min_count(P) - 1);
+  k_assign_scatter<P, W, R><<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2,
+                                                                        ldz, cat_stride, lo, hi);
   count_launch();
   return cudaGetLastError();
 }
@@ -1126,17 +1211,30 @@ static cudaError_t launch_cells_pw(const pk_cellpos* p, const float* w, const in
 }
 
 // Tiles of fewer than cells_min_count(P) particles: the scatter; the others: the key cells (NGP: all
-// on the scatter). Each kernel skips the other's tiles, so both launch whatever the populations.
+// on the scatter). Orders 5 and 6 take every tile on the scatter (a register window of p^3 = 125 or
+// 216 nodes does not fit), with 64-bit regions from kHeavyTile particles on. Each kernel skips the
+// other's tiles, so all launch whatever the populations.
 template <int P>
 static cudaError_t launch_tiles_p(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
                                   float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
-  cudaError_t e = w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
-                    : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-  if (e != cudaSuccess) return e;
-  if constexpr (P > 1)
-    e = w ? launch_cells_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
-          : launch_cells_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-  return e;
+  if constexpr (P >= 5) {
+    cudaError_t e = w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, kHeavyTile - 1)
+                      : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, kHeavyTile - 1);
+    if (e != cudaSuccess) return e;
+    return w ? launch_scatter_pw<P, true, long long>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, kHeavyTile,
+                                                     INT64_MAX)
+             : launch_scatter_pw<P, false, long long>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, kHeavyTile,
+                                                      INT64_MAX);
+  } else {
+    const int64_t hi = int64_t(cells_min_count(P)) - 1;
+    cudaError_t e = w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi)
+                      : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi);
+    if (e != cudaSuccess) return e;
+    if constexpr (P > 1)
+      e = w ? launch_cells_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
+            : launch_cells_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    return e;
+  }
 }
 
 cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
@@ -1147,10 +1245,8 @@ cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float*
     case 2: return launch_tiles_p<2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
     case 3: return launch_tiles_p<3>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
     case 4: return launch_tiles_p<4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 5:
-    case 6:  // orders beyond PCS: the direct scatter of the records (box unused for packed records)
-      if (ncat != 1) return cudaErrorInvalidValue;
-      return launch_assign_direct_f32(order, p, PK_POS_CELL_F32OFF, w, n, ng, 1.0, interlace, g1, g2, ldz, s);
+    case 5: return launch_tiles_p<5>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 6: return launch_tiles_p<6>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
     default: return cudaErrorInvalidValue;
   }
 }

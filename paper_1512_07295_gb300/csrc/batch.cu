@@ -85,7 +85,6 @@ pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* off
   pk_status st = validate(cfg);
   if (st != PK_OK) return st;
   if (cfg->prec != PK_FP32 || !cfg->interlace) return fail(PK_EINVAL, "pk_batch_power supports PK_FP32 with interlacing");
-  if (cfg->order > 4) return fail(PK_EINVAL, "pk_batch_power supports orders 1..4");
   if (n_cat < 1 || !offsets_host || !pos_dev || !pk_dev || !nmodes_dev) return fail(PK_EINVAL, "bad arguments");
   if (batch < 1 || batch > kMaxBatch) return fail(PK_EINVAL, "batch must be 1..%d", kMaxBatch);
   int64_t maxp = 0;

@@ -63,8 +63,6 @@ cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, in
 // assign.cu -- grid layout: node (x, y, z) at element (x * ng + y) * ldz + z of each grid.
 cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
                                      bool interlace, double* g1, double* g2, int ldz, cudaStream_t s);
-cudaError_t launch_assign_direct_f32(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
-                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
 cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
 // FP32 tile assignment (assign_tiles.cu: the scatter on sparse tiles, the key-cell kernel on dense

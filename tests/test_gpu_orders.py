@@ -54,6 +54,47 @@ def test_grids_orders_5_6_packed_records_and_weights(order):
 
 
 @pytest.mark.parametrize("order", [5, 6])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_tiles_orders_5_6_sparse_dense_and_heavy(order, weighted):
+    # the tiled scatter takes every tile for p = 5, 6: sparse tiles, a dense one (~2000 particles) and
+    # a heavy one (>= 16384 particles: 64-bit region); grids node by node against the oracle
+    box, ng = 64.0, 32
+    rng = np.random.default_rng(88 + order)
+    base = rng.uniform(0.0, box, (6000, 3))
+    dense = rng.uniform(0.0, 16.0, (2000, 3)) + np.array([0.0, 16.0, 32.0])
+    heavy = rng.uniform(0.0, 16.0, (20000, 3)) + np.array([48.0, 48.0, 0.0])
+    pos = np.concatenate([base, dense, heavy]) % box
+    cfg = api.Config(ng=ng, box=box, order=order, prec="fp32")
+    cells = api.prepare(_t(pos), cfg)
+    uu = _ref.cellpos_to_units(cells.cpu().numpy(), ng)
+    w = catalogs.random_weights(len(pos), seed=89).astype(np.float32) if weighted else None
+    w64 = None if w is None else w.astype(np.float64)
+    r1 = oracle.assign.assign_units(uu, ng, order, w64)
+    r2 = oracle.assign.assign_units(uu, ng, order, w64, shift=True)
+    api.device_error()
+    g1, g2 = api.assign(cells, cfg, weights=None if w is None else _t(w))
+    assert api.device_error() == 0
+    scale = float(np.max(np.abs(r1)))
+    assert np.max(np.abs(g1.cpu().numpy() - r1)) <= 2e-6 * scale
+    assert np.max(np.abs(g2.cpu().numpy() - r2)) <= 2e-6 * scale
+
+
+@pytest.mark.parametrize("order", [5, 6])
+def test_batch_orders_5_6_match_oracle(order):
+    box, ng = 200.0, 24
+    cats = [catalogs.poisson(n, box, seed=90 + i) for i, n in enumerate([700, 3000, 1500])]
+    cfg = api.Config(ng=ng, box=box, order=order, prec="fp32")
+    cells = torch.cat([api.prepare(_t(c), cfg) for c in cats])
+    offs = np.concatenate([[0], np.cumsum([len(c) for c in cats])])
+    pk, nm = api.batch_power(cells, offs, cfg, batch=2)
+    for i in range(len(cats)):
+        u = _ref.cellpos_to_units(cells[offs[i]:offs[i + 1]].cpu().numpy(), ng)
+        ref_pk, _, ref_cnt = _ref.power_units(u, box, ng, order)
+        assert np.array_equal(nm[i].cpu().numpy(), ref_cnt)
+        assert _ref.rel(pk[i].cpu().numpy(), ref_pk) <= 1e-5, i
+
+
+@pytest.mark.parametrize("order", [5, 6])
 def test_backward_orders_5_6_match_oracle(order):
     box, ng = 100.0, 16
     pos = catalogs.zeldovich(12, box, rms=4.0, seed=84)
@@ -91,7 +132,4 @@ def test_orders_5_6_are_refused_where_unsupported():
         api.power(pos, api.Config(ng=16, box=100.0, order=5, prec="fixed64"))
     with pytest.raises(ffi.PkError):
         api.power(pos, api.Config(ng=16, box=100.0, order=7, prec="fp64"))
-    cells = api.prepare(pos, api.Config(ng=16, box=100.0))
-    offs = np.array([0, 500, 1000], dtype=np.int64)
-    with pytest.raises(ffi.PkError):
-        api.batch_power(cells, offs, api.Config(ng=16, box=100.0, order=5), batch=2)
+
