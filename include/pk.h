@@ -196,14 +196,18 @@ pk_status pk_power_binned(const pk_config* cfg, const pk_cellpos* sorted_dev, co
  * k_f, n != 0), over the triangles s1 >= s2 >= s3 with s1 <= s2 + s3 + 1, s1 slowest.
  * Requires 3 (kmax - 1) < N, kmax = shell_lo + nshells shell_w (Sec. 4.1: k_max = k_f N/3).
  * counts_dev: int64[ntri], ntri = pk_bispectrum_ntri(nshells). Depends only on N and the shells;
- * callers cache it. Computed by an FP64 convolution of shell indicators, rounded, summed in int64. */
+ * callers cache it. Computed by an FP64 convolution of shell indicators, rounded, summed in int64,
+ * on the same grid M as pk_bispectrum. */
 int32_t pk_bispectrum_ntri(int32_t nshells);
 pk_status pk_bispectrum_counts(const pk_config* cfg, int32_t shell_lo, int32_t shell_w, int32_t nshells,
                                int64_t* counts_dev, void* ws, size_t ws_bytes, void* stream);
 
 /* a7 -- FFT bispectrum (eq:Best2, eq:IntI): for each shell I_s(x) = sum_{n in s} delta(n)
  * exp(+2 pi i n.x/N) (inverse FFT of the shell-filtered delta), then for every triangle
- * B = V^2 sum_x I_1 I_2 I_3 / (N_c N_tri) with FP64 sums (NaN where N_tri = 0).
+ * B = V^2 sum_x I_1 I_2 I_3 / (N_c N_tri) with FP64 sums (NaN where N_tri = 0). The sums run on
+ * the smallest grid M <= N of even side with factors 2, 3, 5, 7 and M > 3 (kmax - 1) (the product
+ * of three shell fields then has no alias at n = 0), with N_c = M^3: the same B as on N.
+ * The workspace query sizes for M = N, the largest.
  * delta_k_dev: as written by pk_power / pk_fft_estimate with the same cfg; counts_dev from
  * pk_bispectrum_counts; B_dev: double[ntri]. */
 pk_status pk_bispectrum(const pk_config* cfg, const void* delta_k_dev, int32_t shell_lo, int32_t shell_w,
