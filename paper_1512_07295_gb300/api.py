@@ -349,6 +349,7 @@ def autotune_batch(cells, offsets, cfg, candidates=(16, 32, 64, 128), reps=3):
         b = int(min(max(b, 1), 128))
         ws = batch_workspace(cfg, b, max_group_particles(offs, b), cells.device)
         batch_power(cells, offs, cfg, batch=b, ws=ws, out=(pk, nm))
+        torch.cuda.synchronize()  # the warm-up call (plans, attributes) ends before the timed calls start
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):

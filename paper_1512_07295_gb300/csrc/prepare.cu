@@ -236,6 +236,10 @@ __device__ __forceinline__ int tile_of(const pk_cellpos& r, int ntile) {
   return ((cell_x(r.cell) / kTileCells) * ntile + cell_y(r.cell) / kTileCells) * ntile + cell_z(r.cell) / kTileCells;
 }
 
+// Records per thread and round of the chunk loops: their loads are issued together, so each thread
+// keeps several in flight (one at a time left the kernels waiting on memory at 8 % issue).
+constexpr int kBinUnroll = 4;
+
 __global__ void k_tile_count_smem(const pk_cellpos* __restrict__ p, CatRanges r, int ntile,
                                   unsigned long long* __restrict__ counts) {
   extern __shared__ int s_cnt[];  // [ntiles]
@@ -244,7 +248,17 @@ __global__ void k_tile_count_smem(const pk_cellpos* __restrict__ p, CatRanges r,
   if (beg >= end) return;
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_cnt[t] = 0;
   __syncthreads();
-  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&s_cnt[tile_of(checked(p[i], r.ng), ntile)], 1);
+  for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += int64_t(kBinUnroll) * blockDim.x) {
+    pk_cellpos rec[kBinUnroll];
+#pragma unroll
+    for (int u = 0; u < kBinUnroll; ++u) {
+      const int64_t i = i0 + int64_t(u) * blockDim.x;
+      if (i < end) rec[u] = p[i];
+    }
+#pragma unroll
+    for (int u = 0; u < kBinUnroll; ++u)
+      if (i0 + int64_t(u) * blockDim.x < end) atomicAdd(&s_cnt[tile_of(checked(rec[u], r.ng), ntile)], 1);
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
     if (s_cnt[t]) atomicAdd(&counts[int64_t(c) * ntiles + t], (unsigned long long)s_cnt[t]);
@@ -259,7 +273,17 @@ __global__ void k_tile_place_smem(const pk_cellpos* __restrict__ p, CatRanges r,
   if (beg >= end) return;
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_cnt[t] = 0;
   __syncthreads();
-  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&s_cnt[tile_of(checked(p[i], r.ng), ntile)], 1);
+  for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += int64_t(kBinUnroll) * blockDim.x) {
+    pk_cellpos rec[kBinUnroll];
+#pragma unroll
+    for (int u = 0; u < kBinUnroll; ++u) {
+      const int64_t i = i0 + int64_t(u) * blockDim.x;
+      if (i < end) rec[u] = p[i];
+    }
+#pragma unroll
+    for (int u = 0; u < kBinUnroll; ++u)
+      if (i0 + int64_t(u) * blockDim.x < end) atomicAdd(&s_cnt[tile_of(checked(rec[u], r.ng), ntile)], 1);
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
     const int k = s_cnt[t];
@@ -270,10 +294,25 @@ __global__ void k_tile_place_smem(const pk_cellpos* __restrict__ p, CatRanges r,
     s_cnt[t] = 0;
   }
   __syncthreads();
-  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    const pk_cellpos rec = checked(p[i], r.ng);
-    const int t = tile_of(rec, ntile);
-    out[s_base[t] + atomicAdd(&s_cnt[t], 1)] = rec;
+  for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += int64_t(kBinUnroll) * blockDim.x) {
+    pk_cellpos rec[kBinUnroll];
+#pragma unroll
+    for (int u = 0; u < kBinUnroll; ++u) {
+      const int64_t i = i0 + int64_t(u) * blockDim.x;
+      if (i < end) rec[u] = p[i];
+    }
+    int64_t dst[kBinUnroll];
+#pragma unroll
+    for (int u = 0; u < kBinUnroll; ++u) {
+      if (i0 + int64_t(u) * blockDim.x < end) {
+        rec[u] = checked(rec[u], r.ng);
+        const int t = tile_of(rec[u], ntile);
+        dst[u] = s_base[t] + atomicAdd(&s_cnt[t], 1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBinUnroll; ++u)
+      if (i0 + int64_t(u) * blockDim.x < end) out[dst[u]] = rec[u];
   }
 }
 
