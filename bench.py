@@ -435,7 +435,7 @@ def row_batch(dev, profile_range=False, ncats=512):
     del parts
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     # group size chosen by the library's autotuner, then the call timed eagerly and as a CUDA graph replay
-    batch, tune_ms = api.autotune_batch(cells, offs, cfg, candidates=(32, 64, 128), reps=2)
+    batch, tune_ms = api.autotune_batch(cells, offs, cfg, candidates=(32, 64, 128), reps=2, runs=(1, 2))
     wsc = api.batch_workspace(cfg, batch, api.max_group_particles(offs, batch), dev)
     pkb = torch.empty((ncats, cfg.nb), dtype=torch.float64, device=dev)
     nmb = torch.empty((ncats, cfg.nb), dtype=torch.int64, device=dev)
@@ -455,7 +455,8 @@ def row_batch(dev, profile_range=False, ncats=512):
     torch.cuda.current_stream(dev).wait_stream(cap)
     ms_graph = _time_cuda(graph.replay, 3)
     rows["batch"] = {"workload": f"{ncats} catalogues, {int(sizes.sum())} particles, N_P log-uniform in [1e5, 2e6], L=1000, "
-                                 f"N_G=128, PCS+interlacing, FP32, groups of {batch} (autotuned)",
+                                 f"N_G=128, PCS+interlacing, FP32, groups of {batch}, scatter runs of {cfg.tile_run} "
+                                 f"tile(s) (autotuned)",
                      "ms_per_call": ms, "pk_per_s": ncats / (ms * 1e-3), "particles_per_s": float(sizes.sum()) / (ms * 1e-3),
                      "graph_ms_per_call": ms_graph, "autotune_ms": {str(k): v for k, v in tune_ms.items()}}
     del graph

@@ -81,7 +81,7 @@ typedef struct {
 typedef struct {
   int32_t ng;            /* N: even, 8 <= N <= 1024 */
   int32_t order;         /* p: 1 NGP, 2 CIC, 3 TSC, 4 PCS (Sec. 2.3); 5, 6 the next B-splines
-                            (PK_FP64 and PK_FP32; not pk_batch_power) */
+                            (PK_FP64 and PK_FP32, pk_batch_power included) */
   int32_t interlace;     /* 1: add the H/2-shifted grid (Sec. 3.1); 0: single grid */
   int32_t prec;          /* pk_precision */
   double box;            /* L > 0 */
@@ -89,6 +89,9 @@ typedef struct {
   int32_t bin_w2;        /* bin width in units of k_f/2 (>= 1) */
   int32_t nbins;         /* number of bins (1..2048) */
   int32_t subtract_shot; /* 1: subtract the shot noise V sum(w^2)/sum(w)^2 from every bin */
+  int32_t tile_run;      /* PK_FP32 sparse tiles: tiles per scatter region along z (1, 2, 4; 0 = chosen
+                            from the mean tile population). A run of S tiles shares one shared-memory
+                            region of 12 x 12 x (8 S + 4) nodes per grid. */
 } pk_config;
 
 /* Which call pk_workspace_size sizes. */

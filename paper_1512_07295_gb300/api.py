@@ -29,11 +29,12 @@ class Config:
     bin_w2: int = 2
     nbins: int = 0
     subtract_shot: bool = False
+    tile_run: int = 0
 
     def c(self):
         nb = self.nbins if self.nbins > 0 else self.ng // 2
         return ffi.PkConfig(int(self.ng), int(self.order), int(bool(self.interlace)), _PREC[self.prec], float(self.box),
-                            int(self.bin_lo2), int(self.bin_w2), int(nb), int(bool(self.subtract_shot)))
+                            int(self.bin_lo2), int(self.bin_w2), int(nb), int(bool(self.subtract_shot)), int(self.tile_run))
 
     @property
     def nb(self):
@@ -333,11 +334,25 @@ def batch_power(cells, offsets, cfg, batch=64, ws=None, out=None):
     return pk, nm
 
 
-def autotune_batch(cells, offsets, cfg, candidates=(16, 32, 64, 128), reps=3):
+def autotune_batch(cells, offsets, cfg, candidates=(16, 32, 64, 128), reps=3, runs=None):
     """Chooses the group size of batch_power for these catalogues by timing each candidate (CUDA
     events, after one warm-up call each). Returns (best, {candidate: ms}). The group size sets how
     many catalogues share each batched launch: larger groups fill the GPU with fewer launches but
-    need a larger workspace."""
+    need a larger workspace. runs: also try these scatter run lengths (tiles per region along z,
+    cfg.tile_run); the best run length is then written to cfg.tile_run and the keys are
+    "group/run"."""
+    if runs:
+        best, table = None, {}
+        base = cfg.tile_run
+        for r in runs:
+            cfg.tile_run = int(r)
+            b, t = autotune_batch(cells, offsets, cfg, candidates, reps)
+            for k, v in t.items():
+                table[f"{k}/{r}"] = v
+            if best is None or t[b] < table[f"{best[0]}/{best[1]}"]:
+                best = (b, int(r))
+        cfg.tile_run = best[1] if best else base
+        return best[0], table
     import numpy as np
 
     offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))

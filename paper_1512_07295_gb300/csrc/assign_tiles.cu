@@ -298,38 +298,50 @@ __device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned pari
 // 1..10 of a row form five pairs at even z, one 8-byte vector reduction each (row bases are 8-byte
 // aligned: ldz even), and nodes 0 and 11 go alone; rows that wrap in z take one node at a time.
 // Zero nodes are skipped.
-__device__ __forceinline__ void flush_region(int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
-                                             float inv_scale, float* g1, float* g2, int tid, int nthreads) {
-  static_assert(RS == 12 && (RVOL * 4) % 16 == 0, "rows of 12 nodes, 16-byte aligned");
-  const bool seam = cz0 == 0 || cz0 + RS - 1 > ng;  // some node of a row wraps in z
+template <int RZ>
+__device__ __forceinline__ void flush_rows(int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
+                                           float inv_scale, float* g1, float* g2, int tid, int nthreads) {
+  static_assert(RZ % 8 == 4, "rows of 8 k + 4 nodes: 16-byte aligned, pairs at even z inside");
+  constexpr int Q = RZ / 4, VOL = RS * RS * RZ;
+  const bool seam = cz0 == 0 || cz0 + RZ - 1 > ng;  // some node of a row wraps in z
   const int z0 = cz0 - 1;
   const int nrows = ngrid * RS * RS;
   for (int row = tid; row < nrows; row += nthreads) {
     const int gi = row >= RS * RS ? 1 : 0, rr = row - gi * (RS * RS);
     const int rx = rr / RS, ry = rr - rx * RS;
-    int4* src = reinterpret_cast<int4*>(reg + gi * RVOL + rr * RS);
-    const int4 qa = src[0], qb = src[1], qc = src[2];
-    const int4 zero = make_int4(0, 0, 0, 0);
-    src[0] = zero;
-    src[1] = zero;
-    src[2] = zero;
-    const int iv[RS] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w, qc.x, qc.y, qc.z, qc.w};
+    int4* src = reinterpret_cast<int4*>(reg + gi * VOL + rr * RZ);
+    int iv[RZ];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int4 v = src[q];
+      src[q] = make_int4(0, 0, 0, 0);
+      iv[4 * q] = v.x;
+      iv[4 * q + 1] = v.y;
+      iv[4 * q + 2] = v.z;
+      iv[4 * q + 3] = v.w;
+    }
     float* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
     if (!seam) {
       if (iv[0] != 0) atomicAdd(gg + z0, float(iv[0]) * inv_scale);
 #pragma unroll
-      for (int k = 1; k < RS - 1; k += 2)
+      for (int k = 1; k < RZ - 1; k += 2)
         if ((iv[k] | iv[k + 1]) != 0)
           asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(gg + z0 + k), "f"(float(iv[k]) * inv_scale),
                        "f"(float(iv[k + 1]) * inv_scale)
                        : "memory");
-      if (iv[RS - 1] != 0) atomicAdd(gg + z0 + RS - 1, float(iv[RS - 1]) * inv_scale);
+      if (iv[RZ - 1] != 0) atomicAdd(gg + z0 + RZ - 1, float(iv[RZ - 1]) * inv_scale);
     } else {
 #pragma unroll
-      for (int k = 0; k < RS; ++k)
+      for (int k = 0; k < RZ; ++k)
         if (iv[k] != 0) atomicAdd(gg + wrap(z0 + k, ng), float(iv[k]) * inv_scale);
     }
   }
+}
+
+__device__ __forceinline__ void flush_region(int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
+                                             float inv_scale, float* g1, float* g2, int tid, int nthreads) {
+  static_assert(RS == 12 && (RVOL * 4) % 16 == 0, "rows of 12 nodes, 16-byte aligned");
+  flush_rows<RS>(reg, ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, nthreads);
 }
 
 // The same for 64-bit regions (heavy tiles): rows of RS nodes, each node converted and added on its
@@ -457,25 +469,32 @@ template <int P>
 __host__ __device__ constexpr int region_off() {
   return P >= 5 ? 2 : 1;
 }
-template <int P>
+// Runs of S tiles along z share one region: its rows along z hold 8 S + 4 nodes.
+template <int P, int S = 1>
+__host__ __device__ constexpr int region_z() {
+  return P >= 5 ? region_edge<P>() : T * S + 4;
+}
+template <int P, int S = 1>
 __host__ __device__ constexpr int region_vol() {
-  return region_edge<P>() * region_edge<P>() * region_edge<P>();
+  return region_edge<P>() * region_edge<P>() * region_z<P, S>();
 }
 
 // A finished scatter tile's region into the grids: rows of 12 nodes up to PCS, node by node beyond.
-template <int P, typename R>
+template <int P, int S, typename R>
 __device__ __forceinline__ void flush_scatter_region(R* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz,
                                                      float inv_scale, float* g1, float* g2, int tid, int nthreads) {
-  if constexpr (P >= 5)
+  if constexpr (P >= 5 || sizeof(R) == 8) {
+    static_assert(S == 1, "orders 5, 6 and 64-bit regions take single tiles");
     flush_region_edge<region_edge<P>(), region_off<P>()>(reg, ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, nthreads);
-  else
-    flush_region(reg, ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, nthreads);
+  } else {
+    flush_rows<region_z<P, S>()>(reg, ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, nthreads);
+  }
 }
 
-template <int P, bool W, typename R = int>
+template <int P, bool W, typename R = int, int S = 1>
 struct ScatterSmem {
   int4 sp[2][scatter_chunk<W>()];
-  alignas(16) R reg[2][2][region_vol<P>()];  // two tiles' regions in turn: one is flushed while the next is filled
+  alignas(16) R reg[2][2][region_vol<P, S>()];  // two runs' regions in turn: one is flushed while the next is filled
   float red[2][SCATTER_THREADS / 32];
   unsigned long long mbar[2];
   float sw[2][W ? scatter_chunk<W>() : 1];
@@ -498,17 +517,17 @@ __device__ __forceinline__ int high_start(int l, float f, float* w) {
 }
 
 // Index of the region node where grid G's stencil of a particle at local cell (lx, ly, lz) + f starts.
-template <int P, int G>
+template <int P, int G, int S = 1>
 __device__ __forceinline__ int stencil_origin(int lx, int ly, int lz, float fx, float fy, float fz) {
-  constexpr int E = region_edge<P>(), O = region_off<P>();
+  constexpr int E = region_edge<P>(), O = region_off<P>(), EZ = region_z<P, S>();
   if constexpr (P >= 5) {
     float w[P];
     const int sx = high_start<P, G>(lx, fx, w), sy = high_start<P, G>(ly, fy, w), sz = high_start<P, G>(lz, fz, w);
-    return ((sx + O) * E + sy + O) * E + sz + O;
+    return ((sx + O) * E + sy + O) * EZ + sz + O;
   } else {
     float t;
     const int kx = lx + grid_key<P, G>(fx, &t), ky = ly + grid_key<P, G>(fy, &t), kz = lz + grid_key<P, G>(fz, &t);
-    return ((kx + s0<P>() + O) * E + ky + s0<P>() + O) * E + kz + s0<P>() + O;
+    return ((kx + s0<P>() + O) * E + ky + s0<P>() + O) * EZ + kz + s0<P>() + O;
   }
 }
 
@@ -531,14 +550,14 @@ __device__ __forceinline__ R fixed_product(float x, float y) {
 // otherwise; lanes per bucket.
 template <int P>
 __host__ __device__ constexpr int bank_buckets() {
-  return (P % 2 == 0 && region_edge<P>() == 12) ? 16 : 32;
+  return (P % 2 == 0 && region_edge<P>() == 12) ? 16 : 32;  // 12 (8 S + 4) = 16 (mod 32) for every S
 }
 
 // Adds one particle's p^3 weights on grid G to that grid's region (scale: the weight times the
 // region's fixed-point scale). Region nodes of the stencil: key + S0 + 1 .. key + S0 + p per axis.
 // lane: the caller's lane; for even p the planes are taken in pairs swapped when the lane's bank half
 // differs from the stencil origin's (the bank order above).
-template <int P, int G, typename R>
+template <int P, int G, int S, typename R>
 __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc,
                                                  int lane) {
   if constexpr (P >= 5) {  // orders 5 and 6: the B-spline weights and stencil start per axis
@@ -547,6 +566,7 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
     const int sx = high_start<P, G>(lx, fx, wx), sy = high_start<P, G>(ly, fy, wy), sz = high_start<P, G>(lz, fz, wz);
 #pragma unroll
     for (int a = 0; a < P; ++a) wx[a] *= sc;
+    static_assert(S == 1, "orders 5 and 6 take single tiles");
     const unsigned base = smem_u32(reg + ((sx + O) * E + sy + O) * E + sz + O);
 #pragma unroll
     for (int a = 0; a < P; ++a)
@@ -566,7 +586,8 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
     weights<P>(tz, wz);
 #pragma unroll
     for (int a = 0; a < P; ++a) wx[a] *= sc;
-    const int q = ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1;
+    constexpr int EZ = region_z<P, S>();  // rows along z; planes RS EZ nodes apart (16 mod 32)
+    const int q = ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * EZ + kz + s0<P>() + 1;
     unsigned base_even = smem_u32(reg + q), base_odd = base_even;
     if constexpr (bank_buckets<P>() == 16) {
       if ((q ^ lane) & 16) {  // step a adds plane a ^ 1
@@ -576,8 +597,8 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
           wx[a] = wx[a + 1];
           wx[a + 1] = t;
         }
-        base_even += unsigned(sizeof(R)) * RS * RS;
-        base_odd -= unsigned(sizeof(R)) * RS * RS;
+        base_even += unsigned(sizeof(R)) * RS * EZ;
+        base_odd -= unsigned(sizeof(R)) * RS * EZ;
       }
     }
 #pragma unroll
@@ -588,7 +609,7 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
         const float xy = wx[a] * wy[b];
 #pragma unroll
         for (int c = 0; c < P; ++c)
-          red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * RS + c), fixed_product<P, R>(xy, wz[c]));
+          red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * EZ + c), fixed_product<P, R>(xy, wz[c]));
       }
     }
   }
@@ -598,17 +619,21 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
 // 2^e < 2^30) and, where fixed_product rounds by the 1.5 2^23 addition, node share x max |weight| x
 // 2^e <= 2^22 for every single addition. With weights the block reduces the sum and the maximum
 // (red: two floats per warp); the caller synchronises before the first use.
-template <int P, bool W, typename R>
-__device__ __forceinline__ void scatter_scale(const float* w, int64_t beg, int64_t end, float (*red)[SCATTER_THREADS / 32],
-                                              int tid, float* scale, float* inv_scale) {
+template <int P, bool W, typename R, int S>
+__device__ __forceinline__ void scatter_scale(const float* w, const int64_t (&beg)[S], const int64_t (&end)[S],
+                                              float (*red)[SCATTER_THREADS / 32], int tid, float* scale, float* inv_scale) {
   constexpr int NW = SCATTER_THREADS / 32;
-  float bound = float(end - beg), wmax = 1.0f;
+  float bound = 0.0f, wmax = 1.0f;
+#pragma unroll
+  for (int q = 0; q < S; ++q) bound += float(end[q] - beg[q]);
   if (W) {
     float a = 0.0f, m = 0.0f;
-    for (int64_t i = beg + tid; i < end; i += SCATTER_THREADS) {
-      a += fabsf(w[i]);
-      m = fmaxf(m, fabsf(w[i]));
-    }
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      for (int64_t i = beg[q] + tid; i < end[q]; i += SCATTER_THREADS) {
+        a += fabsf(w[i]);
+        m = fmaxf(m, fabsf(w[i]));
+      }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -641,16 +666,42 @@ __device__ __forceinline__ void scatter_scale(const float* w, int64_t beg, int64
 
 }  // namespace tiles
 
-// a3, FP32, direct scatter: a block takes tiles in a grid-stride sequence and their pieces in
-// order, the copy of the next piece overlapping the use of the current one. Per piece: each record's
-// stencil origin on each grid is bucketed by bank (counts with shared atomics, which also give the
-// record's place in its bucket); one warp per grid turns the counts into offsets; the records are
-// listed in bucket order; then the warps take rounds (grid 1's, then grid 2's), lane l of round k
-// scattering the k-th record of bucket l (even p: record 2 k + l / 16 of bucket l mod 16). Tiles use two regions in turn: a finished tile's region is
-// added to the grids (and cleared) by flush_region in the bucket phase of the next piece. The block
+// The first run r + k stride (k >= 0) below nruns holding a tile of lo .. hi particles, else nruns. A
+// run is S tiles consecutive along z (tile index (t_x N_t + t_y) N_t + t_z, so its tiles are
+// consecutive indices). Warp-parallel as next_tile.
+template <int S>
+__device__ __forceinline__ int next_run(const int64_t* toff, int64_t n, int r, int stride, int nruns, int64_t lo, int64_t hi) {
+  const int lane = threadIdx.x & 31;
+  for (; r < nruns; r += 32 * stride) {
+    const int c = r + lane * stride;
+    bool ok = false;
+    if (c < nruns)
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const int64_t cnt = min(toff[c * S + q + 1], n) - max(toff[c * S + q], int64_t(0));
+        ok |= cnt >= lo && cnt <= hi;
+      }
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (m) return r + (__ffs(m) - 1) * stride;
+  }
+  return nruns;
+}
+
+// a3, FP32, direct scatter: a block takes runs of S tiles along z (one region per run) in a
+// grid-stride sequence, and the runs' pieces in order, the copy of the next piece overlapping the use
+// of the current one. A piece is up to CH consecutive records of the run's tiles of min_count ..
+// max_count particles (tiles of the run outside that range, taken by the key-cell kernel, split the
+// run into segments; a piece never spans two). Per piece: each record's stencil origin on each grid
+// is bucketed by bank (counts with shared atomics, which also give the record's place in its bucket);
+// one warp per grid turns the counts into offsets; the records are listed in bucket order; then the
+// warps take rounds (grid 1's, then grid 2's), lane l of round k scattering the k-th record of
+// bucket l (even p: record 2 k + l / 16 of bucket l mod 16). Runs use two regions in turn: a finished
+// run's region is added to the grids (and cleared) in the bucket phase of the next piece. The block
 // barrier at the top of each piece separates every use of the staging buffers, buckets and regions.
-template <int P, bool W, typename R>
-__global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) == 8) ? 2 : 4)
+// (The tiles of a run are consecutive along z, so the tile index is (t_x N_t + t_y) N_t + t_z and a
+// run is S consecutive indices; S divides N_t.)
+template <int P, bool W, typename R, int S>
+__global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) == 8 || S >= 4) ? 2 : (S == 2 ? 3 : 4))
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
                      int64_t n, int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
                      int64_t cat_stride, int64_t min_count, int64_t max_count) {
@@ -663,84 +714,108 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
     toff += int64_t(cat) * ntile * ntile * ntile;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ScatterSmem<P, W, R>& S = *reinterpret_cast<ScatterSmem<P, W, R>*>(smem_raw);
+  ScatterSmem<P, W, R, S>& Sm = *reinterpret_cast<ScatterSmem<P, W, R, S>*>(smem_raw);
   const int ngrid = interlace ? 2 : 1;
-  const int ntiles = ntile * ntile * ntile;
+  const int nruns = ntile * ntile * (ntile / S);
   const int tid = threadIdx.x;
   if (tid < 2) {
-    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar[tid]));
+    const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&Sm.mbar[tid]));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   }
-  for (int i = tid; i < 2 * 2 * region_vol<P>(); i += THREADS) (&S.reg[0][0][0])[i] = 0;
-  if (tid < 64) (&S.cnt[0][0])[tid] = 0;
+  for (int i = tid; i < 2 * 2 * region_vol<P, S>(); i += THREADS) (&Sm.reg[0][0][0])[i] = 0;
+  if (tid < 64) (&Sm.cnt[0][0])[tid] = 0;
   __syncthreads();
-  // the block's pieces: (tile, first record c0, tile's records [beg, end))
-  struct Piece {
-    int tile;
-    int64_t beg, end, c0;
+  auto in_range = [&](int t) {
+    const int64_t c = min(toff[t + 1], n) - max(toff[t], int64_t(0));
+    return c >= min_count && c <= max_count;
   };
-  // next piece of this tile, else the first of the block's next tile of min_count .. max_count particles
-  // (called by every thread alike)
+  // the block's pieces: run, next tile of the run after the current segment, the segment's records
+  // [c0 ..., end), and whether the piece is the run's first (called by every thread alike)
+  struct Piece {
+    int run, snext;
+    int64_t end, c0;
+    bool first;
+  };
   auto advance = [&](Piece& c) -> bool {
     c.c0 += CH;
+    c.first = false;
     if (c.c0 < c.end) return true;
-    c.tile = next_tile(toff, n, c.tile + int(gridDim.x), int(gridDim.x), ntiles, min_count, max_count);
-    if (c.tile >= ntiles) return false;
-    c.beg = max(toff[c.tile], int64_t(0));
-    c.end = min(toff[c.tile + 1], n);
-    c.c0 = c.beg;
+    int q = c.snext;
+    while (true) {
+      while (q < S && !in_range(c.run * S + q)) ++q;
+      if (q < S) break;
+      c.run = next_run<S>(toff, n, c.run + int(gridDim.x), int(gridDim.x), nruns, min_count, max_count);
+      if (c.run >= nruns) return false;
+      q = 0;
+      c.first = true;
+    }
+    int e = q;
+    while (e + 1 < S && in_range(c.run * S + e + 1)) ++e;
+    c.c0 = max(toff[c.run * S + q], int64_t(0));
+    c.end = min(toff[c.run * S + e + 1], n);
+    c.snext = e + 1;
     return true;
   };
   Piece cur;
-  cur.tile = int(blockIdx.x) - int(gridDim.x);
-  cur.beg = cur.end = 0;
+  cur.run = int(blockIdx.x) - int(gridDim.x);
+  cur.snext = S;
+  cur.end = 0;
   cur.c0 = -CH;
+  cur.first = false;
   if (!advance(cur)) return;
-  if (tid == 0) bulk_load(S.sp[0], p + cur.c0, unsigned(min(int64_t(CH), cur.end - cur.c0)) * 16u, &S.mbar[0]);
+  if (tid == 0) bulk_load(Sm.sp[0], p + cur.c0, unsigned(min(int64_t(CH), cur.end - cur.c0)) * 16u, &Sm.mbar[0]);
   if (W)
-    for (int i = tid; i < int(min(int64_t(CH), cur.end - cur.c0)); i += THREADS) S.sw[0][i] = w[cur.c0 + i];
+    for (int i = tid; i < int(min(int64_t(CH), cur.end - cur.c0)); i += THREADS) Sm.sw[0][i] = w[cur.c0 + i];
   Piece nxt = cur;
   bool has_next = advance(nxt);
   unsigned parity = 0u;  // bit b: the phase buffer b waits for next
   int buf = 0;
-  int rb = 1;  // region of the current tile (switched at each tile's first piece)
+  int rb = 1;  // region of the current run (switched at each run's first piece)
   float scale = 1.0f, inv_scale = 1.0f;
   int cx0 = 0, cy0 = 0, cz0 = 0;
-  bool pending = false;  // the previous tile's region (rb ^ 1) is still to be flushed
+  bool pending = false;  // the previous run's region (rb ^ 1) is still to be flushed
   int pcx0 = 0, pcy0 = 0, pcz0 = 0;
   float pinv = 1.0f;
   while (true) {
     const int m = int(min(int64_t(CH), cur.end - cur.c0));
-    const bool arrived = bulk_wait(&S.mbar[buf], (parity >> buf) & 1u);
+    const bool arrived = bulk_wait(&Sm.mbar[buf], (parity >> buf) & 1u);
     parity ^= 1u << buf;
     if (__syncthreads_or(!arrived)) {  // a copy did not complete: report, drain what is in flight, stop
       if (tid == 0) {
         raise_err(PK_DERR_TIMEOUT);
-        bulk_wait(&S.mbar[buf], ((parity >> buf) & 1u) ^ 1u);
+        bulk_wait(&Sm.mbar[buf], ((parity >> buf) & 1u) ^ 1u);
       }
       return;
     }
     // every use of the other buffer and of the flushed region ended before the barrier above
     if (has_next) {
       const int mn = int(min(int64_t(CH), nxt.end - nxt.c0));
-      if (tid == 0) bulk_load(S.sp[buf ^ 1], p + nxt.c0, unsigned(mn) * 16u, &S.mbar[buf ^ 1]);
+      if (tid == 0) bulk_load(Sm.sp[buf ^ 1], p + nxt.c0, unsigned(mn) * 16u, &Sm.mbar[buf ^ 1]);
       if (W)
-        for (int i = tid; i < mn; i += THREADS) S.sw[buf ^ 1][i] = w[nxt.c0 + i];
+        for (int i = tid; i < mn; i += THREADS) Sm.sw[buf ^ 1][i] = w[nxt.c0 + i];
     }
-    if (cur.c0 == cur.beg) {  // first piece of a tile: the other region, the tile's origin and scale
+    if (cur.first) {  // first piece of a run: the other region, the run's origin and scale
       rb ^= 1;
-      const int tz = cur.tile % ntile, ty = (cur.tile / ntile) % ntile, tx = cur.tile / (ntile * ntile);
+      const int rz = cur.run % (ntile / S), ty = (cur.run / (ntile / S)) % ntile, tx = cur.run / ((ntile / S) * ntile);
       cx0 = tx * T;
       cy0 = ty * T;
-      cz0 = tz * T;
-      scatter_scale<P, W, R>(w, cur.beg, cur.end, S.red, tid, &scale, &inv_scale);
+      cz0 = rz * S * T;
+      int64_t rbeg[S], rend[S];
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const int t = cur.run * S + q;
+        const bool on = in_range(t);
+        rbeg[q] = on ? max(toff[t], int64_t(0)) : 0;
+        rend[q] = on ? min(toff[t + 1], n) : 0;
+      }
+      scatter_scale<P, W, R, S>(w, rbeg, rend, Sm.red, tid, &scale, &inv_scale);
     }
     if (pending) {
-      flush_scatter_region<P>(&S.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+      flush_scatter_region<P, S>(&Sm.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
       pending = false;
     }
-    const int4* sp = S.sp[buf];
-    const float* sw = S.sw[buf];
+    const int4* sp = Sm.sp[buf];
+    const float* sw = Sm.sw[buf];
     // buckets: stencil origin mod NB per grid, and the record's place in its bucket
     constexpr int PER = (CH + THREADS - 1) / THREADS, NB = bank_buckets<P>(), LPB = 32 / NB;
     int qb[PER][2], rk[PER][2];
@@ -752,23 +827,23 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
         const int4 r = sp[j];
         const uint32_t cell = uint32_t(r.x);
         const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-        if ((cell >> 30) != 0 || unsigned(lx) >= unsigned(T) || unsigned(ly) >= unsigned(T) || unsigned(lz) >= unsigned(T)) {
+        if ((cell >> 30) != 0 || unsigned(lx) >= unsigned(T) || unsigned(ly) >= unsigned(T) || unsigned(lz) >= unsigned(S * T)) {
           raise_err(PK_DERR_CELLRANGE);
           continue;
         }
         const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
-        qb[u][0] = stencil_origin<P, 0>(lx, ly, lz, fx, fy, fz) & (NB - 1);
-        rk[u][0] = atomicAdd(&S.cnt[0][qb[u][0]], 1);
+        qb[u][0] = stencil_origin<P, 0, S>(lx, ly, lz, fx, fy, fz) & (NB - 1);
+        rk[u][0] = atomicAdd(&Sm.cnt[0][qb[u][0]], 1);
         if (interlace) {
-          qb[u][1] = stencil_origin<P, 1>(lx, ly, lz, fx, fy, fz) & (NB - 1);
-          rk[u][1] = atomicAdd(&S.cnt[1][qb[u][1]], 1);
+          qb[u][1] = stencil_origin<P, 1, S>(lx, ly, lz, fx, fy, fz) & (NB - 1);
+          rk[u][1] = atomicAdd(&Sm.cnt[1][qb[u][1]], 1);
         }
       }
     }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     if (warp < ngrid) {  // warp g: grid g's bucket offsets, sizes and round count; counts cleared
-      const int c = lane < NB ? S.cnt[warp][lane] : 0;
+      const int c = lane < NB ? Sm.cnt[warp][lane] : 0;
       int incl = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -779,39 +854,39 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (lane < NB) {
-        S.off[warp][lane] = incl - c;
-        S.nr[warp][lane] = c;
-        S.cnt[warp][lane] = 0;
+        Sm.off[warp][lane] = incl - c;
+        Sm.nr[warp][lane] = c;
+        Sm.cnt[warp][lane] = 0;
       }
-      if (lane == 0) S.rounds[warp] = mx;
+      if (lane == 0) Sm.rounds[warp] = mx;
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       if (qb[u][0] < 0) continue;
       const unsigned short j = static_cast<unsigned short>(tid + u * THREADS);
-      S.list[0][S.off[0][qb[u][0]] + rk[u][0]] = j;
-      if (interlace) S.list[1][S.off[1][qb[u][1]] + rk[u][1]] = j;
+      Sm.list[0][Sm.off[0][qb[u][0]] + rk[u][0]] = j;
+      if (interlace) Sm.list[1][Sm.off[1][qb[u][1]] + rk[u][1]] = j;
     }
     __syncthreads();
     // rounds: grid 1's rounds, then grid 2's, dealt to the warps in turn
-    const int r0 = S.rounds[0], rtot = r0 + (interlace ? S.rounds[1] : 0);
+    const int r0 = Sm.rounds[0], rtot = r0 + (interlace ? Sm.rounds[1] : 0);
     for (int item = warp; item < rtot; item += NWARP) {
       const int g = item < r0 ? 0 : 1;
       const int k = (g ? item - r0 : item) * LPB + lane / NB, bkt = lane % NB;
-      if (k >= S.nr[g][bkt]) continue;
-      const int j = S.list[g][S.off[g][bkt] + k];
+      if (k >= Sm.nr[g][bkt]) continue;
+      const int j = Sm.list[g][Sm.off[g][bkt] + k];
       const int4 r = sp[j];
       const uint32_t cell = uint32_t(r.x);
       const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
       const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
       const float sc = (W ? sw[j] : 1.0f) * weight_scale<P>() * scale;
       if (g == 0)
-        scatter_particle<P, 0>(S.reg[rb][0], lx, ly, lz, fx, fy, fz, sc, lane);
+        scatter_particle<P, 0, S>(Sm.reg[rb][0], lx, ly, lz, fx, fy, fz, sc, lane);
       else
-        scatter_particle<P, 1>(S.reg[rb][1], lx, ly, lz, fx, fy, fz, sc, lane);
+        scatter_particle<P, 1, S>(Sm.reg[rb][1], lx, ly, lz, fx, fy, fz, sc, lane);
     }
-    if (cur.c0 + CH >= cur.end) {  // last piece of the tile: its region is flushed with the next piece
+    if (!has_next || nxt.first) {  // last piece of the run: its region is flushed with the next piece
       pending = true;
       pcx0 = cx0;
       pcy0 = cy0;
@@ -824,7 +899,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
     has_next = advance(nxt);
   }
   __syncthreads();
-  if (pending) flush_scatter_region<P>(&S.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+  if (pending) flush_scatter_region<P, S>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
 }
 
 // ---- cells (dense tiles) ---------------------------------------------------------------------------
@@ -1154,19 +1229,19 @@ static int cells_min_count(int order) {
   }
 }
 
-template <int P, bool W, typename R = int>
+template <int P, bool W, typename R = int, int S = 1>
 static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                      bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
                                      int64_t cat_stride, int64_t lo, int64_t hi) {
   const int ntile = tiles_per_axis(ng);
-  const int ntiles = ntile * ntile * ntile;
-  const size_t smem = sizeof(tiles::ScatterSmem<P, W, R>);
+  const int nruns = ntile * ntile * (ntile / S);
+  const size_t smem = sizeof(tiles::ScatterSmem<P, W, R, S>);
   int per_sm = 1;
-  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W, R>), tiles::SCATTER_THREADS, smem, &per_sm);
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W, R, S>), tiles::SCATTER_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
-  const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
-  k_assign_scatter<P, W, R><<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2,
-                                                                        ldz, cat_stride, lo, hi);
+  const dim3 blocks(std::max(1, std::min(nruns, std::max(1, num_sms() * per_sm / ncat))), ncat);
+  k_assign_scatter<P, W, R, S><<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1,
+                                                                           g2, ldz, cat_stride, lo, hi);
   count_launch();
   return cudaGetLastError();
 }
@@ -1216,7 +1291,7 @@ static cudaError_t launch_cells_pw(const pk_cellpos* p, const float* w, const in
 // other's tiles, so all launch whatever the populations.
 template <int P>
 static cudaError_t launch_tiles_p(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng, bool interlace,
-                                  float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride) {
+                                  float* g1, float* g2, int ldz, cudaStream_t s, int ncat, int64_t cat_stride, int run) {
   if constexpr (P >= 5) {
     cudaError_t e = w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, kHeavyTile - 1)
                       : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, kHeavyTile - 1);
@@ -1227,8 +1302,19 @@ static cudaError_t launch_tiles_p(const pk_cellpos* p, const float* w, const int
                                                       INT64_MAX);
   } else {
     const int64_t hi = int64_t(cells_min_count(P)) - 1;
-    cudaError_t e = w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi)
-                      : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi);
+    const int ntile = tiles_per_axis(ng);
+    if (run != 2 && run != 4) run = 1;
+    if (ntile % run != 0) run = 1;
+    cudaError_t e;
+    if (run == 4)
+      e = w ? launch_scatter_pw<P, true, int, 4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi)
+            : launch_scatter_pw<P, false, int, 4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi);
+    else if (run == 2)
+      e = w ? launch_scatter_pw<P, true, int, 2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi)
+            : launch_scatter_pw<P, false, int, 2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi);
+    else
+      e = w ? launch_scatter_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi)
+            : launch_scatter_pw<P, false>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1, hi);
     if (e != cudaSuccess) return e;
     if constexpr (P > 1)
       e = w ? launch_cells_pw<P, true>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride)
@@ -1239,14 +1325,14 @@ static cudaError_t launch_tiles_p(const pk_cellpos* p, const float* w, const int
 
 cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
-                                    int64_t cat_stride) {
+                                    int64_t cat_stride, int run) {
   switch (order) {
-    case 1: return launch_tiles_p<1>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 2: return launch_tiles_p<2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 3: return launch_tiles_p<3>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 4: return launch_tiles_p<4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 5: return launch_tiles_p<5>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
-    case 6: return launch_tiles_p<6>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride);
+    case 1: return launch_tiles_p<1>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, run);
+    case 2: return launch_tiles_p<2>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, run);
+    case 3: return launch_tiles_p<3>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, run);
+    case 4: return launch_tiles_p<4>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, run);
+    case 5: return launch_tiles_p<5>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1);
+    case 6: return launch_tiles_p<6>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, ncat, cat_stride, 1);
     default: return cudaErrorInvalidValue;
   }
 }

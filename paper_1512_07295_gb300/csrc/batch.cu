@@ -124,7 +124,7 @@ pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* off
     // a3: all catalogues' grid pairs
     if ((e = cudaMemsetAsync(L.grids, 0, size_t(2) * nb * per * sizeof(float), s)) != cudaSuccess) return cuda_fail(e, "memset");
     if ((e = launch_assign_tiles_f32(cfg->order, L.sorted, nullptr, L.offsets, rel.off[nb], ng, true, L.grids, L.grids + per,
-                                     ng + 2, s, nb, 2 * per)) != cudaSuccess)
+                                     ng + 2, s, nb, 2 * per, scatter_run(cfg, rel.off[nb], nb))) != cudaSuccess)
       return cuda_fail(e, "batch assign");
     k_batch_sums<<<1, kMaxBatch, 0, s>>>(L.wsums, rel); count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch sums");

@@ -71,7 +71,10 @@ cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* 
 // g + c * cat_stride.
 cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
-                                    int64_t cat_stride = 0);
+                                    int64_t cat_stride = 0, int run = 1);
+// Tiles per scatter run along z for a configuration (pk_config.tile_run, 0: chosen from the mean
+// tile population n / (ncat N_t^3)).
+int scatter_run(const pk_config* c, int64_t n, int ncat);
 // Batch: ncat catalogues (unit weights, interlaced), catalogue c's tile offsets at toff + c * ntiles and
 // its two grids at grids + c * 2 * ng*ng*ldz.
 cudaError_t launch_assign_tile_batch(int order, const pk_cellpos* p, const int64_t* toff, int64_t n, int ng, int ncat,

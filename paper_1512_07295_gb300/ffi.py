@@ -30,6 +30,7 @@ class PkConfig(ctypes.Structure):
         ("bin_w2", c_int32),
         ("nbins", c_int32),
         ("subtract_shot", c_int32),
+        ("tile_run", c_int32),
     ]
 
 

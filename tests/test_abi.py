@@ -31,7 +31,7 @@ def test_binding_covers_the_header(lib):
 
 
 def test_config_struct_layout():
-    assert ctypes.sizeof(ffi.PkConfig) == 40
+    assert ctypes.sizeof(ffi.PkConfig) == 48
     assert ffi.PkConfig.box.offset == 16
 
 

@@ -37,6 +37,23 @@ def test_batch_matches_single_and_oracle():
         assert _ref.rel(pk[i], ref_pk) <= 1e-5, i
 
 
+@pytest.mark.parametrize("run", [2, 4])
+def test_batch_runs_of_tiles_match_oracle(run):
+    box, ng = 300.0, 32
+    sizes = [3000, 700, 12000, 5]
+    cats = [catalogs.poisson(s, box, seed=400 + i) for i, s in enumerate(sizes)]
+    cfg = api.Config(ng=ng, box=box, prec="fp32", tile_run=run)
+    cells = torch.cat([api.prepare(_t(c), cfg) for c in cats])
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    pk, nm = api.batch_power(cells, offs, cfg, batch=3)
+    for i in range(len(cats)):
+        u = _ref.cellpos_to_units(cells[offs[i]:offs[i + 1]].cpu().numpy(), ng)
+        ref_pk, _, ref_cnt = _ref.power_units(u, box, ng, 4)
+        assert np.array_equal(nm[i].cpu().numpy(), ref_cnt)
+        ok = ref_cnt > 0
+        assert _ref.rel(pk[i].cpu().numpy()[ok], ref_pk[ok]) <= 1e-5, i
+
+
 def test_batch_with_empty_catalogue():
     box, ng = 100.0, 16
     cfg = api.Config(ng=ng, box=box, prec="fp32")

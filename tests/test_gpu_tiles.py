@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import _ref
-from paper_1512_07295_gb300 import api, catalogs
+from paper_1512_07295_gb300 import api, catalogs, ffi
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +65,33 @@ def test_dense_tiles_among_sparse_ones(weighted):
     pos = np.concatenate([base, clump1, clump2, clump3])
     w = catalogs.random_weights(len(pos), seed=78).astype(np.float32) if weighted else None
     _check(pos, box, ng, 4, w)
+
+
+@pytest.mark.parametrize("run", [1, 2, 4])
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_scatter_runs_of_tiles_along_z(run, order):
+    # runs of 1, 2, 4 tiles along z share one scatter region: ~200 particles per tile, one dense tile
+    # (key cells) inside a run, so the run's records form two segments, and weights
+    box, ng = 64.0, 32
+    rng = np.random.default_rng(93 + run + order)
+    base = catalogs.poisson(12000, box, seed=94 + order)
+    dense = rng.uniform(0.0, 16.0, (2500, 3)) + np.array([16.0, 32.0, 16.0])
+    pos = np.concatenate([base, dense])
+    w = catalogs.random_weights(len(pos), seed=95).astype(np.float32)
+    cfg = api.Config(ng=ng, box=box, order=order, prec="fp32", tile_run=run)
+    api.device_error()
+    for weights in (None, w):
+        g1, g2 = api.assign(_t(pos), cfg, weights=None if weights is None else _t(weights))
+        assert api.device_error() == 0
+        r1, r2 = _ref.grids(pos, box, ng, order, None if weights is None else weights.astype(np.float64))
+        scale = np.max(np.abs(r1))
+        assert np.max(np.abs(g1.cpu().numpy() - r1)) <= 2e-6 * scale
+        assert np.max(np.abs(g2.cpu().numpy() - r2)) <= 2e-6 * scale
+
+
+def test_tile_run_is_validated():
+    with pytest.raises(ffi.PkError):
+        api.power(_t(catalogs.poisson(100, 10.0, seed=96)), api.Config(ng=16, box=10.0, tile_run=3))
 
 
 @pytest.mark.parametrize("order", [2, 4])
