@@ -130,6 +130,15 @@ pk_status get_plan(int ng, int kind, int batch, PlanEntry* out) {
     return PK_OK;
   }
   PlanEntry e;
+  const long long per = (long long)ng * ng * (ng + 2);
+  e.batch = batch;
+  e.dist = per;
+  {  // the largest divisor of batch whose grids stay within 2^31 - 1 reals (at least one grid)
+    const long long lim = std::max<long long>(1, 2147483647LL / per);
+    e.sub = 1;
+    for (int d = 1; d <= batch; ++d)
+      if (batch % d == 0 && d <= lim) e.sub = d;
+  }
   cufftHandle h = 0;
   if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cufftCreate failed");
   e.h = int(h);
@@ -142,7 +151,7 @@ pk_status get_plan(int ng, int kind, int batch, PlanEntry* out) {
   const bool fwd = kind < 2;
   size_t work = 0;
   cufftResult r = cufftMakePlanMany64(h, 3, n, fwd ? rem : cem, 1, fwd ? rdist : cdist, fwd ? cem : rem, 1,
-                                      fwd ? cdist : rdist, types[kind], batch, &work);
+                                      fwd ? cdist : rdist, types[kind], e.sub, &work);
   if (r != CUFFT_SUCCESS) {
     cufftDestroy(h);
     return fail(PK_ECUFFT, "cufftMakePlanMany64 failed (%d) for ng=%d kind=%d batch=%d", int(r), ng, kind, batch);
@@ -157,14 +166,18 @@ pk_status exec_plan(const PlanEntry& p, int kind, void* data, void* work, cudaSt
   std::lock_guard<std::mutex> lk(g_plan_mu);
   if (cufftSetStream(p.h, s) != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cufftSetStream failed");
   if (cufftSetWorkArea(p.h, work) != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cufftSetWorkArea failed");
-  cufftResult r;
-  switch (kind) {
-    case 0: r = cufftExecR2C(p.h, static_cast<cufftReal*>(data), static_cast<cufftComplex*>(data)); break;
-    case 1: r = cufftExecD2Z(p.h, static_cast<cufftDoubleReal*>(data), static_cast<cufftDoubleComplex*>(data)); break;
-    case 2: r = cufftExecC2R(p.h, static_cast<cufftComplex*>(data), static_cast<cufftReal*>(data)); break;
-    default: r = cufftExecZ2D(p.h, static_cast<cufftDoubleComplex*>(data), static_cast<cufftDoubleReal*>(data)); break;
+  const size_t elem = (kind == 1 || kind == 3) ? 8 : 4;
+  for (int g = 0; g < p.batch; g += p.sub) {
+    void* gd = static_cast<char*>(data) + size_t(g) * size_t(p.dist) * elem;
+    cufftResult r;
+    switch (kind) {
+      case 0: r = cufftExecR2C(p.h, static_cast<cufftReal*>(gd), static_cast<cufftComplex*>(gd)); break;
+      case 1: r = cufftExecD2Z(p.h, static_cast<cufftDoubleReal*>(gd), static_cast<cufftDoubleComplex*>(gd)); break;
+      case 2: r = cufftExecC2R(p.h, static_cast<cufftComplex*>(gd), static_cast<cufftReal*>(gd)); break;
+      default: r = cufftExecZ2D(p.h, static_cast<cufftDoubleComplex*>(gd), static_cast<cufftDoubleReal*>(gd)); break;
+    }
+    if (r != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cuFFT exec failed (%d)", int(r));
   }
-  if (r != CUFFT_SUCCESS) return fail(PK_ECUFFT, "cuFFT exec failed (%d)", int(r));
   return PK_OK;
 }
 

@@ -31,10 +31,15 @@ struct Carver {
 };
 
 // cuFFT plans over the padded in-place layout [ng][ng][ng+2] (reals) / [ng][ng][ng/2+1] (complex),
-// `batch` grids spaced by the padded grid size. kind: 0 R2C, 1 D2Z, 2 C2R, 3 Z2D.
+// `batch` grids spaced by the padded grid size. kind: 0 R2C, 1 D2Z, 2 C2R, 3 Z2D. A batch whose
+// padded reals exceed 2^31 - 1 elements runs as several calls of `sub` grids each: on this GPU cuFFT
+// takes a slower 64-bit-index path past that size (two 1024^3 grids: 18.7 ms in one call, 11.1 ms in
+// two, and no 8 GB work area).
 struct PlanEntry {
   int h = 0;
   size_t work = 0;
+  int batch = 1, sub = 1;
+  int64_t dist = 0;  // reals between consecutive grids
 };
 pk_status get_plan(int ng, int kind, int batch, PlanEntry* out);
 pk_status exec_plan(const PlanEntry& p, int kind, void* data, void* work, cudaStream_t s);
