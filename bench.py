@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--box", type=float, default=2000.0)
     ap.add_argument("--quick", action="store_true", help="small catalogue (128^3, N_G=128) for smoke runs")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, fp64 baseline and cpu baseline")
-    ap.add_argument("--only-row", choices=["adjoint", "batch", "bispectrum", "direct", "multigrid", "e2e", "ng1024"], default=None,
+    ap.add_argument("--only-row", choices=["adjoint", "batch", "bispectrum", "direct", "multigrid", "e2e", "ng1024", "c1"],
+                    default=None,
                     help="time one secondary row on its own workload and print it (no P(k) step)")
     ap.add_argument("--ds-nside", type=int, default=128, help="--only-row direct: particles per side")
     ap.add_argument("--ds-ng", type=int, default=128, help="--only-row direct: grid size")
@@ -619,6 +620,31 @@ def row_ng1024(dev, pos64, box, hbm_peak, ng=1024, profile_range=False):
                                   "peak_gbs": hbm_peak, "frac": path_bytes / (ms * 1e-3) / 1e9 / hbm_peak}}
 
 
+def row_c1(dev):
+    """Config 1: 64^3 Poisson particles, L = 1000 Mpc/h, N_G = 64, PCS + interlacing, from device FP64
+    positions: ms per P(k) in FP64 and FP32, their difference per bin, and P(k) against the shot noise
+    V/N at the lowest 8 bins (the aliased shot noise of PCS + interlacing stays near 1 there)."""
+    import torch
+
+    from paper_1512_07295_gb300 import api, catalogs, ffi
+
+    box, ng = 1000.0, 64
+    pos = torch.from_numpy(catalogs.poisson(64 ** 3, box, seed=5)).to(dev)
+    res = {}
+    pks = {}
+    for prec in ("fp64", "fp32"):
+        cfg = api.Config(ng=ng, box=box, prec=prec)
+        ws = api.workspace(cfg, pos.shape[0], ffi.PK_WS_POWER, dev)
+        res[f"{prec}_ms_per_pk"] = _time_cuda(lambda: api.power(pos, cfg, ws=ws), 10, 3)
+        pks[prec] = api.power(pos, cfg, ws=ws)[0].cpu().numpy()
+    rel = np.abs(pks["fp32"] / pks["fp64"] - 1.0)
+    shot = box ** 3 / pos.shape[0]
+    res.update({"workload": "64^3 Poisson particles, L=1000 Mpc/h, N_G=64, PCS+interlacing, FP64 device positions",
+                "fp32_vs_fp64_max_rel": float(rel.max()), "fp32_vs_fp64_median_rel": float(np.median(rel)),
+                "p_over_shot_noise_first_8_bins": _sig(pks["fp64"][:8] / shot, 4)})
+    return res
+
+
 def row_ng1024_only(dev, a):
     """The N_G = 1024 row on its own: the catalogue generated on the GPU, then row_ng1024."""
     from paper_1512_07295_gb300 import catalogs
@@ -718,7 +744,8 @@ def main():
                "direct": lambda: row_direct(dev, alu_peak(dev), a.ds_nside, a.ds_ng),
                "multigrid": lambda: row_multigrid(dev),
                "e2e": lambda: row_e2e(dev, a.nside, a.ng, a.box, a.profile_range),
-               "ng1024": lambda: row_ng1024_only(dev, a)}[a.only_row]()
+               "ng1024": lambda: row_ng1024_only(dev, a),
+               "c1": lambda: row_c1(dev)}[a.only_row]()
         if rank == 0:
             print(json.dumps({"row": a.only_row, **row}), flush=True)
         return
@@ -845,7 +872,24 @@ def main():
         ms64 = e0.elapsed_time(e1) / k64
         result["fp64_plain"] = {"ms_per_step": ms64, "value": n / (ms64 * 1e-3), "unit": "particles/s",
                                 "speedup_of_fast_path": ms64 / ms_step}
-        del ws64, binned, sorted_, offsets
+        del ws64
+        torch.cuda.empty_cache()
+        # ---- the deterministic path (PK_FIXED64: 64-bit fixed-point grids) on the same catalogue ----
+        cfgfx = api.Config(ng=a.ng, box=a.box, order=4, interlace=True, prec="fixed64")
+        wsfx = api.workspace(cfgfx, n, ffi.PK_WS_POWER_BINNED, dev)
+        pa = api.power_binned(binned, cfgfx, ws=wsfx)[0].clone()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k64):
+            pb = api.power_binned(binned, cfgfx, ws=wsfx)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msfx = e0.elapsed_time(e1) / k64
+        result["fixed64"] = {"ms_per_step": msfx, "value": n / (msfx * 1e-3), "unit": "particles/s",
+                             "bitwise_repeatable": bool(torch.equal(pa, pb)),
+                             "path": "PK_FIXED64: FP32 contributions summed exactly in 64-bit fixed point (grids and "
+                                     "bin sums), binned records resident"}
+        del wsfx, binned, sorted_, offsets
         torch.cuda.empty_cache()
 
         # ---- the FP32 step's error per k-bin against FP64 from the FP64 positions ------------------
@@ -921,6 +965,7 @@ def main():
         # ---- other hot-path rows and the 256^3 accuracy table ---------------------------------------
         result["rows"] = measure_rows(dev, host64, a.box, alu_peak_tflops)
         result["rows"]["accuracy_c2"] = row_accuracy_c2(dev)
+        result["rows"]["c1"] = row_c1(dev)
         if ng1024 is not None:
             result["rows"]["ng1024"] = ng1024
 

@@ -231,10 +231,12 @@ cudaError_t launch_assign_tile_batch(int order, const pk_cellpos* p, const int64
   return launch_tile<float>(order, p, nullptr, toff, n, ng, true, nullptr, grids, grids + per, ldz, s, ncat, 2 * per);
 }
 
+// PK_FIXED64 runs on the bank-ordered scatter (csrc/assign_tiles.cu): 32-bit regions at a per-tile
+// scale that divides the global one, added to the int64 grids by exact integer shifts.
 cudaError_t launch_assign_tile_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n,
                                      int ng, bool interlace, const double* wsums, unsigned long long* g1,
                                      unsigned long long* g2, int ldz, cudaStream_t s) {
-  return launch_tile<unsigned long long>(order, p, w, toff, n, ng, interlace, wsums, g1, g2, ldz, s);
+  return launch_assign_tiles_fixed(order, p, w, toff, n, ng, interlace, wsums, g1, g2, ldz, s);
 }
 
 // ---- small helpers ---------------------------------------------------------------------------------

@@ -384,6 +384,29 @@ __device__ __forceinline__ void flush_region_edge(R* reg, int ngrid, int cx0, in
   }
 }
 
+// A region of the deterministic path added to its int64 grids node by node (integer additions in any
+// order give the same sums) and cleared: edge RS in x and y, EZ along z, first node one below.
+// A run's 32-bit region (scale 2^e) added to the int64 grids at the global scale 2^F, shift = F - e >= 0:
+// integer sums of integers, so the result does not depend on the order of the additions.
+template <int EZ>
+__device__ __forceinline__ void flush_region_fixed(int* reg, int ngrid, int cx0, int cy0, int cz0, int ng, int ldz, int shift,
+                                                   unsigned long long* g1, unsigned long long* g2, int tid, int nthreads) {
+  constexpr int VOL = RS * RS * EZ;
+  const int nrows = ngrid * RS * RS;
+  for (int row = tid; row < nrows; row += nthreads) {
+    const int gi = row >= RS * RS ? 1 : 0, rr = row - gi * (RS * RS);
+    const int rx = rr / RS, ry = rr - rx * RS;
+    int* src = reg + gi * VOL + rr * EZ;
+    unsigned long long* gg = (gi == 0 ? g1 : g2) + (int64_t(wrap(cx0 - 1 + rx, ng)) * ng + wrap(cy0 - 1 + ry, ng)) * ldz;
+#pragma unroll
+    for (int k = 0; k < EZ; ++k) {
+      const int v = src[k];
+      src[k] = 0;
+      if (v != 0) atomicAdd(gg + wrap(cz0 - 1 + k, ng), (unsigned long long)((long long)v * (1ll << shift)));
+    }
+  }
+}
+
 // Largest share of a particle's weight that one node receives: the peak of the one-dimensional
 // window cubed (CIC and NGP 1, TSC 3/4 per axis, PCS 2/3 per axis).
 template <int P>
@@ -535,10 +558,27 @@ __device__ __forceinline__ int stencil_origin(int lx, int ly, int lz, float fx, 
 // that adds 1.5 2^23 (the sum then lies in [2^23, 2^24], where the float's unit is 1, so its low
 // mantissa bits hold the integer; exact for |v| <= 2^22, which scatter_scale guarantees), which runs
 // on the FMA pipe instead of the conversion unit's quarter rate.
+// float -> int64 rounded to nearest (ties away from zero) from the float's bits, in integer
+// instructions: |v| = m 2^e with the 24-bit significand m. On this GPU the float -> int64 conversion
+// runs on the FP64 pipe, a small fraction of the integer rate.
+__device__ __forceinline__ long long float_to_ll(float v) {
+  const int b = __float_as_int(v);
+  const int e = ((b >> 23) & 0xff) - 150;  // v = m 2^e
+  const long long m = (b & 0x7fffff) | 0x800000;
+  long long r;
+  if (e >= 0)
+    r = m << min(e, 39);  // |v| < 2^63 for every value a region holds
+  else if (e > -25)
+    r = (m + (1ll << (-e - 1))) >> (-e);
+  else
+    r = 0;  // |v| < 1/2 (zero and subnormals included)
+  return b < 0 ? -r : r;
+}
+
 template <int P, typename R>
 __device__ __forceinline__ R fixed_product(float x, float y) {
   if constexpr (sizeof(R) == 8) {
-    return __float2ll_rn(x * y);
+    return float_to_ll(x * y);
   } else if constexpr (P >= 3) {
     return __float_as_int(fmaf(x, y, 12582912.0f)) - 0x4B400000;
   } else {
@@ -548,9 +588,15 @@ __device__ __forceinline__ R fixed_product(float x, float y) {
 
 // Buckets of the bank order: 16 for even p on the 12-node region (plane pairs 16 banks apart), 32
 // otherwise; lanes per bucket.
-template <int P>
+template <int P, typename R = int>
+__host__ __device__ constexpr bool flip_planes() {
+  return sizeof(R) == 4 && P % 2 == 0 && region_edge<P>() == 12;  // 12 (8 S + 4) = 16 (mod 32) for every S
+}
+// 64-bit regions: a node spans two banks, so the bank pair of node q is q mod 16, and the two halves of
+// a warp (served in turn) each take one record of every bucket mod 16.
+template <int P, typename R = int>
 __host__ __device__ constexpr int bank_buckets() {
-  return (P % 2 == 0 && region_edge<P>() == 12) ? 16 : 32;  // 12 (8 S + 4) = 16 (mod 32) for every S
+  return sizeof(R) == 8 ? 16 : (flip_planes<P, R>() ? 16 : 32);
 }
 
 // Adds one particle's p^3 weights on grid G to that grid's region (scale: the weight times the
@@ -589,7 +635,7 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
     constexpr int EZ = region_z<P, S>();  // rows along z; planes RS EZ nodes apart (16 mod 32)
     const int q = ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * EZ + kz + s0<P>() + 1;
     unsigned base_even = smem_u32(reg + q), base_odd = base_even;
-    if constexpr (bank_buckets<P>() == 16) {
+    if constexpr (flip_planes<P, R>()) {
       if ((q ^ lane) & 16) {  // step a adds plane a ^ 1
 #pragma unroll
         for (int a = 0; a < P; a += 2) {
@@ -619,13 +665,18 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
 // 2^e < 2^30) and, where fixed_product rounds by the 1.5 2^23 addition, node share x max |weight| x
 // 2^e <= 2^22 for every single addition. With weights the block reduces the sum and the maximum
 // (red: two floats per warp); the caller synchronises before the first use.
-template <int P, bool W, typename R, int S>
+// DET (the deterministic path): the bound is the particle count times max |w| (a maximum does not
+// depend on the order of the records, a floating-point sum may), and the exponent is capped at emax
+// (the global scale's), so that every run's scale divides the global one.
+template <int P, bool W, typename R, int S, bool DET = false>
 __device__ __forceinline__ void scatter_scale(const float* w, const int64_t (&beg)[S], const int64_t (&end)[S],
-                                              float (*red)[SCATTER_THREADS / 32], int tid, float* scale, float* inv_scale) {
+                                              float (*red)[SCATTER_THREADS / 32], int tid, float* scale, float* inv_scale,
+                                              int emax = 127) {
   constexpr int NW = SCATTER_THREADS / 32;
   float bound = 0.0f, wmax = 1.0f;
 #pragma unroll
   for (int q = 0; q < S; ++q) bound += float(end[q] - beg[q]);
+  const float count = bound;
   if (W) {
     float a = 0.0f, m = 0.0f;
 #pragma unroll
@@ -650,7 +701,7 @@ __device__ __forceinline__ void scatter_scale(const float* w, const int64_t (&be
       bound += red[0][q];
       wmax = fmaxf(wmax, red[1][q]);
     }
-    bound *= 1.0001f;  // the FP32 sum's rounding
+    bound = DET ? count * wmax : bound * 1.0001f;  // (the FP32 sum's rounding)
   }
   int ex;
   frexpf(fmaxf(bound * node_share<P>(), 1.0f), &ex);  // node bound < 2^ex
@@ -660,6 +711,7 @@ __device__ __forceinline__ void scatter_scale(const float* w, const int64_t (&be
     frexpf(fmaxf(wmax * node_share<P>(), 1e-30f), &ex1);  // one addition < 2^ex1
     e = min(e, 22 - ex1);
   }
+  e = min(e, emax);
   *scale = ldexpf(1.0f, e);
   *inv_scale = ldexpf(1.0f, -e);
 }
@@ -700,11 +752,16 @@ __device__ __forceinline__ int next_run(const int64_t* toff, int64_t n, int r, i
 // barrier at the top of each piece separates every use of the staging buffers, buckets and regions.
 // (The tiles of a run are consecutive along z, so the tile index is (t_x N_t + t_y) N_t + t_z and a
 // run is S consecutive indices; S divides N_t.)
-template <int P, bool W, typename R, int S>
+// GT: the grids' element type. float: FP32 grids, the region's fixed-point scale per run; unsigned
+// long long (PK_FIXED64, R = long long): int64 grids at the one scale 2^F from qsrc[2] = sum |w|
+// (fixed_scale), every contribution rounded on its own, so the sums do not depend on the order.
+template <int P, bool W, typename R, int S, typename GT = float>
 __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) == 8 || S >= 4) ? 2 : (S == 2 ? 3 : 4))
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
-                     int64_t n, int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                     int64_t cat_stride, int64_t min_count, int64_t max_count) {
+                     int64_t n, int ng, int ntile, int interlace, GT* __restrict__ g1, GT* __restrict__ g2, int ldz,
+                     int64_t cat_stride, int64_t min_count, int64_t max_count, const double* __restrict__ qsrc = nullptr) {
+  constexpr bool FX = sizeof(GT) == 8;
+  static_assert(!FX || (sizeof(R) == 4 && S == 1 && P <= 4), "the deterministic path: 32-bit regions, single tiles");
   using namespace tiles;
   constexpr int CH = scatter_chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
   {
@@ -808,16 +865,29 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
         rbeg[q] = on ? max(toff[t], int64_t(0)) : 0;
         rend[q] = on ? min(toff[t + 1], n) : 0;
       }
-      scatter_scale<P, W, R, S>(w, rbeg, rend, Sm.red, tid, &scale, &inv_scale);
+      if constexpr (FX) {  // the run's scale 2^e (e <= F) and the shift F - e to the global scale 2^F
+        int fx;
+        frexpf(fixed_scale(qsrc[2]), &fx);
+        scatter_scale<P, W, R, S, true>(w, rbeg, rend, Sm.red, tid, &scale, &inv_scale, fx - 1);
+        int es;
+        frexpf(scale, &es);
+        inv_scale = __int_as_float(fx - es);  // the shift F - e, carried in the float's bits
+      } else {
+        scatter_scale<P, W, R, S>(w, rbeg, rend, Sm.red, tid, &scale, &inv_scale);
+      }
     }
     if (pending) {
-      flush_scatter_region<P, S>(&Sm.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+      if constexpr (FX)
+        flush_region_fixed<region_z<P, S>()>(&Sm.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, __float_as_int(pinv),
+                                             g1, g2, tid, THREADS);
+      else
+        flush_scatter_region<P, S>(&Sm.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
       pending = false;
     }
     const int4* sp = Sm.sp[buf];
     const float* sw = Sm.sw[buf];
     // buckets: stencil origin mod NB per grid, and the record's place in its bucket
-    constexpr int PER = (CH + THREADS - 1) / THREADS, NB = bank_buckets<P>(), LPB = 32 / NB;
+    constexpr int PER = (CH + THREADS - 1) / THREADS, NB = bank_buckets<P, R>(), LPB = 32 / NB;
     int qb[PER][2], rk[PER][2];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
@@ -899,7 +969,13 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
     has_next = advance(nxt);
   }
   __syncthreads();
-  if (pending) flush_scatter_region<P, S>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+  if (pending) {
+    if constexpr (FX)
+      flush_region_fixed<region_z<P, S>()>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, __float_as_int(pinv), g1,
+                                           g2, tid, THREADS);
+    else
+      flush_scatter_region<P, S>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+  }
 }
 
 // ---- cells (dense tiles) ---------------------------------------------------------------------------
@@ -1244,6 +1320,43 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
                                                                            g2, ldz, cat_stride, lo, hi);
   count_launch();
   return cudaGetLastError();
+}
+
+// PK_FIXED64: every tile on the bank-ordered scatter (32-bit regions at a scale 2^e per tile that
+// divides the global 2^F), int64 grids.
+template <int P, bool W>
+static cudaError_t launch_scatter_fixed(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                        bool interlace, const double* wsums, unsigned long long* g1, unsigned long long* g2,
+                                        int ldz, cudaStream_t s) {
+  const int ntile = tiles_per_axis(ng);
+  const int nruns = ntile * ntile * ntile;
+  const size_t smem = sizeof(tiles::ScatterSmem<P, W, int, 1>);
+  auto* kern = k_assign_scatter<P, W, int, 1, unsigned long long>;
+  int per_sm = 1;
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), tiles::SCATTER_THREADS, smem, &per_sm);
+  if (e != cudaSuccess) return e;
+  const dim3 blocks(std::max(1, std::min(nruns, num_sms() * per_sm)), 1);
+  kern<<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, 0, 1, INT64_MAX,
+                                                   wsums);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assign_tiles_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                      bool interlace, const double* wsums, unsigned long long* g1, unsigned long long* g2,
+                                      int ldz, cudaStream_t s) {
+  switch (order) {
+#define PK_FX_CASE(P)                                                                              \
+  case P:                                                                                          \
+    return w ? launch_scatter_fixed<P, true>(p, w, toff, n, ng, interlace, wsums, g1, g2, ldz, s)  \
+             : launch_scatter_fixed<P, false>(p, w, toff, n, ng, interlace, wsums, g1, g2, ldz, s);
+    PK_FX_CASE(1)
+    PK_FX_CASE(2)
+    PK_FX_CASE(3)
+    PK_FX_CASE(4)
+#undef PK_FX_CASE
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // Tiles of at least this many particles accumulate their region in 64-bit fixed point. A 32-bit region

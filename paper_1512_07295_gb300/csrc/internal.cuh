@@ -84,6 +84,11 @@ cudaError_t launch_assign_tile_fixed(int order, const pk_cellpos* p, const float
                                      int ng, bool interlace, const double* wsums, unsigned long long* g1,
                                      unsigned long long* g2, int ldz, cudaStream_t s);
 cudaError_t launch_fixed_to_double(unsigned long long* g, int64_t count, const double* wsums, cudaStream_t s);
+// The deterministic path on the bank-ordered scatter (orders 1..4): every tile, a 32-bit region at a
+// scale 2^e <= the global 2^F = fixed_scale(wsums[2]), added to the int64 grids shifted by F - e.
+cudaError_t launch_assign_tiles_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                      bool interlace, const double* wsums, unsigned long long* g1, unsigned long long* g2,
+                                      int ldz, cudaStream_t s);
 // wsums (3 doubles): [sum w, sum w^2, sum |w|]
 cudaError_t launch_weight_sums(const float* w, int64_t n, double* sums, cudaStream_t s);
 cudaError_t launch_set_sums(double* sums, double s1, double s2, cudaStream_t s);
