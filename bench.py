@@ -642,6 +642,18 @@ def row_c1(dev):
     res.update({"workload": "64^3 Poisson particles, L=1000 Mpc/h, N_G=64, PCS+interlacing, FP64 device positions",
                 "fp32_vs_fp64_max_rel": float(rel.max()), "fp32_vs_fp64_median_rel": float(np.median(rel)),
                 "p_over_shot_noise_first_8_bins": _sig(pks["fp64"][:8] / shot, 4)})
+    # the single-particle check: one particle at (123.4, 567.8, 901.2), FP64 grids: its mass and the
+    # p^3 nodes of each stencil
+    cfg64 = api.Config(ng=ng, box=box, prec="fp64")
+    one = torch.tensor([[123.4, 567.8, 901.2]], dtype=torch.float64, device=dev)
+    g1, g2 = api.assign(one, cfg64)
+    res["single_particle"] = {"grid_sums_minus_1": [float(g1.sum().item() - 1.0), float(g2.sum().item() - 1.0)],
+                              "nonzero_nodes": [int(torch.count_nonzero(g1).item()), int(torch.count_nonzero(g2).item())]}
+    # the lattice check: one particle on every node, so every mode n != 0 of either grid vanishes
+    ax = (torch.arange(ng, dtype=torch.float64, device=dev) + 0.0) * (box / ng)
+    lat = torch.stack(torch.meshgrid(ax, ax, ax, indexing="ij"), dim=-1).reshape(-1, 3).contiguous()
+    plat = api.power(lat, cfg64)[0].cpu().numpy()
+    res["lattice_max_p_over_shot_noise"] = float(np.max(np.abs(plat)) / (box ** 3 / lat.shape[0]))
     return res
 
 

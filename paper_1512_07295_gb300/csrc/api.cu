@@ -319,7 +319,7 @@ pk_status run_assign_into(const pk_config* c, const void* pos, int fmt, const pk
     unsigned long long* g1 = static_cast<unsigned long long*>(grids);
     if ((e = cudaMemsetAsync(g1, 0, all * 8, s)) != cudaSuccess) return cuda_fail(e, "memset");
     prof_mark(2, s);
-    e = launch_assign_tile_fixed(c->order, sorted, w, offsets, n, c->ng, two, wsums, g1, two ? g1 + per : nullptr, ldz, s);
+    e = launch_assign_tiles_fixed(c->order, sorted, w, offsets, n, c->ng, two, wsums, g1, two ? g1 + per : nullptr, ldz, s);
     if (e != cudaSuccess) return cuda_fail(e, "assign (fixed)");
     if ((e = launch_fixed_to_double(g1, int64_t(all), wsums, s)) != cudaSuccess) return cuda_fail(e, "fixed->double");
   }
@@ -581,7 +581,7 @@ pk_status pk_assign(const pk_config* cfg, const void* pos_dev, int32_t pos_forma
   // PK_FIXED64: integer sums in the 8-byte output arrays, converted to double in place.
   unsigned long long* g1 = static_cast<unsigned long long*>(grid1_dev);
   unsigned long long* g2 = static_cast<unsigned long long*>(c.interlace ? grid2_dev : nullptr);
-  e = launch_assign_tile_fixed(c.order, sorted, ws_w, offsets, n, c.ng, c.interlace != 0, sums, g1, g2, c.ng, s);
+  e = launch_assign_tiles_fixed(c.order, sorted, ws_w, offsets, n, c.ng, c.interlace != 0, sums, g1, g2, c.ng, s);
   if (e != cudaSuccess) return cuda_fail(e, "assign (fixed)");
   if ((e = launch_fixed_to_double(g1, per, sums, s)) != cudaSuccess) return cuda_fail(e, "fixed->double");
   if (g2 && (e = launch_fixed_to_double(g2, per, sums, s)) != cudaSuccess) return cuda_fail(e, "fixed->double");

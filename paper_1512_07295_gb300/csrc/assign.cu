@@ -1,13 +1,9 @@
 // a3 mass assignment (eq:delgrid, Sec. 2.3) on the grid and on the grid shifted by H/2 (Sec. 3.1).
 //
-// Two kernels:
-//  - k_assign_direct: one thread per particle, FP64 weights, FP64 global atomics straight into the
-//    grid. This is the plain FP64 path (oracle-parity mode and the baseline the fast path is
-//    measured against): it accepts particles in any order.
-//  - k_assign_tile: particles binned by tile of T^3 cells (pk_bin); one block accumulates a tile's
-//    particles into a shared-memory region of (T+4)^3 nodes per grid (the tile plus the stencil halo
-//    of both grids), then adds the region to the grid in global memory. Accumulator type float
-//    (PK_FP32) or 64-bit fixed point (PK_FIXED64, order-independent integer sums).
+// k_assign_direct: one thread per particle, FP64 weights, FP64 global atomics straight into the grid.
+// This is the plain FP64 path (oracle-parity mode and the baseline the fast path is measured
+// against): it accepts particles in any order. The FP32 and PK_FIXED64 paths run on the tiled kernels
+// of assign_tiles.cu; this file also holds the conversions and weight sums they share.
 #include "internal.cuh"
 
 namespace pk {
@@ -105,138 +101,6 @@ static cudaError_t launch_direct(int order, const void* pos, int fmt, const floa
 cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
                                      bool interlace, double* g1, double* g2, int ldz, cudaStream_t s) {
   return launch_direct<double>(order, pos, fmt, w, n, ng, box, interlace, g1, g2, ldz, s);
-}
-
-// ---- tiled shared-memory path ---------------------------------------------------------------------
-
-template <typename Acc>
-struct AccOps;
-template <>
-struct AccOps<float> {
-  static __device__ __forceinline__ float conv(float v, float) { return v; }
-  static __device__ __forceinline__ void add(float* p, float v) { atomicAdd(p, v); }
-};
-template <>
-struct AccOps<unsigned long long> {
-  static __device__ __forceinline__ unsigned long long conv(float v, float q) {
-    return (unsigned long long)__float2ll_rn(v * q);
-  }
-  static __device__ __forceinline__ void add(unsigned long long* p, unsigned long long v) { atomicAdd(p, v); }
-};
-
-template <int P, typename Acc>
-__device__ __forceinline__ void scatter_region(Acc* __restrict__ reg, int rs, int lx, int ly, int lz, const float* f,
-                                               float wgt, float q) {
-  float wx[P], wy[P], wz[P];
-  const int sx = bspline<P>(f[0], wx), sy = bspline<P>(f[1], wy), sz = bspline<P>(f[2], wz);
-  const int bx = lx + sx, by = ly + sy, bz = lz + sz;
-#pragma unroll
-  for (int a = 0; a < P; ++a) {
-#pragma unroll
-    for (int b = 0; b < P; ++b) {
-      const float wxy = wgt * wx[a] * wy[b];
-      Acc* row = reg + ((bx + a) * rs + (by + b)) * rs + bz;
-#pragma unroll
-      for (int d = 0; d < P; ++d) AccOps<Acc>::add(row + d, AccOps<Acc>::conv(wxy * wz[d], q));
-    }
-  }
-}
-
-template <int P, typename Acc>
-__global__ void __launch_bounds__(256) k_assign_tile(const pk_cellpos* __restrict__ p, const float* __restrict__ w,
-                                                     const int64_t* __restrict__ toff, int64_t n, int ng, int tcells,
-                                                     int ntile, int interlace, const double* __restrict__ wsums,
-                                                     Acc* __restrict__ g1, Acc* __restrict__ g2, int ldz,
-                                                     int64_t cat_grid_stride) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const float q = wsums ? fixed_scale(wsums[2]) : 1.0f;
-  // blockIdx.y selects a catalogue of a batch: its grids and its tile offsets
-  {
-    const int cat = blockIdx.y;
-    g1 += cat * cat_grid_stride;
-    if (g2) g2 += cat * cat_grid_stride;
-    toff += int64_t(cat) * ntile * ntile * ntile;
-  }
-  const int rs = tcells + 4;
-  const int rvol = rs * rs * rs;
-  Acc* r1 = reinterpret_cast<Acc*>(smem_raw);
-  Acc* r2 = r1 + rvol;
-  const int nreg = interlace ? 2 : 1;
-  const int ntiles = ntile * ntile * ntile;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t beg = max(toff[t], int64_t(0)), end = min(toff[t + 1], n);  // clamp untrusted offsets
-    if (beg >= end) continue;
-    for (int i = threadIdx.x; i < nreg * rvol; i += blockDim.x) r1[i] = Acc(0);
-    __syncthreads();
-    const int tz = t % ntile, ty = (t / ntile) % ntile, tx = t / (ntile * ntile);
-    const int ox = tx * tcells - 1, oy = ty * tcells - 1, oz = tz * tcells - 1;  // region origin (grid node)
-    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-      const pk_cellpos r = p[i];
-      const float wgt = w ? w[i] : 1.0f;
-      const int lx = cell_x(r.cell) - ox, ly = cell_y(r.cell) - oy, lz = cell_z(r.cell) - oz;  // in [1, tcells]
-      if (lx < 1 || lx > tcells || ly < 1 || ly > tcells || lz < 1 || lz > tcells) {  // not this tile's particle
-        raise_err(PK_DERR_CELLRANGE);
-        continue;
-      }
-      const float f[3] = {r.fx, r.fy, r.fz};
-      scatter_region<P, Acc>(r1, rs, lx, ly, lz, f, wgt, q);
-      if (interlace) {
-        float f2[3];
-        const int dx = half_shift(f[0], &f2[0]), dy = half_shift(f[1], &f2[1]), dz = half_shift(f[2], &f2[2]);
-        scatter_region<P, Acc>(r2, rs, lx + dx, ly + dy, lz + dz, f2, wgt, q);
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nreg * rvol; i += blockDim.x) {
-      const Acc v = r1[i];
-      if (v != Acc(0)) {
-        const int gi = i / rvol, k = i - gi * rvol;
-        const int rx = k / (rs * rs), ry = (k / rs) % rs, rz = k % rs;
-        Acc* g = gi == 0 ? g1 : g2;
-        AccOps<Acc>::add(g + (int64_t(wrap(ox + rx, ng)) * ng + wrap(oy + ry, ng)) * ldz + wrap(oz + rz, ng), v);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <typename Acc>
-static cudaError_t launch_tile(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
-                               bool interlace, const double* q, Acc* g1, Acc* g2, int ldz, cudaStream_t s, int ncat = 1,
-                               int64_t cat_stride = 0) {
-  const int tcells = kTileCells, ntile = tiles_per_axis(ng);
-  const int rs = tcells + 4;
-  const size_t smem = size_t(2) * rs * rs * rs * sizeof(Acc);
-  const int ntiles = ntile * ntile * ntile;
-  const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * 8 / ncat))), ncat);
-  const int threads = 256;
-  switch (order) {
-    case 1: k_assign_tile<1, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
-    case 2: k_assign_tile<2, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
-    case 3: k_assign_tile<3, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
-    case 4: k_assign_tile<4, Acc><<<blocks, threads, smem, s>>>(p, w, toff, n, ng, tcells, ntile, interlace, q, g1, g2, ldz, cat_stride); count_launch(); break;
-    default: return cudaErrorInvalidValue;  // the tile region holds stencils up to PCS
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
-                                   bool interlace, float* g1, float* g2, int ldz, cudaStream_t s) {
-  return launch_tile<float>(order, p, w, toff, n, ng, interlace, nullptr, g1, g2, ldz, s);
-}
-
-cudaError_t launch_assign_tile_batch(int order, const pk_cellpos* p, const int64_t* toff, int64_t n, int ng, int ncat,
-                                     float* grids, int ldz, cudaStream_t s) {
-  const int64_t per = int64_t(ng) * ng * ldz;
-  return launch_tile<float>(order, p, nullptr, toff, n, ng, true, nullptr, grids, grids + per, ldz, s, ncat, 2 * per);
-}
-
-// PK_FIXED64 runs on the bank-ordered scatter (csrc/assign_tiles.cu): 32-bit regions at a per-tile
-// scale that divides the global one, added to the int64 grids by exact integer shifts.
-cudaError_t launch_assign_tile_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n,
-                                     int ng, bool interlace, const double* wsums, unsigned long long* g1,
-                                     unsigned long long* g2, int ldz, cudaStream_t s) {
-  return launch_assign_tiles_fixed(order, p, w, toff, n, ng, interlace, wsums, g1, g2, ldz, s);
 }
 
 // ---- small helpers ---------------------------------------------------------------------------------

@@ -63,26 +63,17 @@ cudaError_t launch_bin_batch(const pk_cellpos* p, const CatRanges& r, int ng, in
 // assign.cu -- grid layout: node (x, y, z) at element (x * ng + y) * ldz + z of each grid.
 cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const float* w, int64_t n, int ng, double box,
                                      bool interlace, double* g1, double* g2, int ldz, cudaStream_t s);
-cudaError_t launch_assign_tile_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
-                                   bool interlace, float* g1, float* g2, int ldz, cudaStream_t s);
 // FP32 tile assignment (assign_tiles.cu: the scatter on sparse tiles, the key-cell kernel on dense
-// ones, chosen per tile), same layout and binned input as the tiled kernel, any particle order inside
-// a tile; ncat > 1: catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids
-// g + c * cat_stride.
+// ones, chosen per tile), same grid layout, records binned by tile (any particle order inside a tile);
+// ncat > 1: catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids g + c * cat_stride.
 cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
                                     int64_t cat_stride = 0, int run = 1);
 // Tiles per scatter run along z for a configuration (pk_config.tile_run, 0: chosen from the mean
 // tile population n / (ncat N_t^3)).
 int scatter_run(const pk_config* c, int64_t n, int ncat);
-// Batch: ncat catalogues (unit weights, interlaced), catalogue c's tile offsets at toff + c * ntiles and
-// its two grids at grids + c * 2 * ng*ng*ldz.
-cudaError_t launch_assign_tile_batch(int order, const pk_cellpos* p, const int64_t* toff, int64_t n, int ng, int ncat,
-                                     float* grids, int ldz, cudaStream_t s);
-// PK_FIXED64: the scale 2^F is derived on the device from wsums[2] = sum |w|.
-cudaError_t launch_assign_tile_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n,
-                                     int ng, bool interlace, const double* wsums, unsigned long long* g1,
-                                     unsigned long long* g2, int ldz, cudaStream_t s);
+// PK_FIXED64: int64 grids at the scale 2^F derived on the device from wsums[2] = sum |w|, converted in
+// place to FP64.
 cudaError_t launch_fixed_to_double(unsigned long long* g, int64_t count, const double* wsums, cudaStream_t s);
 // The deterministic path on the bank-ordered scatter (orders 1..4): every tile, a 32-bit region at a
 // scale 2^e <= the global 2^F = fixed_scale(wsums[2]), added to the int64 grids shifted by F - e.
