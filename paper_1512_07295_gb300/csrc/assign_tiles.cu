@@ -904,15 +904,15 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
         const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
         qb[u][0] = stencil_origin<P, 0, S>(lx, ly, lz, fx, fy, fz) & (NB - 1);
         rk[u][0] = atomicAdd(&Sm.cnt[0][qb[u][0]], 1);
-        if (interlace) {
+        if (interlace) {  // both grids' records share the buckets (one pool, one set of rounds)
           qb[u][1] = stencil_origin<P, 1, S>(lx, ly, lz, fx, fy, fz) & (NB - 1);
-          rk[u][1] = atomicAdd(&Sm.cnt[1][qb[u][1]], 1);
+          rk[u][1] = atomicAdd(&Sm.cnt[0][qb[u][1]], 1);
         }
       }
     }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
-    if (warp < ngrid) {  // warp g: grid g's bucket offsets, sizes and round count; counts cleared
+    if (warp == 0) {  // the pool's bucket offsets, sizes and round count; counts cleared
       const int c = lane < NB ? Sm.cnt[warp][lane] : 0;
       int incl = c;
 #pragma unroll
@@ -931,30 +931,37 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
       if (lane == 0) Sm.rounds[warp] = mx;
     }
     __syncthreads();
+    unsigned short* list = &Sm.list[0][0];  // the pool: record index, grid in bit 15
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       if (qb[u][0] < 0) continue;
       const unsigned short j = static_cast<unsigned short>(tid + u * THREADS);
-      Sm.list[0][Sm.off[0][qb[u][0]] + rk[u][0]] = j;
-      if (interlace) Sm.list[1][Sm.off[1][qb[u][1]] + rk[u][1]] = j;
+      list[Sm.off[0][qb[u][0]] + rk[u][0]] = j;
+      if (interlace) list[Sm.off[0][qb[u][1]] + rk[u][1]] = static_cast<unsigned short>(j | 0x8000u);
     }
     __syncthreads();
-    // rounds: grid 1's rounds, then grid 2's, dealt to the warps in turn
-    const int r0 = Sm.rounds[0], rtot = r0 + (interlace ? Sm.rounds[1] : 0);
+    // rounds of the pool, dealt to the warps in turn; a lane's grid is that of its record
+    const int rtot = Sm.rounds[0];
     for (int item = warp; item < rtot; item += NWARP) {
-      const int g = item < r0 ? 0 : 1;
-      const int k = (g ? item - r0 : item) * LPB + lane / NB, bkt = lane % NB;
-      if (k >= Sm.nr[g][bkt]) continue;
-      const int j = Sm.list[g][Sm.off[g][bkt] + k];
+      const int k = item * LPB + lane / NB, bkt = lane % NB;
+      if (k >= Sm.nr[0][bkt]) continue;
+      const int e = list[Sm.off[0][bkt] + k];
+      const int j = e & 0x7fff, g = e >> 15;
       const int4 r = sp[j];
       const uint32_t cell = uint32_t(r.x);
-      const int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
-      const float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
+      int lx = cell_x(cell) - cx0, ly = cell_y(cell) - cy0, lz = cell_z(cell) - cz0;
+      float fx = __int_as_float(r.y), fy = __int_as_float(r.z), fz = __int_as_float(r.w);
       const float sc = (W ? sw[j] : 1.0f) * weight_scale<P>() * scale;
-      if (g == 0)
-        scatter_particle<P, 0, S>(Sm.reg[rb][0], lx, ly, lz, fx, fy, fz, sc, lane);
-      else
-        scatter_particle<P, 1, S>(Sm.reg[rb][1], lx, ly, lz, fx, fy, fz, sc, lane);
+      if (g) {  // grid 2 samples the particle shifted by H/2: grid 1's stencil of the shifted position
+        float f2;
+        lx += half_shift(fx, &f2);
+        fx = f2;
+        ly += half_shift(fy, &f2);
+        fy = f2;
+        lz += half_shift(fz, &f2);
+        fz = f2;
+      }
+      scatter_particle<P, 0, S>(Sm.reg[rb][g], lx, ly, lz, fx, fy, fz, sc, lane);
     }
     if (!has_next || nxt.first) {  // last piece of the run: its region is flushed with the next piece
       pending = true;
