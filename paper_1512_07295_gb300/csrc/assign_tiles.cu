@@ -997,18 +997,22 @@ namespace tiles {
 constexpr int CELL_THREADS = 256;
 constexpr int CNT_BINS = 64;  // particle counts above 63 share the first place of the ordering
 
-// Pieces of 64 KB of records: a key cell's window is added to the region once per piece, so larger
-// pieces mean fewer (and fuller) additions; two blocks still fit an SM.
-template <bool W>
+// Records per piece: a key cell's window is added to the region once per piece, so larger pieces
+// mean fewer (and fuller) additions and fewer per-piece sorts. 32-bit regions: the largest piece at
+// which two blocks still fit an SM's 228 KB (20 B per record, 24 with weights, beside ~23 KB of
+// histograms, lists and regions): 4608 records, so that a tile of the mean population 8^3 x 8 = 4096
+// and most of the Poisson and clustering spread above it take one piece. 64-bit regions (heavy tiles,
+// one block per SM): 8192.
+template <bool W, typename R = int>
 __host__ __device__ constexpr int cell_chunk() {
-  return W ? 2048 : 4096;
+  return sizeof(R) == 8 ? (W ? 4096 : 8192) : (W ? 3840 : 4608);
 }
 
 // R: the region's integer type, int (32-bit fixed point) or long long (64-bit, the heavy tiles).
 template <bool W, typename R = int>
 struct CellSmem {
-  int4 sp[cell_chunk<W>()];
-  unsigned short perm[2][cell_chunk<W>()];
+  int4 sp[cell_chunk<W, R>()];
+  unsigned short perm[2][cell_chunk<W, R>()];
   int hist[2][NKEY + 1];  // counts -> exclusive offsets -> bucket ends
   alignas(16) R reg[2][RVOL];
   unsigned short order[2][NKEY];  // non-empty key cells per grid, largest bucket first
@@ -1017,7 +1021,7 @@ struct CellSmem {
   float red[CELL_THREADS / 32];
   int scan[2][CELL_THREADS / 32];
   unsigned long long mbar;
-  float sw[W ? cell_chunk<W>() : 1];
+  float sw[W ? cell_chunk<W, R>() : 1];
 };
 
 // One key cell of grid G: its bucket of particles into a register window, then the window into the
@@ -1064,13 +1068,17 @@ __device__ __forceinline__ void cell_key(const CellSmem<W, R>& S, int key, float
 }
 }  // namespace tiles
 
+static_assert(2 * (sizeof(tiles::CellSmem<false, int>) + 1024) <= 233472 &&
+                  2 * (sizeof(tiles::CellSmem<true, int>) + 1024) <= 233472,
+              "two key-cell blocks (32-bit regions) per SM");
+
 template <int P, bool W, typename R>
 __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     k_assign_cells(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
                    int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
                    int64_t cat_stride, int64_t min_count, int64_t max_count) {
   using namespace tiles;
-  constexpr int CH = cell_chunk<W>(), THREADS = CELL_THREADS, NWARP = THREADS / 32;
+  constexpr int CH = cell_chunk<W, R>(), THREADS = CELL_THREADS, NWARP = THREADS / 32;
   constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
   static_assert(CNT_BINS == 64, "count bins: two per lane of one warp");
   {  // blockIdx.y selects a catalogue of a batch: its grids and its tile offsets

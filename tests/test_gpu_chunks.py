@@ -28,7 +28,7 @@ def _t(a):
 @pytest.mark.parametrize("weighted", [False, True])
 def test_dense_tiles_grids_match_oracle(order, weighted):
     # 48^3 clustered particles on N = 16 (8 tiles of 8^3 cells): ~14k particles per tile, staged in
-    # 7 (unit weights) or 14 (weighted) pieces
+    # 3 (unit weights) or 4 (weighted) pieces of the 32-bit-region kernel
     box, ng = 100.0, 16
     pos = catalogs.zeldovich(48, box, rms=3.0, seed=61)
     w = catalogs.random_weights(len(pos), seed=62).astype(np.float32) if weighted else None
@@ -70,7 +70,7 @@ def test_one_slab_spans_several_pieces(order):
 
 
 def test_binned_layout_in_any_order_inside_a_tile():
-    # one tile of 20000 particles (5 staged pieces); the binned order reversed puts every half-cell
+    # one tile of 20000 particles (a heavy tile: 3 staged pieces); the binned order reversed puts every half-cell
     # slab in descending order: key cells are sorted per piece, so the order inside a tile is free
     box, ng = 8.0, 8
     pos = catalogs.poisson(20000, box, seed=65)
