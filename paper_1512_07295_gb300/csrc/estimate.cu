@@ -366,6 +366,226 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 3) k_estimate(const 
   }
 }
 
+// Loads of the half-complex transforms through the read-only path: L1 keeps the lines that a lane's
+// consecutive slots share with its neighbours' (k_estimate_rows reads 8 or 16 bytes per lane and slot).
+__device__ __forceinline__ C2<float> ld_nc(const C2<float>* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ C2<double> ld_nc(const C2<double>* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+
+// One run of equal bins being summed by a lane: bin (-2: none yet), sum of P, sum of |n|, modes.
+template <typename R>
+struct Run {
+  int b;
+  R v, k;
+  int c;
+};
+
+template <typename R>
+__device__ __forceinline__ void priv_add(PrivBin<R>* pw, unsigned* cw, int b, R v, R k, int c) {
+  PrivBin<R>::add(pw[b].sum, v);
+  PrivBin<R>::add(pw[b].k, k);
+  cw[b] += unsigned(c);
+}
+
+// The single-pass estimate with private bins, by rows: a warp takes whole rows (i_x, i_y) of the
+// half-complex grids, lane l the J = ceil((N/2 + 1) / 32) consecutive slots i_z = l J .. l J + J - 1.
+// Along a row |n| grows with i_z (|n_z| = i_z on every stored slot), so the bins of a row's modes are
+// non-decreasing (the out-of-range modes, bin -1, lie at its two ends) and a lane's slots form runs
+// of equal bins, summed in registers. A run that starts and ends inside one lane holds a bin that no
+// other lane of the row holds: it goes to the warp's private bins at once. The lane's first run
+// (head) and last run (tail) may continue in the neighbouring lanes; one segmented shuffle scan per
+// row joins them: a tail carried on through lanes that hold a single run ends in the next lane's
+// head, or at a lane boundary. Those run ends hold distinct bins too, so no update needs an atomic.
+// Per mode the work is that of k_estimate (the stored mode and its Hermitian partner, the window
+// division, the interlacing combine, the exact bin test); the row's phases, windows and |n_xy|^2 are
+// taken once per lane and row, and the scan once per row instead of once per 32 slots.
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(const C2<R>* __restrict__ G1,
+                                                                              const C2<R>* __restrict__ G2,
+                                                                              const R* __restrict__ tab_g, EstimateArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  {
+    const int cat = blockIdx.y;
+    G1 += cat * a.cat_stride;
+    if (G2) G2 += cat * a.cat_stride;
+    a.wsums += 3 * cat;
+    a.bin_sum += int64_t(cat) * a.nbins;
+    a.bin_k += int64_t(cat) * a.nbins;
+    a.bin_cnt += int64_t(cat) * a.nbins;
+  }
+  const int ng = a.ng;
+  R* tab = reinterpret_cast<R*>(smem_raw);  // 1/W, cos, sin (3 ng); 1/W times the norm (ng); V
+  PrivBin<R>* pbin = reinterpret_cast<PrivBin<R>*>(smem_raw + estimate_smem_table_bytes(ng, sizeof(R)));
+  unsigned* pcnt = reinterpret_cast<unsigned*>(pbin + size_t(kEstWarps) * a.nbins);
+  {
+    const R wsum0 = R(a.wsums[0]);
+    const R norm0 = a.interlace ? R(0.5) / wsum0 : R(1) / wsum0;
+    for (int i = threadIdx.x; i < 3 * ng; i += blockDim.x) tab[i] = tab_g[i];
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) tab[3 * ng + i] = tab_g[i] * norm0;
+    if (threadIdx.x == 0) tab[4 * ng] = R(a.box * a.box * a.box);
+    for (int i = threadIdx.x; i < kEstWarps * a.nbins; i += blockDim.x) {
+      pbin[i].sum = PrivBin<R>::zero();
+      pbin[i].k = PrivBin<R>::zero();
+      pcnt[i] = 0u;
+    }
+  }
+  __syncthreads();
+  const R* winv = tab;
+  const R* pc = tab + ng;
+  const R* ps = tab + 2 * ng;
+  const R* winvz = tab + 3 * ng;
+  const R vol = tab[4 * ng];
+  const int lane = threadIdx.x & 31;
+  const int half = ng / 2, lz = half + 1;
+  const int J = (lz + 31) >> 5;
+  const int z0 = min(lane * J, lz), z1 = min(z0 + J, lz);  // this lane's slots (none for the last lanes of short rows)
+  PrivBin<R>* pw = pbin + (threadIdx.x >> 5) * a.nbins;
+  unsigned* cw = pcnt + (threadIdx.x >> 5) * a.nbins;
+  const bool small_bins = int64_t(a.bin_lo2) + int64_t(a.nbins + 1) * a.bin_w2 <= 46340;
+  const float inv_w2 = 1.0f / float(a.bin_w2);
+  const int rows = ng * ng;
+  const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+  C2<R>* dout = static_cast<C2<R>*>(a.delta_out);
+  const C2<R> zero2 = {R(0), R(0)};
+  for (int row = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); row < rows; row += nwarps) {
+    const int ix = row / ng, iy = row - ix * ng;
+    const int nx = signed_mode(ix, ng), ny = signed_mode(iy, ng);
+    const R wxy = winv[ix] * winv[iy];
+    const C2<R> phx = {pc[ix], ps[ix]}, phy = {pc[iy], ps[iy]};
+    const C2<R> phxy = cmul(phx, phy);
+    // partner phase per axis: conjugate except on the Nyquist slot
+    const C2<R> phxy_p = cmul(ix == half ? phx : conj(phx), iy == half ? phy : conj(phy));
+    const int nxy2 = nx * nx + ny * ny;  // |n|^2 <= 3 (N/2)^2 < 2^20
+    const int64_t rbase = int64_t(row) * lz;
+    // the next two slots' loads are in flight while a slot is evaluated
+    C2<R> q1a = zero2, q2a = zero2, q1b = zero2, q2b = zero2;
+    if (z0 < z1) {
+      q1a = ld_nc(G1 + rbase + z0);
+      if (a.interlace) q2a = ld_nc(G2 + rbase + z0);
+    }
+    if (z0 + 1 < z1) {
+      q1b = ld_nc(G1 + rbase + z0 + 1);
+      if (a.interlace) q2b = ld_nc(G2 + rbase + z0 + 1);
+    }
+    Run<R> head = {-2, R(0), R(0), 0}, cur = {-2, R(0), R(0), 0};
+    for (int iz = z0; iz < z1; ++iz) {
+      const C2<R> g1 = q1a, g2 = q2a;
+      q1a = q1b;
+      q2a = q2b;
+      if (iz + 2 < z1) {
+        q1b = ld_nc(G1 + rbase + iz + 2);
+        if (a.interlace) q2b = ld_nc(G2 + rbase + iz + 2);
+      }
+      const int nz = iz == half ? -half : iz;
+      const int n2 = nxy2 + nz * nz;
+      int b = -1;
+      R val = R(0), ks = R(0);
+      int cnt = 0;
+      C2<R> d = zero2;
+      if (n2 != 0) {
+        const R c = wxy * winvz[iz];
+        const bool partner = iz > 0 && iz < half;
+        C2<R> dp;
+        if (a.interlace) {
+          const C2<R> phz = {pc[iz], ps[iz]};
+          const C2<R> t = cmul(cmul(phxy, phz), g2);
+          d = {(g1.x + t.x) * c, (g1.y + t.y) * c};
+          const C2<R> tp = cmul(cmul(phxy_p, conj(phz)), conj(g2));
+          dp = {(g1.x + tp.x) * c, (-g1.y + tp.y) * c};
+        } else {
+          d = {g1.x * c, g1.y * c};
+          dp = conj(d);
+        }
+        const float rn = sqrtf(float(n2));
+        b = small_bins ? bin_of32(4 * n2, 2.0f * rn, a.bin_lo2, a.bin_w2, inv_w2, a.nbins)
+                       : bin_of(4 * (long long)n2, a.bin_lo2, a.bin_w2, a.nbins);
+        if (b >= 0) {
+          val = d.x * d.x + d.y * d.y;
+          cnt = 1;
+          if (partner) {
+            val += dp.x * dp.x + dp.y * dp.y;
+            cnt = 2;
+          }
+          val *= vol;
+          ks = R(cnt) * (sizeof(R) == 4 ? R(rn) : sqrt(R(n2)));
+        }
+      }
+      if (dout) dout[rbase + iz] = d;
+      if (b == cur.b) {
+        cur.v += val;
+        cur.k += ks;
+        cur.c += cnt;
+      } else {
+        if (cur.b != -2) {  // the run cur.b ended inside this lane
+          if (head.b == -2)
+            head = cur;
+          else if (cur.b >= 0)
+            priv_add(pw, cw, cur.b, cur.v, cur.k, cur.c);
+        }
+        cur = {b, val, ks, cnt};
+      }
+    }
+    if (a.nbins == 0) continue;
+    // the lane's runs at its two ends: one run only (pass) or a head and a tail (cur)
+    const bool pass = head.b == -2;
+    const int first = pass ? cur.b : head.b;
+    const int next_first = __shfl_down_sync(0xffffffffu, first, 1);
+    const bool cont = lane < 31 && cur.b >= 0 && next_first == cur.b;  // the tail goes on in the next lane
+    const bool prev_cont = __shfl_up_sync(0xffffffffu, cont ? 1 : 0, 1) != 0 && lane > 0;
+    // segmented inclusive scan of the tails: a segment is a tail and the single-run lanes it goes on through
+    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || !(prev_cont && pass));
+    const int start = 31 - __clz(starts & ((2u << lane) - 1u));
+    R sv = cur.v, sk = cur.k;
+    int sc = cur.c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const R tv = __shfl_up_sync(0xffffffffu, sv, o);
+      const R tk = __shfl_up_sync(0xffffffffu, sk, o);
+      const int tc = __shfl_up_sync(0xffffffffu, sc, o);
+      if (lane - o >= start) {
+        sv += tv;
+        sk += tk;
+        sc += tc;
+      }
+    }
+    // a head ends the run carried in from the previous lanes
+    const R iv = __shfl_up_sync(0xffffffffu, sv, 1), ik = __shfl_up_sync(0xffffffffu, sk, 1);
+    const int ic = __shfl_up_sync(0xffffffffu, sc, 1);
+    if (!pass && head.b >= 0) {
+      if (prev_cont)
+        priv_add(pw, cw, head.b, head.v + iv, head.k + ik, head.c + ic);
+      else
+        priv_add(pw, cw, head.b, head.v, head.k, head.c);
+    }
+    __syncwarp();
+    if (cur.b >= 0 && !cont) priv_add(pw, cw, cur.b, sv, sk, sc);
+    __syncwarp();
+  }
+  __syncthreads();
+  if (a.nbins == 0) return;
+  for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+    // the warps' pairs combined in their own precision, converted to FP64 once
+    auto vs = PrivBin<R>::zero(), ks = PrivBin<R>::zero();
+    unsigned long long c = 0;
+    for (int q = 0; q < kEstWarps; ++q) {
+      const PrivBin<R>& pb = pbin[q * a.nbins + i];
+      PrivBin<R>::merge(vs, pb.sum);
+      PrivBin<R>::merge(ks, pb.k);
+      c += pcnt[q * a.nbins + i];
+    }
+    if (c) {
+      atomicAdd(&a.bin_sum[i], PrivBin<R>::value(vs));
+      atomicAdd(&a.bin_k[i], PrivBin<R>::value(ks));
+      atomicAdd(&a.bin_cnt[i], c);
+    }
+  }
+}
+
 // Deterministic mode, between the passes: scale_b = 2^F_b with F_b = 62 - ceil(log2(max_b M_b)), so
 // that the int64 sum of a bin's quantised values cannot overflow; then clears the sum accumulators.
 __global__ void k_det_scale(EstimateArgs a) {
@@ -412,16 +632,24 @@ cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, c
   // private bins while they fit in a quarter of an SM's shared memory (nbins up to ~640 in FP32 mode)
   b.priv = (a.det_pass == 0 && priv_bytes <= 56 * 1024) ? 1 : 0;
   const size_t smem = tab_bytes + (b.priv ? priv_bytes : size_t(a.nbins) * 24);
-  if ((e = ensure_dynamic_smem(reinterpret_cast<const void*>(k_estimate<R>), smem)) != cudaSuccess) return e;
+  // the single pass with private bins runs by rows (k_estimate_rows); the deterministic passes and the
+  // bin counts beyond the private bins' room take k_estimate's 32-slot items
+  const void* kern = b.priv ? reinterpret_cast<const void*>(k_estimate_rows<R>) : reinterpret_cast<const void*>(k_estimate<R>);
+  if ((e = ensure_dynamic_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t rows = int64_t(a.ng) * a.ng;
   // every block resident at once (the loop is grid-stride; a second partial wave would idle SMs)
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<R>, kEstWarps * 32, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kEstWarps * 32, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int bx = int(std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, std::max<int64_t>(1, int64_t(num_sms()) * per_sm / a.ncat))));
   const dim3 blocks(bx, a.ncat);
-  k_estimate<R><<<blocks, kEstWarps * 32, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
-                                                     static_cast<const R*>(tables), b); count_launch();
+  if (b.priv)
+    k_estimate_rows<R><<<blocks, kEstWarps * 32, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
+                                                            static_cast<const R*>(tables), b);
+  else
+    k_estimate<R><<<blocks, kEstWarps * 32, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
+                                                       static_cast<const R*>(tables), b);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_estimate<float>(const void*, const void*, void*, const EstimateArgs&, cudaStream_t);
