@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
     // partner phase per axis: conjugate except on the Nyquist slot
     const C2<R> phxy_p = cmul(ix == half ? phx : conj(phx), iy == half ? phy : conj(phy));
     const int nxy2 = nx * nx + ny * ny;  // |n|^2 <= 3 (N/2)^2 < 2^20
+    const bool nyq_row = ix == half || iy == half;  // the partner's phase is not the conjugate there
     const int64_t rbase = int64_t(row) * lz;
     // the next two slots' loads are in flight while a slot is evaluated
     C2<R> q1a = zero2, q2a = zero2, q1b = zero2, q2b = zero2;
@@ -490,29 +491,30 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
       if (n2 != 0) {
         const R c = wxy * winvz[iz];
         const bool partner = iz > 0 && iz < half;
-        C2<R> dp;
+        R vp;  // |delta(-n)|^2
         if (a.interlace) {
           const C2<R> phz = {pc[iz], ps[iz]};
           const C2<R> t = cmul(cmul(phxy, phz), g2);
           d = {(g1.x + t.x) * c, (g1.y + t.y) * c};
-          const C2<R> tp = cmul(cmul(phxy_p, conj(phz)), conj(g2));
-          dp = {(g1.x + tp.x) * c, (-g1.y + tp.y) * c};
+          if (nyq_row) {
+            const C2<R> tp = cmul(cmul(phxy_p, conj(phz)), conj(g2));
+            const C2<R> dp = {(g1.x + tp.x) * c, (-g1.y + tp.y) * c};
+            vp = dp.x * dp.x + dp.y * dp.y;
+          }
         } else {
           d = {g1.x * c, g1.y * c};
-          dp = conj(d);
         }
-        const float rn = sqrtf(float(n2));
+        const R vd = d.x * d.x + d.y * d.y;
+        if (!(a.interlace && nyq_row)) vp = vd;  // delta(-n) = conj delta(n) off the Nyquist rows
+        // |n| = sqrt(n2): n2 < 2^20 converts exactly through the float 2^23 + n2
+        const float rn = sqrtf(__int_as_float(0x4B000000 | n2) - 8388608.0f);
         b = small_bins ? bin_of32(4 * n2, 2.0f * rn, a.bin_lo2, a.bin_w2, inv_w2, a.nbins)
                        : bin_of(4 * (long long)n2, a.bin_lo2, a.bin_w2, a.nbins);
         if (b >= 0) {
-          val = d.x * d.x + d.y * d.y;
-          cnt = 1;
-          if (partner) {
-            val += dp.x * dp.x + dp.y * dp.y;
-            cnt = 2;
-          }
-          val *= vol;
-          ks = R(cnt) * (sizeof(R) == 4 ? R(rn) : sqrt(R(n2)));
+          val = (partner ? vd + vp : vd) * vol;
+          cnt = partner ? 2 : 1;
+          const R r = sizeof(R) == 4 ? R(rn) : sqrt(R(n2));
+          ks = partner ? r + r : r;
         }
       }
       if (dout) dout[rbase + iz] = d;
