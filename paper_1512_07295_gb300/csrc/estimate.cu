@@ -8,9 +8,14 @@
 // phase: on a Nyquist slot (i = N/2, n_i = -N/2) the partner index is again -N/2, so its phase is
 // e^{-i pi/2}, not the conjugate. Both are evaluated from the same loads, so every mode of the full
 // N^3 grid is binned exactly once. P(n) = V |delta(n)|^2 (Sec. 2.2 estimator); bins by the exact
-// integer test e_b^2 <= 4|n|^2 < e_{b+1}^2. Each warp takes 32 consecutive slots of the flattened
-// [i_x][i_y][i_z] array (coalesced loads), reduces runs of equal bins with a shuffle scan and adds the
-// run sums to per-warp shared-memory bins (or per-block FP64 bins), flushed once per block.
+// integer test e_b^2 <= 4|n|^2 < e_{b+1}^2. Two kernels sum the shells:
+//  - k_estimate_rows (the single pass, whenever its private bins fit): warps take whole rows and lanes
+//    runs of consecutive slots, whose equal-bin runs are summed in registers into per-row private
+//    shared-memory bins without atomics;
+//  - k_estimate (the deterministic two-pass mode, and bins too many for private copies): warps take 32
+//    consecutive slots of the flattened [i_x][i_y][i_z] array, reduce runs of equal bins with a
+//    shuffle scan and add the run sums to per-block FP64 (or int64) shared bins.
+// Both flush their bins once per block.
 #include "internal.cuh"
 
 namespace pk {
@@ -49,10 +54,9 @@ size_t estimate_table_bytes(int ng, bool dbl) { return size_t(3) * ng * (dbl ? 8
 // Shared-memory tables of k_estimate: the three global tables, the normalised i_z window and V.
 __host__ __device__ inline size_t estimate_smem_table_bytes(int ng, size_t elem) { return ((size_t(4) * ng + 1) * elem + 15) / 16 * 16; }
 
-// Per-warp private bin accumulators (single pass, non-deterministic mode). Within one warp item the
-// bins of the run ends are distinct (|n| grows with i_z), so a warp updates its own copy without
-// atomics: FP32 mode keeps each sum as an FP32 pair (value, compensation; Neumaier's summation,
-// every term is >= 0), FP64 mode as one double.
+// Private bin accumulators of k_estimate_rows (single pass, non-deterministic mode), one copy per row
+// of a warp, updated without atomics: FP32 mode keeps each sum as an FP32 pair (value, compensation;
+// Neumaier's summation, every term is >= 0), FP64 mode as one double.
 template <typename R>
 struct PrivBin;
 template <>
@@ -78,10 +82,10 @@ struct PrivBin<double> {
   __device__ __forceinline__ static double zero() { return 0.0; }
   __device__ __forceinline__ static void merge(double& acc, double o) { acc += o; }
 };
-constexpr int kEstWarps = 8;  // 256 threads
+constexpr int kEstWarps = 8;  // 256 threads (k_estimate; k_estimate_rows at most)
 
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 3) k_estimate(const C2<R>* __restrict__ G1, const C2<R>* __restrict__ G2,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 3) k_estimate(const C2<R>* __restrict__ G1, const C2<R>* __restrict__ G2,
                                                   const R* __restrict__ tab_g, EstimateArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {
@@ -99,8 +103,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 3) k_estimate(const 
   double* s_sum = reinterpret_cast<double*>(bins_raw);
   double* s_k = s_sum + a.nbins;
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_k + a.nbins);
-  PrivBin<R>* pbin = reinterpret_cast<PrivBin<R>*>(bins_raw);  // [kEstWarps][nbins] when a.priv
-  unsigned* pcnt = reinterpret_cast<unsigned*>(pbin + size_t(kEstWarps) * a.nbins);
   {
     // the normalisation 1 / (2 sum w) (1 / sum w without interlacing) rides on the i_z window, and V
     // is kept beside the tables: both are read from shared memory in the loop, not recomputed
@@ -110,18 +112,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 3) k_estimate(const 
     for (int i = threadIdx.x; i < ng; i += blockDim.x) tab[3 * ng + i] = tab_g[i] * norm0;
     if (threadIdx.x == 0) tab[4 * ng] = R(a.box * a.box * a.box);
   }
-  if (a.priv) {
-    for (int i = threadIdx.x; i < kEstWarps * a.nbins; i += blockDim.x) {
-      pbin[i].sum = PrivBin<R>::zero();
-      pbin[i].k = PrivBin<R>::zero();
-      pcnt[i] = 0u;
-    }
-  } else {
-    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
-      s_sum[i] = 0.0;
-      s_k[i] = 0.0;
-      s_cnt[i] = 0ull;
-    }
+  for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+    s_sum[i] = 0.0;
+    s_k[i] = 0.0;
+    s_cnt[i] = 0ull;
   }
   __syncthreads();
   const R* winv = tab;
@@ -275,22 +269,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 3) k_estimate(const 
         // the run's mode count: its lanes with one mode plus its lanes with two
         const unsigned run = ((2u << lane) - 1u) & ~((1u << start) - 1u);
         const int sc = __popc(__ballot_sync(0xffffffffu, cnt >= 1) & run) + __popc(__ballot_sync(0xffffffffu, cnt == 2) & run);
-        if (!a.priv && end && b >= 0) {
+        if (end && b >= 0) {
           atomicAdd(&s_sum[b], double(sv));
           atomicAdd(&s_k[b], double(sk));
           atomicAdd(&s_cnt[b], (unsigned long long)sc);
-        }
-        if (a.priv) {  // run ends of one row have distinct bins, of two rows maybe not: rows in turn
-          const int nseg = __reduce_max_sync(0xffffffffu, rseg) + 1;
-          for (int seg = 0; seg < nseg; ++seg) {
-            if (end && b >= 0 && rseg == seg) {
-              PrivBin<R>& pb = pbin[(threadIdx.x >> 5) * a.nbins + b];
-              PrivBin<R>::add(pb.sum, sv);
-              PrivBin<R>::add(pb.k, sk);
-              pcnt[(threadIdx.x >> 5) * a.nbins + b] += unsigned(sc);
-            }
-            __syncwarp();
-          }
         }
       } else if (a.det_pass == 1) {  // deterministic mode, pass 1: per-bin maximum and mode count
         double sv = double(val);
@@ -330,24 +312,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 3) k_estimate(const 
   __syncthreads();
   if (a.nbins == 0) return;
   for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
-    if (a.priv) {
-      // the warps' pairs combined in their own precision, converted to FP64 once (FP64 and
-      // conversions to it run at a small fraction of the FP32 rate on this GPU)
-      auto vs = PrivBin<R>::zero(), ks = PrivBin<R>::zero();
-      unsigned long long c = 0;
-      for (int q = 0; q < kEstWarps; ++q) {
-        const PrivBin<R>& pb = pbin[q * a.nbins + i];
-        PrivBin<R>::merge(vs, pb.sum);
-        PrivBin<R>::merge(ks, pb.k);
-        c += pcnt[q * a.nbins + i];
-      }
-      const double v = PrivBin<R>::value(vs), k = PrivBin<R>::value(ks);
-      if (c) {
-        atomicAdd(&a.bin_sum[i], v);
-        atomicAdd(&a.bin_k[i], k);
-        atomicAdd(&a.bin_cnt[i], c);
-      }
-    } else if (a.det_pass == 0) {
+    if (a.det_pass == 0) {
       if (s_cnt[i]) {
         atomicAdd(&a.bin_sum[i], s_sum[i]);
         atomicAdd(&a.bin_k[i], s_k[i]);
@@ -393,18 +358,21 @@ __device__ __forceinline__ void priv_add(PrivBin<R>* pw, unsigned* cw, int b, R 
 }
 
 // The single-pass estimate with private bins, by rows: a warp takes whole rows (i_x, i_y) of the
-// half-complex grids, lane l the J = ceil((N/2 + 1) / 32) consecutive slots i_z = l J .. l J + J - 1.
+// half-complex grids, RW rows at a time (RW = 1 for N >= 256; short rows share a warp), and lane s of
+// a row's L = 32 / RW lanes takes the J = ceil((N/2 + 1) / L) consecutive slots i_z = s J .. s J + J - 1.
 // Along a row |n| grows with i_z (|n_z| = i_z on every stored slot), so the bins of a row's modes are
 // non-decreasing (the out-of-range modes, bin -1, lie at its two ends) and a lane's slots form runs
 // of equal bins, summed in registers. A run that starts and ends inside one lane holds a bin that no
-// other lane of the row holds: it goes to the warp's private bins at once. The lane's first run
-// (head) and last run (tail) may continue in the neighbouring lanes; one segmented shuffle scan per
-// row joins them: a tail carried on through lanes that hold a single run ends in the next lane's
-// head, or at a lane boundary. Those run ends hold distinct bins too, so no update needs an atomic.
-// Per mode the work is that of k_estimate (the stored mode and its Hermitian partner, the window
-// division, the interlacing combine, the exact bin test); the row's phases, windows and |n_xy|^2 are
-// taken once per lane and row, and the scan once per row instead of once per 32 slots.
-template <typename R>
+// other lane of the row holds: it goes to the row's private bins at once (one copy per row of the
+// warp, so rows never meet). The lane's first run (head) and last run (tail) may continue in the
+// neighbouring lanes of the row; one segmented shuffle scan per row joins them: a tail carried on
+// through lanes that hold a single run ends in the next lane's head, or at a lane boundary. Those run
+// ends hold distinct bins too, so no update needs an atomic. Per mode the work is that of k_estimate
+// (the stored mode and its Hermitian partner, the window division, the interlacing combine, the exact
+// bin test); the row's phases, windows and |n_xy|^2 are taken once per lane and row, and the scan
+// once per row instead of once per 32 slots. Blocks of 2 to 8 warps (fewer when the bins are many).
+// SMALL: every bin edge squared fits 32 bits (bin_lo2 + (nbins + 1) bin_w2 <= 46340), the 32-bit bin test.
+template <typename R, bool SMALL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(const C2<R>* __restrict__ G1,
                                                                               const C2<R>* __restrict__ G2,
                                                                               const R* __restrict__ tab_g, EstimateArgs a) {
@@ -419,16 +387,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
     a.bin_cnt += int64_t(cat) * a.nbins;
   }
   const int ng = a.ng;
+  const int RW = a.rows_per_warp, ncopy = int(blockDim.x >> 5) * RW;  // private bin copies of the block
   R* tab = reinterpret_cast<R*>(smem_raw);  // 1/W, cos, sin (3 ng); 1/W times the norm (ng); V
   PrivBin<R>* pbin = reinterpret_cast<PrivBin<R>*>(smem_raw + estimate_smem_table_bytes(ng, sizeof(R)));
-  unsigned* pcnt = reinterpret_cast<unsigned*>(pbin + size_t(kEstWarps) * a.nbins);
+  unsigned* pcnt = reinterpret_cast<unsigned*>(pbin + size_t(ncopy) * a.nbins);
   {
     const R wsum0 = R(a.wsums[0]);
     const R norm0 = a.interlace ? R(0.5) / wsum0 : R(1) / wsum0;
     for (int i = threadIdx.x; i < 3 * ng; i += blockDim.x) tab[i] = tab_g[i];
     for (int i = threadIdx.x; i < ng; i += blockDim.x) tab[3 * ng + i] = tab_g[i] * norm0;
     if (threadIdx.x == 0) tab[4 * ng] = R(a.box * a.box * a.box);
-    for (int i = threadIdx.x; i < kEstWarps * a.nbins; i += blockDim.x) {
+    for (int i = threadIdx.x; i < ncopy * a.nbins; i += blockDim.x) {
       pbin[i].sum = PrivBin<R>::zero();
       pbin[i].k = PrivBin<R>::zero();
       pcnt[i] = 0u;
@@ -442,17 +411,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
   const R vol = tab[4 * ng];
   const int lane = threadIdx.x & 31;
   const int half = ng / 2, lz = half + 1;
-  const int J = (lz + 31) >> 5;
-  const int z0 = min(lane * J, lz), z1 = min(z0 + J, lz);  // this lane's slots (none for the last lanes of short rows)
-  PrivBin<R>* pw = pbin + (threadIdx.x >> 5) * a.nbins;
-  unsigned* cw = pcnt + (threadIdx.x >> 5) * a.nbins;
-  const bool small_bins = int64_t(a.bin_lo2) + int64_t(a.nbins + 1) * a.bin_w2 <= 46340;
+  const int L = 32 / RW, grp = lane / L, sub = lane - grp * L;  // the lane's row of the warp, its place in it
+  const int J = (lz + L - 1) / L;
+  const int zb = min(sub * J, lz), ze = min(zb + J, lz);  // this lane's slots (none for the last lanes of a row)
+  PrivBin<R>* pw = pbin + ((threadIdx.x >> 5) * RW + grp) * a.nbins;
+  unsigned* cw = pcnt + ((threadIdx.x >> 5) * RW + grp) * a.nbins;
   const float inv_w2 = 1.0f / float(a.bin_w2);
   const int rows = ng * ng;
   const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
   C2<R>* dout = static_cast<C2<R>*>(a.delta_out);
   const C2<R> zero2 = {R(0), R(0)};
-  for (int row = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); row < rows; row += nwarps) {
+  for (int row0 = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * RW; row0 < rows; row0 += nwarps * RW) {
+    const int row = min(row0 + grp, rows - 1);
+    const int z0 = row0 + grp < rows ? zb : lz, z1 = row0 + grp < rows ? ze : lz;  // rows past the last: no slots
     const int ix = row / ng, iy = row - ix * ng;
     const int nx = signed_mode(ix, ng), ny = signed_mode(iy, ng);
     const R wxy = winv[ix] * winv[iy];
@@ -464,23 +435,28 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
     const bool nyq_row = ix == half || iy == half;  // the partner's phase is not the conjugate there
     const int64_t rbase = int64_t(row) * lz;
     // the next two slots' loads are in flight while a slot is evaluated
-    C2<R> q1a = zero2, q2a = zero2, q1b = zero2, q2b = zero2;
-    if (z0 < z1) {
-      q1a = ld_nc(G1 + rbase + z0);
-      if (a.interlace) q2a = ld_nc(G2 + rbase + z0);
-    }
-    if (z0 + 1 < z1) {
-      q1b = ld_nc(G1 + rbase + z0 + 1);
-      if (a.interlace) q2b = ld_nc(G2 + rbase + z0 + 1);
+    constexpr int PF = 2;
+    C2<R> q1[PF], q2[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      q1[u] = zero2;
+      q2[u] = zero2;
+      if (z0 + u < z1) {
+        q1[u] = ld_nc(G1 + rbase + z0 + u);
+        if (a.interlace) q2[u] = ld_nc(G2 + rbase + z0 + u);
+      }
     }
     Run<R> head = {-2, R(0), R(0), 0}, cur = {-2, R(0), R(0), 0};
     for (int iz = z0; iz < z1; ++iz) {
-      const C2<R> g1 = q1a, g2 = q2a;
-      q1a = q1b;
-      q2a = q2b;
-      if (iz + 2 < z1) {
-        q1b = ld_nc(G1 + rbase + iz + 2);
-        if (a.interlace) q2b = ld_nc(G2 + rbase + iz + 2);
+      const C2<R> g1 = q1[0], g2 = q2[0];
+#pragma unroll
+      for (int u = 0; u + 1 < PF; ++u) {
+        q1[u] = q1[u + 1];
+        q2[u] = q2[u + 1];
+      }
+      if (iz + PF < z1) {
+        q1[PF - 1] = ld_nc(G1 + rbase + iz + PF);
+        if (a.interlace) q2[PF - 1] = ld_nc(G2 + rbase + iz + PF);
       }
       const int nz = iz == half ? -half : iz;
       const int n2 = nxy2 + nz * nz;
@@ -508,8 +484,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
         if (!(a.interlace && nyq_row)) vp = vd;  // delta(-n) = conj delta(n) off the Nyquist rows
         // |n| = sqrt(n2): n2 < 2^20 converts exactly through the float 2^23 + n2
         const float rn = sqrtf(__int_as_float(0x4B000000 | n2) - 8388608.0f);
-        b = small_bins ? bin_of32(4 * n2, 2.0f * rn, a.bin_lo2, a.bin_w2, inv_w2, a.nbins)
-                       : bin_of(4 * (long long)n2, a.bin_lo2, a.bin_w2, a.nbins);
+        if constexpr (SMALL)
+          b = bin_of32(4 * n2, 2.0f * rn, a.bin_lo2, a.bin_w2, inv_w2, a.nbins);
+        else
+          b = bin_of(4 * (long long)n2, a.bin_lo2, a.bin_w2, a.nbins);
         if (b >= 0) {
           val = (partner ? vd + vp : vd) * vol;
           cnt = partner ? 2 : 1;
@@ -537,10 +515,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
     const bool pass = head.b == -2;
     const int first = pass ? cur.b : head.b;
     const int next_first = __shfl_down_sync(0xffffffffu, first, 1);
-    const bool cont = lane < 31 && cur.b >= 0 && next_first == cur.b;  // the tail goes on in the next lane
-    const bool prev_cont = __shfl_up_sync(0xffffffffu, cont ? 1 : 0, 1) != 0 && lane > 0;
+    const bool cont = sub < L - 1 && cur.b >= 0 && next_first == cur.b;  // the tail goes on in the next lane
+    const bool prev_cont = __shfl_up_sync(0xffffffffu, cont ? 1 : 0, 1) != 0 && sub > 0;
     // segmented inclusive scan of the tails: a segment is a tail and the single-run lanes it goes on through
-    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || !(prev_cont && pass));
+    const unsigned starts = __ballot_sync(0xffffffffu, sub == 0 || !(prev_cont && pass));
     const int start = 31 - __clz(starts & ((2u << lane) - 1u));
     R sv = cur.v, sk = cur.k;
     int sc = cur.c;
@@ -574,7 +552,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_estimate_rows(c
     // the warps' pairs combined in their own precision, converted to FP64 once
     auto vs = PrivBin<R>::zero(), ks = PrivBin<R>::zero();
     unsigned long long c = 0;
-    for (int q = 0; q < kEstWarps; ++q) {
+    for (int q = 0; q < ncopy; ++q) {
       const PrivBin<R>& pb = pbin[q * a.nbins + i];
       PrivBin<R>::merge(vs, pb.sum);
       PrivBin<R>::merge(ks, pb.k);
@@ -630,23 +608,43 @@ cudaError_t launch_estimate_pass(const void* G1, const void* G2, void* tables, c
   if (e != cudaSuccess) return e;
   EstimateArgs b = a;
   const size_t tab_bytes = estimate_smem_table_bytes(a.ng, sizeof(R));
-  const size_t priv_bytes = size_t(kEstWarps) * a.nbins * (sizeof(PrivBin<R>) + sizeof(unsigned));
-  // private bins while they fit in a quarter of an SM's shared memory (nbins up to ~640 in FP32 mode)
-  b.priv = (a.det_pass == 0 && priv_bytes <= 56 * 1024) ? 1 : 0;
-  const size_t smem = tab_bytes + (b.priv ? priv_bytes : size_t(a.nbins) * 24);
-  // the single pass with private bins runs by rows (k_estimate_rows); the deterministic passes and the
-  // bin counts beyond the private bins' room take k_estimate's 32-slot items
-  const void* kern = b.priv ? reinterpret_cast<const void*>(k_estimate_rows<R>) : reinterpret_cast<const void*>(k_estimate<R>);
+  const size_t bin_bytes = size_t(a.nbins) * (sizeof(PrivBin<R>) + sizeof(unsigned));
+  // The single pass runs by rows (k_estimate_rows) with private bins in at most 96 KB, so that two
+  // blocks still fit an SM (N = 1024: 512 bins, eight copies, 80 KB): RW rows per warp, the fewest that leave at most a fifth of the lane slots idle
+  // (RW = 1 from N = 256 on), and blocks of 8 warps, else 4 or 2 when the bins are many. The
+  // deterministic passes, and bins beyond that room, take k_estimate's 32-slot items with shared
+  // atomics.
+  int wpb = 0;
+  if (a.det_pass == 0) {
+    const int lz = a.ng / 2 + 1;
+    for (int rw = 1; rw <= 32 && !wpb; rw *= 2) {
+      const int L = 32 / rw, J = (lz + L - 1) / L;
+      if (rw < 32 && 5 * lz < 4 * L * J) continue;  // more than a fifth of the slots idle
+      b.rows_per_warp = rw;
+      for (int w = kEstWarps; w >= 2 && !wpb; w /= 2)
+        if (size_t(w) * rw * bin_bytes <= 96 * 1024) wpb = w;
+    }
+  }
+  b.priv = wpb ? 1 : 0;
+  const int threads = wpb ? 32 * wpb : kEstWarps * 32;
+  const size_t smem = tab_bytes + (wpb ? size_t(wpb) * b.rows_per_warp * bin_bytes : size_t(a.nbins) * 24);
+  const bool small = int64_t(a.bin_lo2) + int64_t(a.nbins + 1) * a.bin_w2 <= 46340;
+  const void* kern = !wpb ? reinterpret_cast<const void*>(k_estimate<R>)
+                     : small ? reinterpret_cast<const void*>(k_estimate_rows<R, true>)
+                             : reinterpret_cast<const void*>(k_estimate_rows<R, false>);
   if ((e = ensure_dynamic_smem(kern, smem)) != cudaSuccess) return e;
   const int64_t rows = int64_t(a.ng) * a.ng;
   // every block resident at once (the loop is grid-stride; a second partial wave would idle SMs)
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kEstWarps * 32, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int bx = int(std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, std::max<int64_t>(1, int64_t(num_sms()) * per_sm / a.ncat))));
   const dim3 blocks(bx, a.ncat);
-  if (b.priv)
-    k_estimate_rows<R><<<blocks, kEstWarps * 32, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
+  if (b.priv && small)
+    k_estimate_rows<R, true><<<blocks, threads, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
+                                                           static_cast<const R*>(tables), b);
+  else if (b.priv)
+    k_estimate_rows<R, false><<<blocks, threads, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),
                                                             static_cast<const R*>(tables), b);
   else
     k_estimate<R><<<blocks, kEstWarps * 32, smem, s>>>(static_cast<const C2<R>*>(G1), static_cast<const C2<R>*>(G2),

@@ -105,6 +105,8 @@ struct EstimateArgs {
   double* det_scale = nullptr;
   // set by the launcher: per-warp private bins in shared memory instead of shared atomics
   int priv = 0;
+  // set by the launcher for the row kernel: rows a warp takes at once (a private bin copy each)
+  int rows_per_warp = 1;
 };
 size_t estimate_table_bytes(int ng, bool dbl);
 template <typename R>
