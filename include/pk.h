@@ -232,7 +232,7 @@ pk_status pk_power_backward(const pk_config* cfg, const void* pos_dev, int32_t p
 /* a9 -- Batched power spectra of n_cat independent catalogues (PK_FP32 only, unit weights):
  * catalogue c holds particles offsets_host[c] .. offsets_host[c+1]-1 of pos_dev (pk_cellpos, any
  * order within a catalogue, offsets non-decreasing). Outputs pk_dev / nmodes_dev: [n_cat][nbins].
- * Groups of `batch` catalogues (1..128) are binned, assigned, transformed (one batched cuFFT) and
+ * Groups of `batch` catalogues (1..512) are binned, assigned, transformed (one batched cuFFT) and
  * estimated together with a fixed number of launches per group and no host synchronisation, so the
  * whole call can be captured in a CUDA graph. ws sized by pk_batch_workspace_size. */
 pk_status pk_batch_power(const pk_config* cfg, int32_t n_cat, const int64_t* offsets_host,

@@ -334,7 +334,7 @@ def batch_power(cells, offsets, cfg, batch=64, ws=None, out=None):
     return pk, nm
 
 
-def autotune_batch(cells, offsets, cfg, candidates=(16, 32, 64, 128), reps=3, runs=None):
+def autotune_batch(cells, offsets, cfg, candidates=(32, 64, 128, 256, 512), reps=3, runs=None):
     """Chooses the group size of batch_power for these catalogues by timing each candidate (CUDA
     events, after one warm-up call each). Returns (best, {candidate: ms}). The group size sets how
     many catalogues share each batched launch: larger groups fill the GPU with fewer launches but
@@ -361,7 +361,7 @@ def autotune_batch(cells, offsets, cfg, candidates=(16, 32, 64, 128), reps=3, ru
     nm = torch.empty((ncat, cfg.nb), dtype=torch.int64, device=cells.device)
     times = {}
     for b in candidates:
-        b = int(min(max(b, 1), 128))
+        b = int(min(max(b, 1), 512))
         ws = batch_workspace(cfg, b, max_group_particles(offs, b), cells.device)
         batch_power(cells, offs, cfg, batch=b, ws=ws, out=(pk, nm))
         torch.cuda.synchronize()  # the warm-up call (plans, attributes) ends before the timed calls start

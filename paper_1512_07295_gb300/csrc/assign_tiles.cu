@@ -759,21 +759,17 @@ template <int P, bool W, typename R, int S, typename GT = float>
 __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) == 8 || S >= 4) ? 2 : (S == 2 ? 3 : 4))
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
                      int64_t n, int ng, int ntile, int interlace, GT* __restrict__ g1, GT* __restrict__ g2, int ldz,
-                     int64_t cat_stride, int64_t min_count, int64_t max_count, const double* __restrict__ qsrc = nullptr) {
+                     int64_t cat_stride, int64_t min_count, int64_t max_count, int ncat, const double* __restrict__ qsrc = nullptr) {
   constexpr bool FX = sizeof(GT) == 8;
   static_assert(!FX || (sizeof(R) == 4 && S == 1 && P <= 4), "the deterministic path: 32-bit regions, single tiles");
   using namespace tiles;
   constexpr int CH = scatter_chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
-  {
-    const int cat = blockIdx.y;
-    g1 += cat * cat_stride;
-    if (g2) g2 += cat * cat_stride;
-    toff += int64_t(cat) * ntile * ntile * ntile;
-  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<P, W, R, S>& Sm = *reinterpret_cast<ScatterSmem<P, W, R, S>*>(smem_raw);
   const int ngrid = interlace ? 2 : 1;
-  const int nruns = ntile * ntile * (ntile / S);
+  // runs of all catalogues of a batch in one sequence: run R of catalogue R / nruns_cat covers the tiles
+  // R S .. R S + S - 1 of the catalogues' consecutive tile offsets, so the blocks share every catalogue
+  const int nruns_cat = ntile * ntile * (ntile / S), nruns = ncat * nruns_cat;
   const int tid = threadIdx.x;
   if (tid < 2) {
     const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&Sm.mbar[tid]));
@@ -832,6 +828,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
   int cx0 = 0, cy0 = 0, cz0 = 0;
   bool pending = false;  // the previous run's region (rb ^ 1) is still to be flushed
   int pcx0 = 0, pcy0 = 0, pcz0 = 0;
+  int ccat = 0, pcat = 0;  // catalogues of the current and of the pending run
   float pinv = 1.0f;
   while (true) {
     const int m = int(min(int64_t(CH), cur.end - cur.c0));
@@ -853,7 +850,9 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
     }
     if (cur.first) {  // first piece of a run: the other region, the run's origin and scale
       rb ^= 1;
-      const int rz = cur.run % (ntile / S), ty = (cur.run / (ntile / S)) % ntile, tx = cur.run / ((ntile / S) * ntile);
+      const int cat = cur.run / nruns_cat, run = cur.run - cat * nruns_cat;
+      ccat = cat;
+      const int rz = run % (ntile / S), ty = (run / (ntile / S)) % ntile, tx = run / ((ntile / S) * ntile);
       cx0 = tx * T;
       cy0 = ty * T;
       cz0 = rz * S * T;
@@ -879,9 +878,10 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
     if (pending) {
       if constexpr (FX)
         flush_region_fixed<region_z<P, S>()>(&Sm.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, __float_as_int(pinv),
-                                             g1, g2, tid, THREADS);
+                                             g1 + pcat * cat_stride, g2 ? g2 + pcat * cat_stride : nullptr, tid, THREADS);
       else
-        flush_scatter_region<P, S>(&Sm.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+        flush_scatter_region<P, S>(&Sm.reg[rb ^ 1][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1 + pcat * cat_stride,
+                                   g2 ? g2 + pcat * cat_stride : nullptr, tid, THREADS);
       pending = false;
     }
     const int4* sp = Sm.sp[buf];
@@ -966,6 +966,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
     if (!has_next || nxt.first) {  // last piece of the run: its region is flushed with the next piece
       pending = true;
       pcx0 = cx0;
+      pcat = ccat;
       pcy0 = cy0;
       pcz0 = cz0;
       pinv = inv_scale;
@@ -978,10 +979,11 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) =
   __syncthreads();
   if (pending) {
     if constexpr (FX)
-      flush_region_fixed<region_z<P, S>()>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, __float_as_int(pinv), g1,
-                                           g2, tid, THREADS);
+      flush_region_fixed<region_z<P, S>()>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, __float_as_int(pinv),
+                                           g1 + pcat * cat_stride, g2 ? g2 + pcat * cat_stride : nullptr, tid, THREADS);
     else
-      flush_scatter_region<P, S>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1, g2, tid, THREADS);
+      flush_scatter_region<P, S>(&Sm.reg[rb][0][0], ngrid, pcx0, pcy0, pcz0, ng, ldz, pinv, g1 + pcat * cat_stride,
+                                 g2 ? g2 + pcat * cat_stride : nullptr, tid, THREADS);
   }
 }
 
@@ -1076,22 +1078,17 @@ template <int P, bool W, typename R>
 __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     k_assign_cells(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
                    int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                   int64_t cat_stride, int64_t min_count, int64_t max_count) {
+                   int64_t cat_stride, int64_t min_count, int64_t max_count, int ncat) {
   using namespace tiles;
   constexpr int CH = cell_chunk<W, R>(), THREADS = CELL_THREADS, NWARP = THREADS / 32;
   constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
   static_assert(CNT_BINS == 64, "count bins: two per lane of one warp");
-  {  // blockIdx.y selects a catalogue of a batch: its grids and its tile offsets
-    const int cat = blockIdx.y;
-    g1 += cat * cat_stride;
-    if (g2) g2 += cat * cat_stride;
-    toff += int64_t(cat) * ntile * ntile * ntile;
-  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CellSmem<W, R>& S = *reinterpret_cast<CellSmem<W, R>*>(smem_raw);
   constexpr int BITS = sizeof(R) == 8 ? 62 : 30;  // node bound x scale < 2^BITS
   const int ngrid = interlace ? 2 : 1;
-  const int ntiles = ntile * ntile * ntile;
+  // the tiles of all catalogues of a batch in one sequence (catalogue t / ntiles_cat, consecutive offsets)
+  const int ntiles_cat = ntile * ntile * ntile, ntiles = ncat * ntiles_cat;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     const unsigned b = static_cast<unsigned>(__cvta_generic_to_shared(&S.mbar));
@@ -1105,7 +1102,10 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
   for (int tile = next_tile(toff, n, blockIdx.x, gridDim.x, ntiles, min_count, max_count), nt = 0; tile < ntiles; tile = nt) {
     nt = next_tile(toff, n, tile + int(gridDim.x), int(gridDim.x), ntiles, min_count, max_count);
     const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
-    const int tz = tile % ntile, ty = (tile / ntile) % ntile, tx = tile / (ntile * ntile);
+    const int cat = tile / ntiles_cat, lt = tile - cat * ntiles_cat;
+    float* const cg1 = g1 + cat * cat_stride;
+    float* const cg2 = g2 ? g2 + cat * cat_stride : nullptr;
+    const int tz = lt % ntile, ty = (lt / ntile) % ntile, tx = lt / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
     float scale, inv_scale;
     tile_scale<P, W, BITS>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
@@ -1277,7 +1277,7 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
       }
       __syncthreads();
     }
-    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, g1, g2, tid, THREADS);
+    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, cg1, cg2, tid, THREADS);
     __syncthreads();
   }
 }
@@ -1330,9 +1330,11 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
   int per_sm = 1;
   cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W, R, S>), tiles::SCATTER_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
-  const dim3 blocks(std::max(1, std::min(nruns, std::max(1, num_sms() * per_sm / ncat))), ncat);
+  // one sequence of runs over all catalogues (blocks take runs of any catalogue, so uneven catalogues
+  // leave no tail of idle blocks)
+  const dim3 blocks(unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(nruns) * ncat, int64_t(num_sms()) * per_sm))), 1);
   k_assign_scatter<P, W, R, S><<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1,
-                                                                           g2, ldz, cat_stride, lo, hi);
+                                                                           g2, ldz, cat_stride, lo, hi, ncat);
   count_launch();
   return cudaGetLastError();
 }
@@ -1352,7 +1354,7 @@ static cudaError_t launch_scatter_fixed(const pk_cellpos* p, const float* w, con
   if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(nruns, num_sms() * per_sm)), 1);
   kern<<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, 0, 1, INT64_MAX,
-                                                   wsums);
+                                                   1, wsums);
   count_launch();
   return cudaGetLastError();
 }
@@ -1393,9 +1395,9 @@ static cudaError_t launch_cells_one(const pk_cellpos* p, const float* w, const i
   int per_sm = 1;
   cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_cells<P, W, R>), tiles::CELL_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
-  const dim3 blocks(std::max(1, std::min(ntiles, std::max(1, num_sms() * per_sm / ncat))), ncat);
+  const dim3 blocks(unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(ntiles) * ncat, int64_t(num_sms()) * per_sm))), 1);
   k_assign_cells<P, W, R><<<blocks, tiles::CELL_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
-                                                                    cat_stride, lo, hi);
+                                                                    cat_stride, lo, hi, ncat);
   count_launch();
   return cudaGetLastError();
 }

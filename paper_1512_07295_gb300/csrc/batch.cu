@@ -1,7 +1,8 @@
 // a9 batched power spectra of many independent catalogues (mock catalogues): per group of up to
 // kMaxBatch catalogues, one batched counting sort (key = catalogue * ntiles + tile), one tiled
-// assignment launch over all (catalogue, tile) pairs (blockIdx.y = catalogue), one batched cuFFT of
-// all 2 x batch grids, one fused estimate launch and one finalisation launch. No host
+// assignment launch per kernel over all (catalogue, tile) pairs as one sequence (blocks take tiles of
+// any catalogue, so catalogues of uneven sizes leave no tail), one batched cuFFT of all 2 x batch
+// grids, one fused estimate launch and one finalisation launch. No host
 // synchronisation and no allocation, so the sequence can be captured in a CUDA graph and replayed.
 #include "host.cuh"
 

@@ -45,7 +45,7 @@ cudaError_t launch_bin_finish(const pk_cellpos* cells, const float* w, int64_t n
                               float* wsorted, int64_t* offsets, unsigned long long* counts, int64_t* sub,
                               long long* scan_scratch, cudaStream_t s);
 
-constexpr int kMaxBatch = 128;
+constexpr int kMaxBatch = 512;
 struct CatRanges {  // particle ranges of the catalogues of one batch group (absolute indices)
   int64_t off[kMaxBatch + 1];
   int nb;
@@ -65,7 +65,8 @@ cudaError_t launch_assign_direct_f64(int order, const void* pos, int fmt, const 
                                      bool interlace, double* g1, double* g2, int ldz, cudaStream_t s);
 // FP32 tile assignment (assign_tiles.cu: the scatter on sparse tiles, the key-cell kernel on dense
 // ones, chosen per tile), same grid layout, records binned by tile (any particle order inside a tile);
-// ncat > 1: catalogue c (blockIdx.y) uses tile offsets toff + c * ntiles and grids g + c * cat_stride.
+// ncat > 1: catalogue c's tiles have offsets toff + c * ntiles (one array of ncat * ntiles + 1
+// offsets) and grids g + c * cat_stride; the kernels take the tiles of all catalogues as one sequence.
 cudaError_t launch_assign_tiles_f32(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                     bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat = 1,
                                     int64_t cat_stride = 0, int run = 1);
