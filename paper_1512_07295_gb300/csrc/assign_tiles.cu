@@ -477,9 +477,12 @@ __device__ __forceinline__ int next_tile(const int64_t* toff, int64_t n, int t, 
 constexpr int SCATTER_THREADS = 256;
 
 // Pieces of the scatter are staged in two buffers: the next piece is copied while this one is used.
-template <bool W>
+// 768 records for runs of two or four tiles without weights (fewer barriers and bucket phases per
+// record, fuller last rounds; the blocks per SM of the launch bounds still fit); 512 otherwise: with
+// weights the buffers would not fit, and single tiles (four blocks per SM, 64 registers) would spill.
+template <int P, bool W, typename R = int, int S = 1>
 __host__ __device__ constexpr int scatter_chunk() {
-  return 512;
+  return (W || S == 1 || (P >= 5 && sizeof(R) == 8)) ? 512 : 768;
 }
 
 // Scatter region per order: nodes -1 .. T+2 of the tile (edge RS, first node one below the tile) up to
@@ -516,17 +519,17 @@ __device__ __forceinline__ void flush_scatter_region(R* reg, int ngrid, int cx0,
 
 template <int P, bool W, typename R = int, int S = 1>
 struct ScatterSmem {
-  int4 sp[2][scatter_chunk<W>()];
+  int4 sp[2][scatter_chunk<P, W, R, S>()];
   alignas(16) R reg[2][2][region_vol<P, S>()];  // two runs' regions in turn: one is flushed while the next is filled
   float red[2][SCATTER_THREADS / 32];
   unsigned long long mbar[2];
-  float sw[2][W ? scatter_chunk<W>() : 1];
+  float sw[2][W ? scatter_chunk<P, W, R, S>() : 1];
   // the piece's buckets per grid: counts (then cleared), sizes and offsets, the records in bucket order
   int cnt[2][32];
   int nr[2][32];
   int off[2][32];
   int rounds[2];
-  unsigned short list[2][scatter_chunk<W>()];
+  unsigned short list[2][scatter_chunk<P, W, R, S>()];
 };
 
 // First stencil node on one axis of grid G, relative to the tile origin, for orders 5 and 6 (from the
@@ -739,6 +742,12 @@ __device__ __forceinline__ int next_run(const int64_t* toff, int64_t n, int r, i
   return nruns;
 }
 
+// Blocks per SM of the scatter's launch bounds.
+template <int P, typename R, int S>
+__host__ __device__ constexpr int scatter_blocks() {
+  return (P >= 5 || sizeof(R) == 8 || S >= 4) ? 2 : (S == 2 ? 3 : 4);
+}
+
 // a3, FP32, direct scatter: a block takes runs of S tiles along z (one region per run) in a
 // grid-stride sequence, and the runs' pieces in order, the copy of the next piece overlapping the use
 // of the current one. A piece is up to CH consecutive records of the run's tiles of min_count ..
@@ -756,14 +765,14 @@ __device__ __forceinline__ int next_run(const int64_t* toff, int64_t n, int r, i
 // long long (PK_FIXED64, R = long long): int64 grids at the one scale 2^F from qsrc[2] = sum |w|
 // (fixed_scale), every contribution rounded on its own, so the sums do not depend on the order.
 template <int P, bool W, typename R, int S, typename GT = float>
-__global__ void __launch_bounds__(tiles::SCATTER_THREADS, (P >= 5 || sizeof(R) == 8 || S >= 4) ? 2 : (S == 2 ? 3 : 4))
+__global__ void __launch_bounds__(tiles::SCATTER_THREADS, scatter_blocks<P, R, S>())
     k_assign_scatter(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff,
                      int64_t n, int ng, int ntile, int interlace, GT* __restrict__ g1, GT* __restrict__ g2, int ldz,
                      int64_t cat_stride, int64_t min_count, int64_t max_count, int ncat, const double* __restrict__ qsrc = nullptr) {
   constexpr bool FX = sizeof(GT) == 8;
   static_assert(!FX || (sizeof(R) == 4 && S == 1 && P <= 4), "the deterministic path: 32-bit regions, single tiles");
   using namespace tiles;
-  constexpr int CH = scatter_chunk<W>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
+  constexpr int CH = scatter_chunk<P, W, R, S>(), THREADS = SCATTER_THREADS, NWARP = THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<P, W, R, S>& Sm = *reinterpret_cast<ScatterSmem<P, W, R, S>*>(smem_raw);
   const int ngrid = interlace ? 2 : 1;
@@ -1327,6 +1336,8 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
   const int ntile = tiles_per_axis(ng);
   const int nruns = ntile * ntile * (ntile / S);
   const size_t smem = sizeof(tiles::ScatterSmem<P, W, R, S>);
+  static_assert(scatter_blocks<P, R, S>() * (sizeof(tiles::ScatterSmem<P, W, R, S>) + 1024) <= 233472,
+                "the launch bounds' blocks per SM fit the SM's shared memory");
   int per_sm = 1;
   cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_scatter<P, W, R, S>), tiles::SCATTER_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
