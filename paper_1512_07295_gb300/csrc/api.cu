@@ -107,9 +107,8 @@ pk_status validate(const pk_config* c) {
 // fastest with single tiles (fewer blocks per catalogue at the lower occupancy of longer runs).
 int scatter_run(const pk_config* c, int64_t n, int ncat) {
   if (c->tile_run > 0) return c->tile_run;
-  if (ncat != 1) return 1;
   const int nt = c->ng / kTileCells;
-  const double mean = double(n) / (double(nt) * nt * nt);
+  const double mean = double(n) / (double(std::max(ncat, 1)) * nt * nt * nt);
   return mean >= 100.0 && mean <= 700.0 ? 2 : 1;
 }
 

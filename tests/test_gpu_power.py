@@ -242,3 +242,22 @@ def test_small_workspace_is_rejected():
     st = ffi.lib().pk_power(ctypes.byref(cfg.c()), api._p(pos), ffi.PK_POS_F64_XYZ, None, 100, api._p(out), api._p(out),
                             api._p(cnt), None, api._p(ws), 64, None)
     assert st == ffi.PK_ESIZE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("lo2, w2, nb", [(0, 1, 200), (0, 1, 400), (0, 1, 700), (2, 300, 200)])
+def test_estimate_paths_by_bin_count(prec, lo2, w2, nb):
+    # N = 64 puts four rows in each warp of the row estimate. 200 and 400 bins need its blocks of
+    # four and two warps (private copies within 96 KB); 700 bins go to the item kernel with shared
+    # atomics; edges up to 2 + 200 x 300 squared exceed 32 bits, so the last case takes the 64-bit bin
+    # test. Bins past the grid's largest |n| stay empty.
+    box, ng = 200.0, 64
+    pos = catalogs.zeldovich(32, box, rms=3.0, seed=71)
+    edges = lo2 + w2 * np.arange(nb + 1)
+    ref_pk, _, ref_cnt, _ = _ref.power(pos, box, ng, 4, edges=edges)
+    pk, _, cnt = api.power(_t(pos), api.Config(ng=ng, box=box, prec=prec, bin_lo2=lo2, bin_w2=w2, nbins=nb))
+    assert np.array_equal(cnt.cpu().numpy(), ref_cnt)
+    pk = pk.cpu().numpy()
+    full = ref_cnt > 0
+    assert np.all(np.isnan(pk[~full]))
+    assert _ref.rel(pk[full], ref_pk[full]) <= (1e-10 if prec == "fp64" else 1e-5)
