@@ -29,6 +29,7 @@ constexpr int K = T + 1;       // key cells per axis and grid
 constexpr int NKEY = K * K * K;
 constexpr int RS = T + 4;  // region edge (nodes -1 .. T+2)
 constexpr int RVOL = RS * RS * RS;
+constexpr int kDetRun = 32;  // deterministic mode: rounded particles summed per window (det_tile_scale)
 // Stencil start relative to the key cell: PCS and TSC start one node below it.
 template <int P>
 __host__ __device__ constexpr int s0() {
@@ -128,6 +129,16 @@ __device__ __forceinline__ f2x mul2(f2x a, f2x b) {
   return r;
 }
 __device__ __forceinline__ void fma2(f2x& d, f2x a, f2x b) { asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b)); }
+__device__ __forceinline__ f2x fma2c(f2x a, f2x b, f2x c) {
+  f2x r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 
 // Per-particle operands of the window update. Even p: the y weights as P/2 packed pairs and the x
 // and z weights broadcast into both halves of a pair; odd p: scalar weights.
@@ -184,6 +195,20 @@ struct Window<P, true> {
       }
     }
   }
+  // The deterministic mode: every product rounded to an integer by the FMA that adds 1.5 2^23 (exact
+  // for |product| <= 2^22), the integers summed exactly (the caller keeps every partial sum below 2^24).
+  __device__ __forceinline__ void add_rounded(const Operands<P>& o) {
+    const f2x m = pack2(12582912.0f, 12582912.0f), mn = pack2(-12582912.0f, -12582912.0f);
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+#pragma unroll
+      for (int bp = 0; bp < P / 2; ++bp) {
+        const f2x xy = mul2(o.xa[a], o.y2[bp]);
+#pragma unroll
+        for (int c = 0; c < P; ++c) v[a][bp][c] = add2(v[a][bp][c], add2(fma2c(xy, o.z2[c], m), mn));
+      }
+    }
+  }
   __device__ __forceinline__ void row(int a, int b, float* out) const {
 #pragma unroll
     for (int c = 0; c < P; ++c) out[c] = half2x(v[a][ypair<P>(b)][c], yhigh<P>(b));
@@ -209,6 +234,16 @@ struct Window<P, false> {
         const float xy = o.wx[a] * o.wy[b];
 #pragma unroll
         for (int c = 0; c < P; ++c) v[a][b][c] = fmaf(xy, o.wz[c], v[a][b][c]);
+      }
+  }
+  __device__ __forceinline__ void add_rounded(const Operands<P>& o) {
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b) {
+        const float xy = o.wx[a] * o.wy[b];
+#pragma unroll
+        for (int c = 0; c < P; ++c) v[a][b][c] += fmaf(xy, o.wz[c], 12582912.0f) - 12582912.0f;
       }
   }
   __device__ __forceinline__ void row(int a, int b, float* out) const {
@@ -443,6 +478,36 @@ __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t 
 // The first tile t + k stride (k >= 0) below ntiles whose population end - beg lies in [lo, hi], else
 // ntiles. Warp-parallel: 32 candidates per round of loads and a ballot; every lane of a full warp
 // calls it with the same arguments and gets the same answer, so all warps of a block agree.
+// Deterministic mode (k_assign_cells with int64 grids): the tile's scale 2^e with
+//  - node share x count x max |w| x 2^e < 2^30: no node of the 32-bit region can overflow (a count and
+//    a maximum, not a floating-point sum, so the scale does not depend on the order of the records);
+//  - 32 products of at most node share x max |w| x 2^e < 2^(ex1 + e) each below 2^24: a window's
+//    partial sums of kDetRun = 32 rounded products stay exact in FP32 (e <= 19 - ex1);
+//  - e <= F, the global scale 2^F = fixed_scale(qsrc[2]); shift = F - e carries the tile's integers to it.
+template <int P, bool W>
+__device__ __forceinline__ void det_tile_scale(const float* w, int64_t beg, int64_t end, const double* qsrc, float* red,
+                                               int nwarp, int tid, int nthreads, float* scale, int* shift) {
+  float wmax = 1.0f;
+  if (W) {
+    float m = 0.0f;
+    for (int64_t i = beg + tid; i < end; i += nthreads) m = fmaxf(m, fabsf(w[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    wmax = 0.0f;
+    for (int q = 0; q < nwarp; ++q) wmax = fmaxf(wmax, red[q]);
+  }
+  int ex, ex1, fx;
+  frexpf(fmaxf(float(end - beg) * wmax * node_share<P>(), 1.0f), &ex);  // node bound < 2^ex
+  frexpf(fmaxf(wmax * node_share<P>(), 1e-30f), &ex1);                  // one product < 2^ex1
+  frexpf(fixed_scale(qsrc[2]), &fx);                                     // 2^F = 2^(fx - 1)
+  static_assert(kDetRun == 32, "the window bound below is for 32 products");
+  const int e = min(min(30 - ex, 19 - ex1), fx - 1);
+  *scale = ldexpf(1.0f, e);
+  *shift = fx - 1 - e;
+}
+
 __device__ __forceinline__ int next_tile(const int64_t* toff, int64_t n, int t, int stride, int ntiles, int64_t lo,
                                          int64_t hi) {
   const int lane = threadIdx.x & 31;
@@ -1040,32 +1105,7 @@ struct CellSmem {
 // on the particle weight, so the window already holds fixed-point values; the next record is loaded
 // before the current one is accumulated.
 template <int P, bool W, typename R, int G>
-__device__ __forceinline__ void cell_key(const CellSmem<W, R>& S, int key, float wscale) {
-  const int* ends = S.hist[G];
-  const unsigned short* perm = S.perm[G];
-  const int jb = key == 0 ? 0 : ends[key - 1], je = ends[key];
-  const int kx = key % K, kz = (key / K) % K, ky = key / (K * K);
-  Window<P> win;
-  win.zero();
-  int4 r = make_int4(0, 0, 0, 0);
-  float rw = 1.0f;
-  if (jb < je) {
-    const int i = perm[jb];
-    r = S.sp[i];
-    if (W) rw = S.sw[i];
-  }
-  for (int j = jb; j < je; ++j) {
-    const int4 c = r;
-    const float cw = rw;
-    if (j + 1 < je) {
-      const int i = perm[j + 1];
-      r = S.sp[i];
-      if (W) rw = S.sw[i];
-    }
-    win.add(particle_operands<P, G>(c, cw * wscale));
-  }
-  const unsigned base =
-      smem_u32(&S.reg[G][0] + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1);
+__device__ __forceinline__ void add_window(const CellSmem<W, R>& S, const Window<P>& win, unsigned base) {
 #pragma unroll
   for (int a = 0; a < P; ++a)
 #pragma unroll
@@ -1077,18 +1117,69 @@ __device__ __forceinline__ void cell_key(const CellSmem<W, R>& S, int key, float
         red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * RS + c), to_fixed(v[c], static_cast<R*>(nullptr)));
     }
 }
+
+template <int P, bool W, typename R, int G, bool DET = false>
+__device__ __forceinline__ void cell_key(const CellSmem<W, R>& S, int key, float wscale) {
+  const int* ends = S.hist[G];
+  const unsigned short* perm = S.perm[G];
+  const int jb = key == 0 ? 0 : ends[key - 1], je = ends[key];
+  const int kx = key % K, kz = (key / K) % K, ky = key / (K * K);
+  const unsigned base =
+      smem_u32(&S.reg[G][0] + ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * RS + kz + s0<P>() + 1);
+  if constexpr (DET) {
+    // every product rounded to an integer, at most kDetRun particles per window (partial sums < 2^24,
+    // exact in FP32), so the region receives the same integers in any order
+    for (int j0 = jb; j0 < je; j0 += kDetRun) {
+      const int j1 = min(je, j0 + kDetRun);
+      Window<P> win;
+      win.zero();
+      for (int j = j0; j < j1; ++j) {
+        const int i = perm[j];
+        win.add_rounded(particle_operands<P, G>(S.sp[i], (W ? S.sw[i] : 1.0f) * wscale));
+      }
+      add_window<P, W, R, G>(S, win, base);
+    }
+  } else {
+    Window<P> win;
+    win.zero();
+    int4 r = make_int4(0, 0, 0, 0);
+    float rw = 1.0f;
+    if (jb < je) {
+      const int i = perm[jb];
+      r = S.sp[i];
+      if (W) rw = S.sw[i];
+    }
+    for (int j = jb; j < je; ++j) {
+      const int4 c = r;
+      const float cw = rw;
+      if (j + 1 < je) {
+        const int i = perm[j + 1];
+        r = S.sp[i];
+        if (W) rw = S.sw[i];
+      }
+      win.add(particle_operands<P, G>(c, cw * wscale));
+    }
+    add_window<P, W, R, G>(S, win, base);
+  }
+}
 }  // namespace tiles
 
 static_assert(2 * (sizeof(tiles::CellSmem<false, int>) + 1024) <= 233472 &&
                   2 * (sizeof(tiles::CellSmem<true, int>) + 1024) <= 233472,
               "two key-cell blocks (32-bit regions) per SM");
 
-template <int P, bool W, typename R>
+// GT: the grids' element type. float: FP32 grids. unsigned long long (PK_FIXED64, R = int): int64 grids
+// at the one scale 2^F from qsrc[2] = sum |w|; every product is rounded to an integer at the tile's
+// scale 2^e <= 2^F (det_tile_scale) and the integers are summed exactly, so the grids do not depend on
+// the order of the records or of the additions.
+template <int P, bool W, typename R, typename GT = float>
 __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     k_assign_cells(const pk_cellpos* __restrict__ p, const float* __restrict__ w, const int64_t* __restrict__ toff, int64_t n,
-                   int ng, int ntile, int interlace, float* __restrict__ g1, float* __restrict__ g2, int ldz,
-                   int64_t cat_stride, int64_t min_count, int64_t max_count, int ncat) {
+                   int ng, int ntile, int interlace, GT* __restrict__ g1, GT* __restrict__ g2, int ldz,
+                   int64_t cat_stride, int64_t min_count, int64_t max_count, int ncat, const double* __restrict__ qsrc = nullptr) {
   using namespace tiles;
+  constexpr bool DET = sizeof(GT) == 8;
+  static_assert(!DET || sizeof(R) == 4, "the deterministic mode: 32-bit regions");
   constexpr int CH = cell_chunk<W, R>(), THREADS = CELL_THREADS, NWARP = THREADS / 32;
   constexpr int SCAN_PER_THREAD = (NKEY + 1 + THREADS - 1) / THREADS;
   static_assert(CNT_BINS == 64, "count bins: two per lane of one warp");
@@ -1112,12 +1203,16 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
     nt = next_tile(toff, n, tile + int(gridDim.x), int(gridDim.x), ntiles, min_count, max_count);
     const int64_t beg = max(toff[tile], int64_t(0)), end = min(toff[tile + 1], n);
     const int cat = tile / ntiles_cat, lt = tile - cat * ntiles_cat;
-    float* const cg1 = g1 + cat * cat_stride;
-    float* const cg2 = g2 ? g2 + cat * cat_stride : nullptr;
+    GT* const cg1 = g1 + cat * cat_stride;
+    GT* const cg2 = g2 ? g2 + cat * cat_stride : nullptr;
     const int tz = lt % ntile, ty = (lt / ntile) % ntile, tx = lt / (ntile * ntile);
     const int cx0 = tx * T, cy0 = ty * T, cz0 = tz * T;  // first cell of the tile
     float scale, inv_scale;
-    tile_scale<P, W, BITS>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
+    int shift = 0;  // deterministic mode: F - e
+    if constexpr (DET)
+      det_tile_scale<P, W>(w, beg, end, qsrc, S.red, NWARP, tid, THREADS, &scale, &shift);
+    else
+      tile_scale<P, W, BITS>(w, beg, end, S.red, NWARP, tid, THREADS, &scale, &inv_scale);
     const float wscale = scale * weight_scale<P>();
     for (int64_t c0 = beg; c0 < end; c0 += CH) {
       const int m = int(min(int64_t(CH), end - c0));
@@ -1276,17 +1371,20 @@ __global__ void __launch_bounds__(tiles::CELL_THREADS, 2)
         for (int r0 = 0; r0 < nitems; r0 += 2 * nt) {  // two rounds: ascending, then descending
           const int i0 = r0 + t, i1 = r0 + 2 * nt - 1 - t;
           if (gsel == 0) {
-            if (i0 < nitems) cell_key<P, W, R, 0>(S, order[i0], wscale);
-            if (i1 < nitems) cell_key<P, W, R, 0>(S, order[i1], wscale);
+            if (i0 < nitems) cell_key<P, W, R, 0, DET>(S, order[i0], wscale);
+            if (i1 < nitems) cell_key<P, W, R, 0, DET>(S, order[i1], wscale);
           } else {
-            if (i0 < nitems) cell_key<P, W, R, 1>(S, order[i0], wscale);
-            if (i1 < nitems) cell_key<P, W, R, 1>(S, order[i1], wscale);
+            if (i0 < nitems) cell_key<P, W, R, 1, DET>(S, order[i0], wscale);
+            if (i1 < nitems) cell_key<P, W, R, 1, DET>(S, order[i1], wscale);
           }
         }
       }
       __syncthreads();
     }
-    flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, cg1, cg2, tid, THREADS);
+    if constexpr (DET)
+      flush_region_fixed<RS>(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, shift, cg1, cg2, tid, THREADS);
+    else
+      flush_region(&S.reg[0][0], ngrid, cx0, cy0, cz0, ng, ldz, inv_scale, cg1, cg2, tid, THREADS);
     __syncthreads();
   }
 }
@@ -1350,8 +1448,15 @@ static cudaError_t launch_scatter_pw(const pk_cellpos* p, const float* w, const 
   return cudaGetLastError();
 }
 
-// PK_FIXED64: every tile on the bank-ordered scatter (32-bit regions at a scale 2^e per tile that
-// divides the global 2^F), int64 grids.
+// The key-cell kernel over the tiles of lo .. hi particles (defined below).
+template <int P, bool W, typename R, typename GT = float>
+static cudaError_t launch_cells_one(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
+                                    bool interlace, GT* g1, GT* g2, int ldz, cudaStream_t s, int ncat,
+                                    int64_t cat_stride, int64_t lo, int64_t hi, const double* qsrc = nullptr);
+
+// PK_FIXED64, int64 grids: the sparse tiles on the bank-ordered scatter (32-bit regions at a scale 2^e
+// per tile that divides the global 2^F), the dense ones (orders 2..4) on the key cells summing rounded
+// products exactly (the same regions and scales).
 template <int P, bool W>
 static cudaError_t launch_scatter_fixed(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                         bool interlace, const double* wsums, unsigned long long* g1, unsigned long long* g2,
@@ -1364,10 +1469,14 @@ static cudaError_t launch_scatter_fixed(const pk_cellpos* p, const float* w, con
   cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), tiles::SCATTER_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
   const dim3 blocks(std::max(1, std::min(nruns, num_sms() * per_sm)), 1);
-  kern<<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, 0, 1, INT64_MAX,
-                                                   1, wsums);
+  kern<<<blocks, tiles::SCATTER_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz, 0, 1,
+                                                   int64_t(cells_min_count(P)) - 1, 1, wsums);
   count_launch();
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if constexpr (P >= 2 && P <= 4)  // the dense tiles: key cells summing rounded products exactly
+    return launch_cells_one<P, W, int, unsigned long long>(p, w, toff, n, ng, interlace, g1, g2, ldz, s, 1, 0,
+                                                           cells_min_count(P), INT64_MAX, wsums);
+  return cudaSuccess;
 }
 
 cudaError_t launch_assign_tiles_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
@@ -1396,19 +1505,19 @@ cudaError_t launch_assign_tiles_fixed(int order, const pk_cellpos* p, const floa
 // with twice the region memory, runs one block per SM.
 constexpr int64_t kHeavyTile = 16384;
 
-template <int P, bool W, typename R>
+template <int P, bool W, typename R, typename GT>
 static cudaError_t launch_cells_one(const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
-                                    bool interlace, float* g1, float* g2, int ldz, cudaStream_t s, int ncat,
-                                    int64_t cat_stride, int64_t lo, int64_t hi) {
+                                    bool interlace, GT* g1, GT* g2, int ldz, cudaStream_t s, int ncat,
+                                    int64_t cat_stride, int64_t lo, int64_t hi, const double* qsrc) {
   const int ntile = tiles_per_axis(ng);
   const int ntiles = ntile * ntile * ntile;
   const size_t smem = sizeof(tiles::CellSmem<W, R>);
   int per_sm = 1;
-  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_cells<P, W, R>), tiles::CELL_THREADS, smem, &per_sm);
+  cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_assign_cells<P, W, R, GT>), tiles::CELL_THREADS, smem, &per_sm);
   if (e != cudaSuccess) return e;
   const dim3 blocks(unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(ntiles) * ncat, int64_t(num_sms()) * per_sm))), 1);
-  k_assign_cells<P, W, R><<<blocks, tiles::CELL_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2, ldz,
-                                                                    cat_stride, lo, hi, ncat);
+  k_assign_cells<P, W, R, GT><<<blocks, tiles::CELL_THREADS, smem, s>>>(p, w, toff, n, ng, ntile, interlace ? 1 : 0, g1, g2,
+                                                                        ldz, cat_stride, lo, hi, ncat, qsrc);
   count_launch();
   return cudaGetLastError();
 }

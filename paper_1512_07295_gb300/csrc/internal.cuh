@@ -76,8 +76,9 @@ int scatter_run(const pk_config* c, int64_t n, int ncat);
 // PK_FIXED64: int64 grids at the scale 2^F derived on the device from wsums[2] = sum |w|, converted in
 // place to FP64.
 cudaError_t launch_fixed_to_double(unsigned long long* g, int64_t count, const double* wsums, cudaStream_t s);
-// The deterministic path on the bank-ordered scatter (orders 1..4): every tile, a 32-bit region at a
-// scale 2^e <= the global 2^F = fixed_scale(wsums[2]), added to the int64 grids shifted by F - e.
+// The deterministic path (orders 1..4): every tile a 32-bit region at a scale 2^e <= the global
+// 2^F = fixed_scale(wsums[2]), added to the int64 grids shifted by F - e; sparse tiles on the
+// bank-ordered scatter, dense ones on the key cells (products rounded one by one, summed exactly).
 cudaError_t launch_assign_tiles_fixed(int order, const pk_cellpos* p, const float* w, const int64_t* toff, int64_t n, int ng,
                                       bool interlace, const double* wsums, unsigned long long* g1, unsigned long long* g2,
                                       int ldz, cudaStream_t s);
