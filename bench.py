@@ -38,7 +38,7 @@ METRIC = "particles/s & P(k)/s (PCS+interlace, N_g=512), % HBM roofline vs plain
 # DRAM bytes (read + write) per particle of one k_assign_cells<4,false> launch, from an ncu capture of
 # the 256^3-particle / N_G = 128 case (8 particles per cell, as in the 1024^3 / N_G = 512 workload, so
 # the per-particle traffic carries over). None when the kernel has changed since the capture.
-ASSIGN_TRAFFIC_PER_PARTICLE = 299.13e6 / 256 ** 3
+ASSIGN_TRAFFIC_PER_PARTICLE = 299.68e6 / 256 ** 3
 ASSIGN_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 256^3 particles / N_G=128 "
                          "(profiles/k_assign_cells_pcs_interlace_256cube_ng128.md), scaled by the particle count")
 RMS_DISP = 4.0
