@@ -202,6 +202,10 @@ pk_status pk_power_binned(const pk_config* cfg, const pk_cellpos* sorted_dev, co
  * callers cache it. Computed by an FP64 convolution of shell indicators, rounded, summed in int64,
  * on the same grid M as pk_bispectrum. */
 int32_t pk_bispectrum_ntri(int32_t nshells);
+/* a7 -- The triangles of pk_bispectrum_counts and pk_bispectrum in their output order: tri_host (HOST
+ * memory, int32[3 ntri], caller-owned) receives (s1, s2, s3) per triangle. Returns ntri, or 0 (and
+ * writes nothing) for nshells outside 1..64 or a NULL tri_host. Host work only. */
+int32_t pk_bispectrum_triangles(int32_t nshells, int32_t* tri_host);
 pk_status pk_bispectrum_counts(const pk_config* cfg, int32_t shell_lo, int32_t shell_w, int32_t nshells,
                                int64_t* counts_dev, void* ws, size_t ws_bytes, void* stream);
 

@@ -264,8 +264,12 @@ def bispectrum_ntri(nshells):
 
 
 def triangles(nshells):
-    """Shell triples (s1 >= s2 >= s3, s1 <= s2 + s3 + 1) in the library's order."""
-    return [(a, b, c) for a in range(nshells) for b in range(a + 1) for c in range(b + 1) if a <= b + c + 1]
+    """Shell triples (s1, s2, s3) of pk_bispectrum's outputs, in order (pk_bispectrum_triangles)."""
+    import numpy as np
+
+    tri = np.zeros(3 * max(bispectrum_ntri(nshells), 1), dtype=np.int32)
+    m = int(ffi.lib().pk_bispectrum_triangles(int(nshells), tri.ctypes.data_as(ctypes.c_void_p)))
+    return [tuple(int(v) for v in tri[3 * i:3 * i + 3]) for i in range(m)]
 
 
 def bispectrum_counts(cfg, shell_lo, shell_w, nshells, device="cuda"):

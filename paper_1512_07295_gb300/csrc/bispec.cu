@@ -580,6 +580,13 @@ int32_t pk_bispectrum_ntri(int32_t nshells) {
   return int32_t(make_triangles(nshells).size() / 3);
 }
 
+int32_t pk_bispectrum_triangles(int32_t nshells, int32_t* tri_host) {
+  if (nshells < 1 || nshells > 64 || !tri_host) return 0;
+  const std::vector<int> t = make_triangles(nshells);
+  for (size_t i = 0; i < t.size(); ++i) tri_host[i] = int32_t(t[i]);
+  return int32_t(t.size() / 3);
+}
+
 pk_status pk_bispectrum_counts(const pk_config* cfg, int32_t shell_lo, int32_t shell_w, int32_t nshells, int64_t* counts_dev,
                                void* ws, size_t ws_bytes, void* stream) {
   clear_err();

@@ -54,6 +54,7 @@ SIGNATURES = {
     "pk_power_binned": (c_int32, [_CFG, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_size_t, c_void_p]),
     "pk_bispectrum_ntri": (c_int32, [c_int32]),
+    "pk_bispectrum_triangles": (c_int32, [c_int32, c_void_p]),
     "pk_bispectrum_counts": (c_int32, [_CFG, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pk_bispectrum": (c_int32, [_CFG, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pk_power_backward": (c_int32, [_CFG, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_size_t,

@@ -45,6 +45,29 @@ def test_host_only_calls(lib):
     assert lib.pk_bispectrum_ntri(0) == 0
 
 
+def test_bispectrum_triangle_list(lib):
+    # Shells of width w hold w s <= |k| < w (s + 1) (shell_lo = 0). Three wave vectors with those
+    # lengths can close (k1 + k2 + k3 = 0) iff the longest can be at most the sum of the other two: the
+    # smallest k1 (w s1) below the largest k2 + k3 (w (s2 + s3 + 2), an open bound). The list must be
+    # every such ordered triple s1 >= s2 >= s3 once, s1 slowest, with 508 triangles for the 16 shells
+    # of the bispectrum configuration.
+    for nshells in (1, 2, 5, 16):
+        n = lib.pk_bispectrum_ntri(nshells)
+        tri = (ctypes.c_int32 * (3 * n))()
+        assert lib.pk_bispectrum_triangles(nshells, tri) == n
+        got = [tuple(tri[3 * i:3 * i + 3]) for i in range(n)]
+        closable = []
+        for s1 in range(nshells):
+            for s2 in range(s1 + 1):
+                for s3 in range(s2 + 1):
+                    if s1 < s2 + s3 + 2:  # min |k1| < max(|k2| + |k3|), in units of w
+                        closable.append((s1, s2, s3))
+        assert got == closable
+    assert lib.pk_bispectrum_ntri(16) == 508
+    assert lib.pk_bispectrum_triangles(0, (ctypes.c_int32 * 3)()) == 0
+    assert lib.pk_bispectrum_triangles(16, None) == 0
+
+
 def test_invalid_config_is_rejected_before_any_launch(lib):
     cfg = ffi.PkConfig()
     lib.pk_default_config(ctypes.byref(cfg), 63, 1000.0)  # odd grid
