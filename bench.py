@@ -436,7 +436,7 @@ def row_batch(dev, profile_range=False, ncats=512):
     del parts
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     # group size chosen by the library's autotuner, then the call timed eagerly and as a CUDA graph replay
-    batch, tune_ms = api.autotune_batch(cells, offs, cfg, candidates=(64, 128, 256, 512), reps=2, runs=(1, 2))
+    batch, tune_ms = api.autotune_batch(cells, offs, cfg, candidates=(64, 128, 256, 512), reps=2, runs=(1, 2, 4))
     wsc = api.batch_workspace(cfg, batch, api.max_group_particles(offs, batch), dev)
     pkb = torch.empty((ncats, cfg.nb), dtype=torch.float64, device=dev)
     nmb = torch.empty((ncats, cfg.nb), dtype=torch.int64, device=dev)
