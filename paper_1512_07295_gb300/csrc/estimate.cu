@@ -225,8 +225,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 3) k_estimate(const 
             const C2<R> phz = {pc[iz], ps[iz]};
             const C2<R> t = cmul(cmul(phxy, phz), g2);
             d = {(g1.x + t.x) * c, (g1.y + t.y) * c};
-            const C2<R> tp = cmul(cmul(phxy_p, conj(phz)), conj(g2));
-            dp = {(g1.x + tp.x) * c, (-g1.y + tp.y) * c};
+            if (ix == half || iy == half) {  // the partner's phase is not the conjugate on the Nyquist rows
+              const C2<R> tp = cmul(cmul(phxy_p, conj(phz)), conj(g2));
+              dp = {(g1.x + tp.x) * c, (-g1.y + tp.y) * c};
+            } else {
+              dp = conj(d);
+            }
           } else {
             d = {g1.x * c, g1.y * c};
             dp = conj(d);
@@ -242,7 +246,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 3) k_estimate(const 
               cnt = 2;
             }
             val *= *vol;
-            ks = R(cnt) * (sizeof(R) == 4 ? R(rn) : sqrt(R(n2)));
+            // |n| sums are not used by the deterministic mode's first pass
+            if (a.det_pass != 1) ks = R(cnt) * (sizeof(R) == 4 ? R(rn) : sqrt(R(n2)));
           }
         }
         if (dout) dout[idx] = d;
