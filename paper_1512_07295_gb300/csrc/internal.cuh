@@ -105,7 +105,8 @@ struct EstimateArgs {
   // (nbins doubles, device) holds the per-bin fixed-point scales between the passes
   int det_pass = 0;
   double* det_scale = nullptr;
-  // set by the launcher: per-warp private bins in shared memory instead of shared atomics
+  // set by the launcher: 1 = k_estimate_rows (private bins per row of a warp, no atomics), 0 = k_estimate
+  // (32-slot items, shared atomics: the deterministic passes and bins beyond the private copies' room)
   int priv = 0;
   // set by the launcher for the row kernel: rows a warp takes at once (a private bin copy each)
   int rows_per_warp = 1;
