@@ -107,3 +107,26 @@ def test_autotuned_group_size_gives_the_same_spectra():
     b, nb = api.batch_power(cells, offs, cfg, batch=3)
     assert torch.equal(na, nb)
     assert _ref.rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-6
+
+
+def test_one_group_of_the_largest_size():
+    # 600 catalogues of 50 .. 3000 particles in groups of 512 (the largest): the tile kernels take the
+    # runs of all 512 catalogues of the first group as one sequence; every spectrum equals the
+    # single-catalogue path, and a sample of them the FP64 oracle
+    box, ng = 200.0, 16
+    sizes = catalogs.batch_sizes(600, 50, 3000, seed=72)
+    cats = [catalogs.poisson(int(s), box, seed=300 + i) for i, s in enumerate(sizes)]
+    cfg = api.Config(ng=ng, box=box, prec="fp32")
+    cells = torch.cat([api.prepare(_t(c), cfg) for c in cats])
+    offs = np.concatenate([[0], np.cumsum([len(c) for c in cats])])
+    pk, nm = api.batch_power(cells, offs, cfg, batch=512)
+    pk, nm = pk.cpu().numpy(), nm.cpu().numpy()
+    for i in range(len(cats)):
+        single, _, cnt = api.power(cells[offs[i]:offs[i + 1]].contiguous(), cfg)
+        assert np.array_equal(nm[i], cnt.cpu().numpy())
+        assert _ref.rel(pk[i], single.cpu().numpy()) <= 1e-6, i
+    for i in (0, 255, 511, 512, 599):
+        u = _ref.cellpos_to_units(cells[offs[i]:offs[i + 1]].cpu().numpy(), ng)
+        ref_pk, _, ref_cnt = _ref.power_units(u, box, ng, 4)
+        assert np.array_equal(nm[i], ref_cnt)
+        assert _ref.rel(pk[i], ref_pk) <= 1e-5, i
