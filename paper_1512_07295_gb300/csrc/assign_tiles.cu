@@ -654,6 +654,19 @@ __device__ __forceinline__ R fixed_product(float x, float y) {
   }
 }
 
+// Fixed-point value of one addition: through fixed_product, or (SUB) the bits of the subnormal product
+// (mul.rn.f32 without .ftz keeps subnormal results whatever the compiler's flush-to-zero setting).
+template <int P, typename R, bool SUB>
+__device__ __forceinline__ R node_value(float xy, float z) {
+  if constexpr (SUB) {
+    float r;
+    asm("mul.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(xy), "f"(z));
+    return __float_as_int(r);
+  } else {
+    return fixed_product<P, R>(xy, z);
+  }
+}
+
 // Buckets of the bank order: 16 for even p on the 12-node region (plane pairs 16 banks apart), 32
 // otherwise; lanes per bucket.
 template <int P, typename R = int>
@@ -671,15 +684,30 @@ __host__ __device__ constexpr int bank_buckets() {
 // region's fixed-point scale). Region nodes of the stencil: key + S0 + 1 .. key + S0 + p per axis.
 // lane: the caller's lane; for even p the planes are taken in pairs swapped when the lane's bank half
 // differs from the stencil origin's (the bank order above).
-template <int P, int G, int S, typename R>
+// NN (unit weights: every product >= 0) with orders 3..6 and 32-bit regions: the products are rounded
+// to integers by the multiply itself. With the x weights scaled by 2^-100 and the z weights by 2^-49
+// (both exact, the operands stay normal), x y z 2^-149 falls in the subnormal range, whose spacing
+// is 2^-149: the multiply rounds it (to nearest, ties to even) to m 2^-149 with m = round(x y z), and
+// the float's bits are m itself (every addition stays below 2^22 < 2^23, scatter_scale's cap). The
+// same integers as the 1.5 2^23 addition of fixed_product, without its bias subtraction.
+template <int P, typename R, bool NN>
+__host__ __device__ constexpr bool subnormal_rounding() {
+  return NN && P >= 3 && sizeof(R) == 4;
+}
+
+template <int P, int G, int S, typename R, bool NN = false>
 __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz, float fx, float fy, float fz, float sc,
                                                  int lane) {
+  constexpr bool SUB = subnormal_rounding<P, R, NN>();
   if constexpr (P >= 5) {  // orders 5 and 6: the B-spline weights and stencil start per axis
     constexpr int E = region_edge<P>(), O = region_off<P>();
     float wx[P], wy[P], wz[P];
     const int sx = high_start<P, G>(lx, fx, wx), sy = high_start<P, G>(ly, fy, wy), sz = high_start<P, G>(lz, fz, wz);
 #pragma unroll
-    for (int a = 0; a < P; ++a) wx[a] *= sc;
+    for (int a = 0; a < P; ++a) wx[a] *= SUB ? sc * 0x1p-100f : sc;
+    if constexpr (SUB)
+#pragma unroll
+      for (int c = 0; c < P; ++c) wz[c] *= 0x1p-49f;
     static_assert(S == 1, "orders 5 and 6 take single tiles");
     const unsigned base = smem_u32(reg + ((sx + O) * E + sy + O) * E + sz + O);
 #pragma unroll
@@ -689,7 +717,7 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
         const float xy = wx[a] * wy[b];
 #pragma unroll
         for (int c = 0; c < P; ++c)
-          red_shared(base + unsigned(sizeof(R)) * ((a * E + b) * E + c), fixed_product<P, R>(xy, wz[c]));
+          red_shared(base + unsigned(sizeof(R)) * ((a * E + b) * E + c), node_value<P, R, SUB>(xy, wz[c]));
       }
   } else {
     float tx, ty, tz;
@@ -699,7 +727,10 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
     weights<P>(ty, wy);
     weights<P>(tz, wz);
 #pragma unroll
-    for (int a = 0; a < P; ++a) wx[a] *= sc;
+    for (int a = 0; a < P; ++a) wx[a] *= SUB ? sc * 0x1p-100f : sc;
+    if constexpr (SUB)
+#pragma unroll
+      for (int c = 0; c < P; ++c) wz[c] *= 0x1p-49f;
     constexpr int EZ = region_z<P, S>();  // rows along z; planes RS EZ nodes apart (16 mod 32)
     const int q = ((kx + s0<P>() + 1) * RS + ky + s0<P>() + 1) * EZ + kz + s0<P>() + 1;
     unsigned base_even = smem_u32(reg + q), base_odd = base_even;
@@ -723,7 +754,7 @@ __device__ __forceinline__ void scatter_particle(R* reg, int lx, int ly, int lz,
         const float xy = wx[a] * wy[b];
 #pragma unroll
         for (int c = 0; c < P; ++c)
-          red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * EZ + c), fixed_product<P, R>(xy, wz[c]));
+          red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * EZ + c), node_value<P, R, SUB>(xy, wz[c]));
       }
     }
   }
@@ -1035,7 +1066,7 @@ __global__ void __launch_bounds__(tiles::SCATTER_THREADS, scatter_blocks<P, R, S
         lz += half_shift(fz, &f2);
         fz = f2;
       }
-      scatter_particle<P, 0, S>(Sm.reg[rb][g], lx, ly, lz, fx, fy, fz, sc, lane);
+      scatter_particle<P, 0, S, R, !W>(Sm.reg[rb][g], lx, ly, lz, fx, fy, fz, sc, lane);
     }
     if (!has_next || nxt.first) {  // last piece of the run: its region is flushed with the next piece
       pending = true;
