@@ -209,25 +209,6 @@ struct Window<P, true> {
       }
     }
   }
-  // The deterministic mode with unit weights: the x weights carry 2^-100 and the z weights are scaled
-  // by 2^-49 here, so every product x y z 2^-149 is subnormal and the multiply rounds it to an integer
-  // multiple m 2^-149; sums of such values are exact integer sums up to 2^24 2^-149 (det_tile_scale
-  // keeps them there), and the float's bits are the integer m.
-  __device__ __forceinline__ void add_subnormal(const Operands<P>& o) {
-    const f2x s49 = pack2(0x1p-49f, 0x1p-49f);
-    f2x zs[P];
-#pragma unroll
-    for (int c = 0; c < P; ++c) zs[c] = mul2(o.z2[c], s49);
-#pragma unroll
-    for (int a = 0; a < P; ++a) {
-#pragma unroll
-      for (int bp = 0; bp < P / 2; ++bp) {
-        const f2x xy = mul2(o.xa[a], o.y2[bp]);
-#pragma unroll
-        for (int c = 0; c < P; ++c) v[a][bp][c] = add2(v[a][bp][c], mul2(xy, zs[c]));
-      }
-    }
-  }
   __device__ __forceinline__ void row(int a, int b, float* out) const {
 #pragma unroll
     for (int c = 0; c < P; ++c) out[c] = half2x(v[a][ypair<P>(b)][c], yhigh<P>(b));
@@ -263,23 +244,6 @@ struct Window<P, false> {
         const float xy = o.wx[a] * o.wy[b];
 #pragma unroll
         for (int c = 0; c < P; ++c) v[a][b][c] += fmaf(xy, o.wz[c], 12582912.0f) - 12582912.0f;
-      }
-  }
-  __device__ __forceinline__ void add_subnormal(const Operands<P>& o) {
-    float zs[P];
-#pragma unroll
-    for (int c = 0; c < P; ++c) asm("mul.rn.f32 %0, %1, %2;" : "=f"(zs[c]) : "f"(o.wz[c]), "f"(0x1p-49f));
-#pragma unroll
-    for (int a = 0; a < P; ++a)
-#pragma unroll
-      for (int b = 0; b < P; ++b) {
-        const float xy = o.wx[a] * o.wy[b];
-#pragma unroll
-        for (int c = 0; c < P; ++c) {
-          float t;
-          asm("mul.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(xy), "f"(zs[c]));
-          asm("add.rn.f32 %0, %0, %1;" : "+f"(v[a][b][c]) : "f"(t));
-        }
       }
   }
   __device__ __forceinline__ void row(int a, int b, float* out) const {
@@ -511,13 +475,14 @@ __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t 
   *inv_scale = ldexpf(1.0f, ex - BITS);
 }
 
+// The first tile t + k stride (k >= 0) below ntiles whose population end - beg lies in [lo, hi], else
+// ntiles. Warp-parallel: 32 candidates per round of loads and a ballot; every lane of a full warp
+// calls it with the same arguments and gets the same answer, so all warps of a block agree.
 // Deterministic mode (k_assign_cells with int64 grids): the tile's scale 2^e with
 //  - node share x count x max |w| x 2^e < 2^30: no node of the 32-bit region can overflow (a count and
 //    a maximum, not a floating-point sum, so the scale does not depend on the order of the records);
 //  - 32 products of at most node share x max |w| x 2^e < 2^(ex1 + e) each below 2^24: a window's
-//    partial sums of kDetRun = 32 rounded products stay within 2^24, exact in FP32 (e <= 19 - ex1);
-//    with unit weights they are held as m 2^-149, exact too, and for 0 <= m <= 2^24 (subnormal, then
-//    the lowest normal binade, where the spacing is still 2^-149) the float's bits are m itself;
+//    partial sums of kDetRun = 32 rounded products stay exact in FP32 (e <= 19 - ex1);
 //  - e <= F, the global scale 2^F = fixed_scale(qsrc[2]); shift = F - e carries the tile's integers to it.
 template <int P, bool W>
 __device__ __forceinline__ void det_tile_scale(const float* w, int64_t beg, int64_t end, const double* qsrc, float* red,
@@ -543,9 +508,6 @@ __device__ __forceinline__ void det_tile_scale(const float* w, int64_t beg, int6
   *shift = fx - 1 - e;
 }
 
-// The first tile t + k stride (k >= 0) below ntiles whose population end - beg lies in [lo, hi], else
-// ntiles. Warp-parallel: 32 candidates per round of loads and a ballot; every lane of a full warp
-// calls it with the same arguments and gets the same answer, so all warps of a block agree.
 __device__ __forceinline__ int next_tile(const int64_t* toff, int64_t n, int t, int stride, int ntiles, int64_t lo,
                                          int64_t hi) {
   const int lane = threadIdx.x & 31;
@@ -1187,20 +1149,6 @@ __device__ __forceinline__ void add_window(const CellSmem<W, R>& S, const Window
     }
 }
 
-// The deterministic windows of unit weights hold m 2^-149 with 0 <= m <= 2^24: their bits are m.
-template <int P, bool W, typename R, int G>
-__device__ __forceinline__ void add_window_bits(const CellSmem<W, R>& S, const Window<P>& win, unsigned base) {
-#pragma unroll
-  for (int a = 0; a < P; ++a)
-#pragma unroll
-    for (int b = 0; b < P; ++b) {
-      float v[P];
-      win.row(a, b, v);
-#pragma unroll
-      for (int c = 0; c < P; ++c) red_shared(base + unsigned(sizeof(R)) * ((a * RS + b) * RS + c), __float_as_int(v[c]));
-    }
-}
-
 template <int P, bool W, typename R, int G, bool DET = false>
 __device__ __forceinline__ void cell_key(const CellSmem<W, R>& S, int key, float wscale) {
   const int* ends = S.hist[G];
@@ -1218,15 +1166,9 @@ __device__ __forceinline__ void cell_key(const CellSmem<W, R>& S, int key, float
       win.zero();
       for (int j = j0; j < j1; ++j) {
         const int i = perm[j];
-        if constexpr (W)
-          win.add_rounded(particle_operands<P, G>(S.sp[i], S.sw[i] * wscale));
-        else
-          win.add_subnormal(particle_operands<P, G>(S.sp[i], wscale * 0x1p-100f));
+        win.add_rounded(particle_operands<P, G>(S.sp[i], (W ? S.sw[i] : 1.0f) * wscale));
       }
-      if constexpr (W)
-        add_window<P, W, R, G>(S, win, base);
-      else
-        add_window_bits<P, W, R, G>(S, win, base);
+      add_window<P, W, R, G>(S, win, base);
     }
   } else {
     Window<P> win;
