@@ -475,9 +475,6 @@ __device__ __forceinline__ void tile_scale(const float* w, int64_t beg, int64_t 
   *inv_scale = ldexpf(1.0f, ex - BITS);
 }
 
-// The first tile t + k stride (k >= 0) below ntiles whose population end - beg lies in [lo, hi], else
-// ntiles. Warp-parallel: 32 candidates per round of loads and a ballot; every lane of a full warp
-// calls it with the same arguments and gets the same answer, so all warps of a block agree.
 // Deterministic mode (k_assign_cells with int64 grids): the tile's scale 2^e with
 //  - node share x count x max |w| x 2^e < 2^30: no node of the 32-bit region can overflow (a count and
 //    a maximum, not a floating-point sum, so the scale does not depend on the order of the records);
@@ -508,6 +505,9 @@ __device__ __forceinline__ void det_tile_scale(const float* w, int64_t beg, int6
   *shift = fx - 1 - e;
 }
 
+// The first tile t + k stride (k >= 0) below ntiles whose population end - beg lies in [lo, hi], else
+// ntiles. Warp-parallel: 32 candidates per round of loads and a ballot; every lane of a full warp
+// calls it with the same arguments and gets the same answer, so all warps of a block agree.
 __device__ __forceinline__ int next_tile(const int64_t* toff, int64_t n, int t, int stride, int ntiles, int64_t lo,
                                          int64_t hi) {
   const int lane = threadIdx.x & 31;
